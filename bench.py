@@ -1,0 +1,420 @@
+"""Benchmark: Mpixels/s of the vector order-statistic filters on one GB300,
+minimax vs exact, with the PSNR drop of every minimax variant.
+
+Workload (one step): three seeded 1024 x 1024 RGBX synthetic images
+(piecewise-smooth polygons, channels correlated ~0.9) with 5 %, 15 % and
+30 % random-valued per-channel impulses; on each image and for windows 3 x 3
+and 5 x 5, every filter of the paper with every approximation: VMF (exact),
+BVDF (exact, minimax arccos of degree 2..6), AMNFE and AMNFG (exact, minimax
+exp of degree 2..6, the paper's (4,4) rational), EVMF (exact, minimax
+z ln z of degree 2..6, the paper's rational): 28 variants x 2 windows x 3
+images = 168 launches, 176 Mpixels per step.
+
+`value` is the whole-job throughput (output pixels of all launches / time).
+Per filter and window, `per_filter_window` gives the exact path's Mpix/s and
+the fastest minimax variant whose PSNR drop against the exact output is at
+most 0.05 dB, with its speedup.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 1024
+NOISE = [(0.05, 2), (0.15, 3), (0.30, 4)]  # (p, seed)
+WINDOWS = [3, 5]
+METRIC = "Mpixels/s per filter/window, minimax vs exact, 1 GB300, at ≤0.05 dB PSNR drop"
+POOL = 48  # rotating input/output copies: 48 x 8 MB = 384 MB > 129 MB L2
+
+
+def variants():
+    out = [("vmf", "exact", 0)]
+    out += [("bvdf", "exact", 0)] + [("bvdf", "poly", d) for d in range(2, 7)]
+    for c in ("amnfe", "amnfg", "evmf"):
+        out += [(c, "exact", 0)] + [(c, "poly", d) for d in range(2, 7)] + [(c, "rational", 4)]
+    return out
+
+
+def vkey(c, a, d, w):
+    return "%s/%s/w%d" % (c, a if a != "poly" else "poly%d" % d, w)
+
+
+# ---------------------------------------------------------------- clocks
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------- roofline model
+
+# FP32-pipe instructions per pair / per sample of each kernel, counted from the
+# kernel source (vf_kernels.cuh); MUFU (SFU) operations separately.  FFMA,
+# FADD, FMUL, FMNMX, FSETP/FSEL each count as one.
+def ops_per_pixel(crit, approx, deg, w):
+    n = w * w
+    P = n * (n - 1) // 2
+    if crit == "vmf":
+        return P * 8 + n, P          # 3 sub, mul + 2 fma, 2 agg adds; argmin
+    if crit == "bvdf":
+        if approx == "exact":
+            return None, None        # atan2f: library sequence, not counted
+        # dot 3, rr 1, z 2, cross 9, t2 3, 1+z 1, two Horner chains 2 deg,
+        # select 2, 2 agg adds; rcp + sqrt on MUFU
+        return P * (23 + 2 * deg) + n, 2 * P
+    if crit in ("amnfe", "amnfg"):
+        per_e = {"exact": None, "poly": deg, "rational": 10}[approx]
+        if per_e is None:
+            return None, None
+        return P * 7 + n * (14 + per_e), n * (1 + (approx == "rational"))
+    return None, None                # EVMF: data-dependent switch fraction
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="profiling: run one kernel, e.g. bvdf/poly4/w5, on a --size image")
+    ap.add_argument("--size", type=int, default=6144)
+    ap.add_argument("--launches", type=int, default=2)
+    args = ap.parse_args()
+    if args.case:
+        return run_case(args)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1009_0959_gb300 import synth, vfilt
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # inputs: resident in HBM before timing; rotating pool larger than L2
+    imgs = []
+    for p, seed in NOISE:
+        clean, noisy = synth.noisy(H, W, p, seed + 100 * rank)
+        imgs.append((clean, noisy))
+    dev_imgs = [torch.from_numpy(synth.to_rgbx(n)).cuda() for _, n in imgs]
+    pool_in = [dev_imgs[k % 3].clone() for k in range(POOL)]
+    pool_out = [torch.empty_like(pool_in[0]) for _ in range(POOL)]
+    V = variants()
+    launches = [(c, a, d, w, k) for w in WINDOWS for (c, a, d) in V for k in range(3)]
+
+    # quality (outside the timed region): PSNR vs clean, drop vs the exact path
+    quality = {}
+    ref_out = {}
+    for w in WINDOWS:
+        for (c, a, d) in V:
+            psnr, changed = [], []
+            for k in range(3):
+                o = vfilt.filter(dev_imgs[k], criterion=c, window=w, approx=a, degree=max(d, 2))
+                o = o.cpu().numpy()[..., :3]
+                if a == "exact":
+                    ref_out[(c, w, k)] = o
+                clean = imgs[k][0]
+                mse = ((clean.astype(np.float64) - o) ** 2).mean()
+                psnr.append(10 * math.log10(255 ** 2 / mse))
+                changed.append(float(np.any(o != ref_out[(c, w, k)], axis=-1).mean()))
+            quality[vkey(c, a, d, w)] = {"psnr_db": psnr, "changed": changed}
+    for w in WINDOWS:
+        for (c, a, d) in V:
+            q = quality[vkey(c, a, d, w)]
+            qe = quality[vkey(c, "exact", 0, w)]
+            q["psnr_drop_db"] = max(pe - pa for pe, pa in zip(qe["psnr_db"], q["psnr_db"]))
+            q["changed_max"] = max(q["changed"])
+
+    stream = torch.cuda.current_stream()
+    per = {vkey(c, a, d, w): [] for (c, a, d, w, k) in launches}
+
+    def step(record):
+        for i, (c, a, d, w, k) in enumerate(launches):
+            slot = (step.counter + i) % POOL
+            src = pool_in[(slot // 3) * 3 + k]  # a copy of image k, rotating
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            vfilt.filter(src, pool_out[slot], criterion=c, window=w, approx=a, degree=max(d, 2),
+                         stream=stream)
+            if record:
+                e1.record(stream)
+                per[vkey(c, a, d, w)].append((e0, e1))
+        step.counter += len(launches)
+    step.counter = 0
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+        dist.barrier()
+
+    pix_per_step = len(launches) * H * W
+    value = pix_per_step * args.steps * world / (ms_total / 1e3) / 1e6
+    kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v) for k, v in per.items()}
+
+    # per filter / window: exact vs fastest minimax meeting the 0.05 dB bar
+    pfw = {}
+    for w in WINDOWS:
+        for crit in ("vmf", "bvdf", "amnfe", "amnfg", "evmf"):
+            ex = vkey(crit, "exact", 0, w)
+            ent = {"exact_mpix_s": round(H * W / kern_ms[ex] / 1e3, 1)}
+            best = None
+            for (c, a, d) in V:
+                if c != crit or a == "exact":
+                    continue
+                k = vkey(c, a, d, w)
+                q = quality[k]
+                row = {"mpix_s": round(H * W / kern_ms[k] / 1e3, 1),
+                       "speedup": round(kern_ms[ex] / kern_ms[k], 3),
+                       "psnr_drop_db": round(q["psnr_drop_db"], 4),
+                       "changed_max": round(q["changed_max"], 5),
+                       "meets_bar": q["psnr_drop_db"] <= 0.05}
+                ent[k.split("/")[1]] = row
+                if row["meets_bar"] and (best is None or row["mpix_s"] > ent[best]["mpix_s"]):
+                    best = k.split("/")[1]
+            ent["best_minimax"] = best
+            pfw["%s/w%d" % (crit, w)] = ent
+
+    # roofline: the kernel with the largest share of the step
+    share = {k: v * args.steps * 3 for k, v in kern_ms.items()}
+    dom = max(share, key=share.get)
+    c, a, wtag = dom.split("/")
+    d = int(a[4:]) if a.startswith("poly") else 4
+    a = "poly" if a.startswith("poly") else a
+    fp32, mufu = ops_per_pixel(c, a, d, int(wtag[1:]))
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tinst = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lane-instructions/s
+    roof = {"bound": "alu", "kernel": dom, "unit": "Tinst/s", "peak": round(peak_tinst, 2),
+            "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (recipe unit counts and max "
+                           "clock)" % sm_max,
+            "traffic": None}
+    if fp32 is not None:
+        ach = fp32 * H * W / (kern_ms[dom] / 1e3) / 1e12
+        roof.update({"achieved": round(ach, 3), "frac": round(ach / peak_tinst, 4),
+                     "ops_per_pixel": fp32, "mufu_per_pixel": mufu})
+    else:
+        roof.update({"achieved": None, "frac": None,
+                     "note": "per-pixel FP32 count of this kernel is not fixed by the source"})
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpixels/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded piecewise-smooth RGB, random-valued impulses)",
+            "config": {"workload": "3 x 1024x1024 RGBX (p=5/15/30%), VMF/BVDF/AMNFE/AMNFG/EVMF, "
+                                   "exact + minimax poly deg 2-6 + paper rationals, w=3,5",
+                       "launches_per_step": len(launches), "mpix_per_step": pix_per_step / 1e6,
+                       "l2": "inputs rotate through a %d MB pool (> 129 MB L2)" %
+                             (POOL * 8),
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "gpu_launches": len(launches) * args.steps,
+            "clocks": ck, "roofline": roof, "per_filter_window": pfw}
+
+    # end to end through the public host-buffer call (copies inside the timing)
+    hin = [torch.from_numpy(synth.to_rgbx(n)).pin_memory() for _, n in imgs]
+    hout = [torch.empty_like(h).pin_memory() for h in hin]
+    for (c, a, d) in V[:2]:
+        vfilt.filter_host(hin[0], hout[0], criterion=c, window=3, approx=a, degree=max(d, 2))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for (c, a, d, w, k) in launches:
+        vfilt.filter_host(hin[k], hout[k], criterion=c, window=w, approx=a, degree=max(d, 2))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    line["e2e"] = {"value": round(pix_per_step * world / e2e_s / 1e6, 1), "unit": "Mpixels/s",
+                   "h2d_bytes_per_step": len(launches) * H * W * 4,
+                   "d2h_bytes_per_step": len(launches) * H * W * 4,
+                   "call": "vf_filter_host (pinned host buffers, one step)"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(imgs, V, budget_s=15.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_case(args):
+    """One filter variant on a size x size RGBX image (inputs > L2 from 5800 x
+    5800 up), `launches` back-to-back launches, for ncu captures; prints the
+    CUDA-event time of the last launch."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1009_0959_gb300 import synth, vfilt
+    c, a, w = args.case.split("/")
+    d = int(a[4:]) if a.startswith("poly") else 4
+    a = "poly" if a.startswith("poly") else a
+    n = args.size
+    tile = synth.to_rgbx(synth.noisy(512, 512, 0.15, 3)[1])
+    img = torch.from_numpy(tile).cuda().repeat((n + 511) // 512, (n + 511) // 512, 1)[:n, :n]
+    img = img.contiguous()
+    out = torch.empty_like(img)
+    for _ in range(args.launches):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        vfilt.filter(img, out, criterion=c, window=int(w[1:]), approx=a, degree=d)
+        e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": args.case, "size": n, "ms": round(ms, 4),
+                      "mpix_s": round(n * n / ms / 1e3, 1)}))
+    return 0
+
+
+def _oracle_rows_sample(imgs, V, budget_s):
+    """Time the FP64 oracle over every launch of a step on a sample of rows,
+    growing the sample until about budget_s of CPU time.  Returns
+    (Mpix/s, threads, description)."""
+    from oracle import filters as F
+    threads = os.cpu_count() or 1
+    rows = threads  # one row per thread at least
+    while True:
+        t = time.perf_counter()
+        npx = 0
+        for w in WINDOWS:
+            for (c, a, d) in V:
+                cfg = F.Config(c, w, a, max(d, 2))
+                for _, noisy in imgs:
+                    r0 = (H - rows) // 2
+                    F.filter_image(noisy, cfg, threads=threads, rows=(r0, r0 + rows))
+                    npx += rows * W
+        dt = time.perf_counter() - t
+        if dt >= budget_s / 3 or rows >= 256:
+            desc = ("%d middle row(s) x 1024 px of each of the %d launches of one step "
+                    "(%.2f Mpix, %.1f s)" % (rows, len(WINDOWS) * len(V) * 3, npx / 1e6, dt))
+            return npx / dt / 1e6, threads, desc
+        rows *= 2
+
+
+def cpu_baseline(imgs, V, budget_s=15.0):
+    v, threads, desc = _oracle_rows_sample(imgs, V, budget_s)
+    return {"value": round(v, 4), "unit": "Mpixels/s", "cores": threads, "kind": "oracle",
+            "sample": desc}
+
+
+def reference_arm(args, rank, world):
+    """The FP64 oracle as the reference arm, on this arm's config and metric;
+    each step is a bounded row sample of the workload."""
+    if rank != 0:
+        return 0
+    from paper_1009_0959_gb300 import synth
+    imgs = [synth.noisy(H, W, p, seed) for p, seed in NOISE]
+    V = variants()
+    vals = []
+    for _ in range(args.warmup):
+        _oracle_rows_sample(imgs, V, budget_s=2.0)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        v, threads, desc = _oracle_rows_sample(imgs, V, budget_s=2.0)
+        vals.append(v)
+    el = time.perf_counter() - t
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixels/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / max(args.steps, 1) * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3 x 1024x1024 RGB (p=5/15/30%), VMF/BVDF/AMNFE/AMNFG/EVMF, "
+                                   "exact + minimax poly deg 2-6 + paper rationals, w=3,5"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "Mpixels/s", "cores": threads,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 4), "unit": "Mpixels/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main() or 0)

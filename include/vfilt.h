@@ -1,0 +1,154 @@
+/*
+ * vfilt.h -- C ABI of the GB300 (sm_103a) vector order-statistic filters.
+ *
+ * The library computes, for every pixel of an M x N RGB image, the output
+ * y(r,c) = F(W(r,c)) of a filter F over the w x w window W(r,c) that slides
+ * over the image in raster order (arXiv 1009.0959, Sec. 3).  F is one of
+ *   VF_VMF    vector median: argmin_i sum_j ||x_i - x_j||_2
+ *             (Sec. 3.3, first branch of Eq. equ_evf)
+ *   VF_BVDF   basic vector directional filter: argmin_i sum_j A(x_i, x_j),
+ *             A = arccos of the normalised dot product (Sec. 3.1)
+ *   VF_AMNFE  adaptive multichannel non-parametric filter, exponential
+ *             kernel exp(-||x||_1)                  (Sec. 3.2, Eq. equ_amnf)
+ *   VF_AMNFG  the same with the Gaussian kernel exp(-0.5 ||x||_2^2)
+ *   VF_EVMF   entropy vector median filter: VMF where P_C > beta_C, the
+ *             centre elsewhere                      (Sec. 3.3, Eq. equ_evf)
+ * with the elementary function of the criterion (arccos, exp, z log z)
+ * evaluated exactly (CUDA's single-precision math library) or through a
+ * minimax polynomial of degree 2..6 (Sec. 2, Tables 1-2) or the paper's (4,4)
+ * minimax rationals (Sec. 3.2 tab_exp_rat, Sec. 3.3 tab_ent_rat).
+ *
+ * Conventions shared by every call:
+ *   - Images are interleaved 8-bit, 3 (RGB) or 4 (RGBX) bytes per pixel,
+ *     rows `pitch` bytes apart.  Only the first three bytes are colour; a
+ *     fourth byte is copied from the centre pixel (AMNF) or the selected
+ *     pixel (selection filters).
+ *   - Borders replicate the nearest image pixel; the window samples are
+ *     indexed in raster order, argmin ties go to the lowest index.
+ *   - Device pointers are owned by the caller.  The library never frees or
+ *     retains caller memory after a call returns.  Input and output must not
+ *     overlap (the windows read neighbours): VF_ERR_ALIAS.
+ *   - Calls are asynchronous on the given stream (0 = legacy default stream)
+ *     and return a status; they never abort.  A CUDA launch error is
+ *     VF_ERR_CUDA and its text is kept in the context (vf_last_error).
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef VFILT_H
+#define VFILT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VF_OK = 0,
+  VF_ERR_ARG = 1,         /* null pointer, bad size, bad enum value */
+  VF_ERR_ALIAS = 2,       /* input and output ranges overlap */
+  VF_ERR_UNSUPPORTED = 3, /* valid request this build does not provide */
+  VF_ERR_CUDA = 4,        /* a CUDA call failed (text in vf_last_error) */
+  VF_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  VF_ERR_OOM = 6          /* device or host allocation failed */
+} vf_status;
+
+typedef enum { VF_VMF = 0, VF_BVDF = 1, VF_AMNFE = 2, VF_AMNFG = 3, VF_EVMF = 4 } vf_criterion;
+
+typedef enum { VF_EXACT = 0, VF_MINIMAX_POLY = 1, VF_MINIMAX_RATIONAL = 2 } vf_approx;
+
+/* Arithmetic of the pairwise terms and of the approximant evaluation.  The
+ * aggregates are always accumulated in FP32. */
+typedef enum { VF_FP32 = 0, VF_FP16X2 = 1, VF_BF16X2 = 2 } vf_precision;
+
+/* Elementary functions the minimax approximants stand in for. */
+typedef enum {
+  VF_FN_ACOS_LO = 0, /* arccos(z) on [0, 0.5]                    (Table 1, ARCCOS) */
+  VF_FN_ACOS_HI = 1, /* 2 arcsin(tau / sqrt 2) on [0, 1/sqrt 2]   (Table 1, ARCSIN) */
+  VF_FN_EXP = 2,     /* exp(-z) on [0, exp_cutoff]                (Table 2)         */
+  VF_FN_ENT = 3      /* z ln z on [ent_cutoff, 1]                 (tab_ent_rat)     */
+} vf_function;
+
+/* Filter parameters.  Fill with vf_default_params, then override. */
+typedef struct {
+  int window;             /* w: 3, 5 or 7 (n = w*w samples)                  */
+  vf_criterion criterion;
+  vf_approx approx;       /* VF_EXACT for VF_VMF (it has no elementary fn)   */
+  int degree;             /* polynomial degree 2..6 (VF_MINIMAX_POLY)        */
+  vf_precision precision;
+  float kappa;            /* AMNF kernel-width exponent; Sec. 3.2: 0.33      */
+  float exp_cutoff;       /* exp(-z) = 0 for z > exp_cutoff; Sec. 3.2: 10    */
+  float ent_cutoff;       /* z ln z = 0 for z < ent_cutoff; Sec. 3.3: 0.05 at
+                             n = 9.  A negative value selects the default
+                             0.05 * 9 / n for n > 9 (0.05 at n = 9).          */
+} vf_params;
+
+/* Optional per-call counters, accumulated (atomically) into a caller-owned
+ * DEVICE array of three unsigned long long: [0] pixels written,
+ * [1] near ties (selection filters: best and second-best aggregate of a
+ * different colour within 1e-5 relative; EVMF: also a switch decision within
+ * 1e-5 relative), [2] EVMF pixels sent to the vector median. */
+#define VF_STAT_PIXELS 0
+#define VF_STAT_NEAR_TIES 1
+#define VF_STAT_SWITCHED 2
+
+typedef struct vf_ctx vf_ctx;
+
+/* Create / destroy a context.  It holds the fitted coefficient cache, the
+ * last error text and the device scratch of the batched calls. */
+vf_status vf_create(vf_ctx** ctx);
+void vf_destroy(vf_ctx* ctx);
+
+const char* vf_status_string(vf_status s);
+const char* vf_last_error(const vf_ctx* ctx);
+
+/* window 3, VF_VMF, VF_EXACT, degree 4, FP32, kappa 0.33, exp_cutoff 10,
+ * ent_cutoff -1 (the window's default). */
+void vf_default_params(vf_params* p);
+
+/* The minimax approximant the library evaluates for `fn` (Sec. 2): for
+ * VF_MINIMAX_POLY the library's own Remez exchange fit (host, FP64) of degree
+ * `degree` on [lo, hi]; for VF_MINIMAX_RATIONAL the paper's printed (4,4)
+ * rational (VF_FN_EXP: tab_exp_rat on [0, 10]; VF_FN_ENT: tab_ent_rat on
+ * [0.05, 1]; lo and hi are ignored).  num[0..*num_len), den[0..*den_len)
+ * receive coefficients in increasing powers (den_len = 0 for a polynomial;
+ * arrays of 8 suffice), *eps the maximum error on [lo, hi] (polynomial) or
+ * on the rational's interval.  Host memory; synchronous. */
+vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int degree,
+                             double lo, double hi, double* num, int* num_len, double* den,
+                             int* den_len, double* eps);
+
+/* Filter one image (Sec. 3): d_out(r,c) = F(W(r,c)) for every pixel.
+ *   d_in, d_out   device pointers, height x width pixels of `channels`
+ *                 (3 or 4) bytes, rows in_pitch / out_pitch bytes apart
+ *                 (pitch >= width * channels)
+ *   p             filter parameters (host memory, read during the call)
+ *   stream        CUDA stream (cudaStream_t) the kernel is launched on
+ *   d_stats       optional device counters (see VF_STAT_*), or NULL; when
+ *                 given, the kernel also detects near ties (a little slower)
+ * Errors: VF_ERR_ARG (null pointers, sizes < 1, channels not 3/4, pitch too
+ * small, bad enums, degree out of 2..6), VF_ERR_ALIAS, VF_ERR_UNSUPPORTED
+ * (window not 3/5/7, a rational for BVDF, EXP rational with a cut-off other
+ * than 10, FP16X2/BF16X2 for a criterion without a packed path),
+ * VF_ERR_CUDA. */
+vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                    int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                    void* stream, unsigned long long* d_stats);
+
+/* The same filter on HOST images: copies h_in to device staging owned by the
+ * context (allocated on first use, grown when a larger image comes, freed by
+ * vf_destroy), runs vf_filter there and copies the result to h_out, all on
+ * `stream`, then waits for the stream.  Pinned host memory (cudaHostAlloc)
+ * makes the copies asynchronous DMA; pageable memory works too.  h_in and
+ * h_out may be the same buffer (the device copies are distinct).
+ * Errors: as vf_filter, plus VF_ERR_OOM when the staging cannot be
+ * allocated.  Synchronous with respect to the host. */
+vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height, int width,
+                         int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VFILT_H */

@@ -1,0 +1,284 @@
+// vf_api.cpp -- the C ABI of include/vfilt.h: argument checks, the minimax
+// coefficient cache and kernel dispatch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+
+#include "../../include/vfilt.h"
+#include "vf_internal.h"
+
+using namespace vf;
+
+namespace {
+
+// The paper's (4,4) minimax rationals (increasing powers), the library's own
+// copy: Sec. 3.2, tab_exp_rat (exp(-z) on [0, 10]) and Sec. 3.3, tab_ent_rat
+// (z ln z on [0.05, 1]).
+const double kExpRatNum[5] = {3.206619e-02, -1.195191e-02, 1.756974e-03, -1.199261e-04,
+                              3.182685e-06};
+const double kExpRatDen[5] = {3.206627e-02, 2.011147e-02, 5.853684e-03, 9.780143e-04,
+                              1.251598e-04};
+const double kExpRatEps = 2.227050e-06;
+const double kEntRatNum[5] = {-1.519742e-04, -6.835769e-02, -8.856923e-01, -5.369609e-01,
+                              1.491165};
+const double kEntRatDen[5] = {1.532270e-02, 3.987796e-01, 1.461793, 6.827004e-01,
+                              -4.469776e-02};
+const double kEntRatEps = 7.342477e-07;
+
+struct FitKey {
+  int fn, degree;
+  double lo, hi;
+  bool operator<(const FitKey& o) const {
+    return std::tie(fn, degree, lo, hi) < std::tie(o.fn, o.degree, o.lo, o.hi);
+  }
+};
+struct FitVal {
+  double coef[8];
+  double eps;
+};
+
+}  // namespace
+
+struct vf_ctx {
+  std::map<FitKey, FitVal> fits;
+  std::string last_error;
+  int tile_rows = 4;  // TY of the single-image launches
+  // device staging of vf_filter_host (grown on demand, freed by vf_destroy)
+  uint8_t* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  int stage_device = -1;
+};
+
+namespace {
+
+vf_status fail(vf_ctx* ctx, vf_status s, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return s;
+}
+
+const FitVal* get_fit(vf_ctx* ctx, int fn, int degree, double lo, double hi) {
+  FitKey k{fn, degree, lo, hi};
+  auto it = ctx->fits.find(k);
+  if (it != ctx->fits.end()) return &it->second;
+  FitVal v{};
+  if (!remez_fit(fn, degree, lo, hi, v.coef, &v.eps)) return nullptr;
+  return &(ctx->fits[k] = v);
+}
+
+float default_ent_cutoff(int n) { return n <= 9 ? 0.05f : 0.05f * 9.0f / (float)n; }
+
+bool overlap(const uint8_t* a, size_t na, const uint8_t* b, size_t nb) {
+  return a < b + nb && b < a + na;
+}
+
+}  // namespace
+
+extern "C" {
+
+vf_status vf_create(vf_ctx** ctx) {
+  if (!ctx) return VF_ERR_ARG;
+  *ctx = new (std::nothrow) vf_ctx();
+  return *ctx ? VF_OK : VF_ERR_OOM;
+}
+
+void vf_destroy(vf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->d_stage) cudaFree(ctx->d_stage);
+  delete ctx;
+}
+
+const char* vf_status_string(vf_status s) {
+  switch (s) {
+    case VF_OK: return "ok";
+    case VF_ERR_ARG: return "invalid argument";
+    case VF_ERR_ALIAS: return "input and output overlap";
+    case VF_ERR_UNSUPPORTED: return "unsupported combination";
+    case VF_ERR_CUDA: return "CUDA error";
+    case VF_ERR_TIMEOUT: return "device wait timed out";
+    case VF_ERR_OOM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+const char* vf_last_error(const vf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+void vf_default_params(vf_params* p) {
+  if (!p) return;
+  p->window = 3;
+  p->criterion = VF_VMF;
+  p->approx = VF_EXACT;
+  p->degree = 4;
+  p->precision = VF_FP32;
+  p->kappa = 0.33f;
+  p->exp_cutoff = 10.0f;
+  p->ent_cutoff = -1.0f;
+}
+
+vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int degree, double lo,
+                             double hi, double* num, int* num_len, double* den, int* den_len,
+                             double* eps) {
+  if (!ctx || !num || !num_len || !den || !den_len || !eps) return VF_ERR_ARG;
+  if (approx == VF_MINIMAX_RATIONAL) {
+    if (fn != VF_FN_EXP && fn != VF_FN_ENT)
+      return fail(ctx, VF_ERR_UNSUPPORTED, "the paper gives rationals for EXP and ENT only");
+    const double* n = fn == VF_FN_EXP ? kExpRatNum : kEntRatNum;
+    const double* d = fn == VF_FN_EXP ? kExpRatDen : kEntRatDen;
+    for (int k = 0; k < 5; ++k) num[k] = n[k], den[k] = d[k];
+    *num_len = 5;
+    *den_len = 5;
+    *eps = fn == VF_FN_EXP ? kExpRatEps : kEntRatEps;
+    return VF_OK;
+  }
+  if (approx != VF_MINIMAX_POLY) return fail(ctx, VF_ERR_ARG, "approx must be poly or rational");
+  if (degree < 2 || degree > 6) return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
+  if ((int)fn < 0 || (int)fn > 3 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
+  const FitVal* f = get_fit(ctx, (int)fn, degree, lo, hi);
+  if (!f) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
+  for (int k = 0; k <= degree; ++k) num[k] = f->coef[k];
+  *num_len = degree + 1;
+  *den_len = 0;
+  *eps = f->eps;
+  return VF_OK;
+}
+
+vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                    int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                    void* stream, unsigned long long* d_stats) {
+  if (!ctx) return VF_ERR_ARG;
+  if (!d_in || !d_out || !p) return fail(ctx, VF_ERR_ARG, "null pointer");
+  if (height < 1 || width < 1) return fail(ctx, VF_ERR_ARG, "image size must be >= 1 x 1");
+  if (channels != 3 && channels != 4) return fail(ctx, VF_ERR_ARG, "channels must be 3 or 4");
+  if (in_pitch < (size_t)width * channels || out_pitch < (size_t)width * channels)
+    return fail(ctx, VF_ERR_ARG, "pitch smaller than a row");
+  if ((int)p->criterion < 0 || (int)p->criterion > 4) return fail(ctx, VF_ERR_ARG, "bad criterion");
+  if ((int)p->approx < 0 || (int)p->approx > 2) return fail(ctx, VF_ERR_ARG, "bad approximation");
+  if ((int)p->precision < 0 || (int)p->precision > 2) return fail(ctx, VF_ERR_ARG, "bad precision");
+  if (p->window < 1 || (p->window & 1) == 0 || p->window > 15)
+    return fail(ctx, VF_ERR_ARG, "window must be odd, 1..15");
+  if (p->window != 3 && p->window != 5 && p->window != 7)
+    return fail(ctx, VF_ERR_UNSUPPORTED, "windows 3, 5 and 7 are built");
+  if (p->approx == VF_MINIMAX_POLY && (p->degree < 2 || p->degree > 6))
+    return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
+  if (!(p->kappa >= 0.0f) || !(p->exp_cutoff > 0.0f)) return fail(ctx, VF_ERR_ARG, "bad kappa/cut-off");
+  if (p->precision != VF_FP32)
+    return fail(ctx, VF_ERR_UNSUPPORTED, "packed precision is not built for this criterion");
+  const size_t in_bytes = (size_t)(height - 1) * in_pitch + (size_t)width * channels;
+  const size_t out_bytes = (size_t)(height - 1) * out_pitch + (size_t)width * channels;
+  if (overlap(d_in, in_bytes, d_out, out_bytes))
+    return fail(ctx, VF_ERR_ALIAS, "input and output overlap");
+
+  const int w = p->window, n = w * w;
+  const int crit = (int)p->criterion;
+  int apx = (int)p->approx;
+  if (crit == kVMF) apx = kExact;  // the vector median has no elementary function
+  if (apx == kRational && crit == kBVDF)
+    return fail(ctx, VF_ERR_UNSUPPORTED, "the paper gives no rational for arccos");
+
+  Launch L{};
+  L.in = d_in;
+  L.out = d_out;
+  L.height = height;
+  L.width = width;
+  L.channels = channels;
+  L.vec4_in = channels == 4 && ((uintptr_t)d_in % 4 == 0) && in_pitch % 4 == 0;
+  L.vec4_out = channels == 4 && ((uintptr_t)d_out % 4 == 0) && out_pitch % 4 == 0;
+  L.in_pitch = (long long)in_pitch;
+  L.out_pitch = (long long)out_pitch;
+  L.kappa_scale = (float)std::pow((double)n, -(double)p->kappa / 3.0);
+  L.exp_cutoff = p->exp_cutoff;
+  L.ent_cutoff = p->ent_cutoff < 0.0f ? default_ent_cutoff(n) : p->ent_cutoff;
+  L.stats = d_stats;
+
+  // coefficients of the approximant, rounded to FP32
+  if (apx != kExact) {
+    auto put = [](float* dst, const double* src, int len) {
+      for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
+    };
+    if (crit == kBVDF) {
+      const FitVal* lo = get_fit(ctx, 0, p->degree, 0.0, 0.5);
+      const FitVal* hi = get_fit(ctx, 1, p->degree, 0.0, 1.0 / std::sqrt(2.0));
+      if (!lo || !hi) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
+      put(L.c.a, lo->coef, p->degree + 1);
+      put(L.c.b, hi->coef, p->degree + 1);
+    } else if (crit == kAMNFE || crit == kAMNFG) {
+      if (apx == kRational) {
+        if (p->exp_cutoff != 10.0f)
+          return fail(ctx, VF_ERR_UNSUPPORTED, "the paper's EXP rational is fitted on [0, 10]");
+        put(L.c.a, kExpRatNum, 5);
+        put(L.c.b, kExpRatDen, 5);
+      } else {
+        const FitVal* f = get_fit(ctx, 2, p->degree, 0.0, (double)p->exp_cutoff);
+        if (!f) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
+        put(L.c.a, f->coef, p->degree + 1);
+      }
+    } else if (crit == kEVMF) {
+      if (apx == kRational) {
+        put(L.c.a, kEntRatNum, 5);
+        put(L.c.b, kEntRatDen, 5);
+      } else {
+        if (!(L.ent_cutoff > 0.0f) || L.ent_cutoff >= 1.0f)
+          return fail(ctx, VF_ERR_ARG, "the ENT polynomial needs a cut-off in (0, 1)");
+        const FitVal* f = get_fit(ctx, 3, p->degree, (double)L.ent_cutoff, 1.0);
+        if (!f) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
+        put(L.c.a, f->coef, p->degree + 1);
+      }
+    }
+  }
+
+  const int ty = ctx->tile_rows;
+  L.tiles_x = (width + kTX - 1) / kTX;
+  const int tiles_y = (height + ty - 1) / ty;
+  const long long grid = (long long)L.tiles_x * tiles_y;
+  if (grid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_filter(L, crit, w, apx, p->degree, ty, (int)grid, s);
+  if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+
+vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height, int width,
+                         int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                         void* stream) {
+  if (!ctx) return VF_ERR_ARG;
+  if (!h_in || !h_out || !p) return fail(ctx, VF_ERR_ARG, "null pointer");
+  if (height < 1 || width < 1) return fail(ctx, VF_ERR_ARG, "image size must be >= 1 x 1");
+  if (channels != 3 && channels != 4) return fail(ctx, VF_ERR_ARG, "channels must be 3 or 4");
+  const size_t row = (size_t)width * channels;
+  if (in_pitch < row || out_pitch < row) return fail(ctx, VF_ERR_ARG, "pitch smaller than a row");
+  const size_t dpitch = (row + 15) / 16 * 16;  // 16-byte rows on the device
+  const size_t need = 2 * dpitch * (size_t)height;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  if (need > ctx->stage_bytes || dev != ctx->stage_device) {
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_bytes = 0;
+    if (cudaMalloc(&ctx->d_stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, VF_ERR_OOM, "device staging allocation failed");
+    }
+    ctx->stage_bytes = need;
+    ctx->stage_device = dev;
+  }
+  uint8_t* d_in = ctx->d_stage;
+  uint8_t* d_out = ctx->d_stage + dpitch * (size_t)height;
+  cudaStream_t s = (cudaStream_t)stream;
+  e = cudaMemcpy2DAsync(d_in, dpitch, h_in, in_pitch, row, height, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  vf_status st = vf_filter(ctx, d_in, d_out, height, width, channels, dpitch, dpitch, p, stream,
+                           nullptr);
+  if (st != VF_OK) return st;
+  e = cudaMemcpy2DAsync(h_out, out_pitch, d_out, dpitch, row, height, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+}  // extern "C"

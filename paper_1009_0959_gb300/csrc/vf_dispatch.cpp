@@ -1,0 +1,28 @@
+// vf_dispatch.cpp -- criterion x window dispatch to the kernel translation units.
+#include "vf_internal.h"
+
+namespace vf {
+
+#define VF_CASE(name)                                                     \
+  switch (w) {                                                            \
+    case 3: return launch_##name##_w3(L, approx, degree, ty, grid, s);    \
+    case 5: return launch_##name##_w5(L, approx, degree, ty, grid, s);    \
+    case 7: return launch_##name##_w7(L, approx, degree, ty, grid, s);    \
+    default: return cudaErrorInvalidValue;                                \
+  }
+
+cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int degree, int ty,
+                          int grid, cudaStream_t s) {
+  switch (criterion) {
+    case kVMF: VF_CASE(vmf)
+    case kBVDF: VF_CASE(bvdf)
+    case kAMNFE: VF_CASE(amnfe)
+    case kAMNFG: VF_CASE(amnfg)
+    case kEVMF: VF_CASE(evmf)
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+#undef VF_CASE
+
+}  // namespace vf

@@ -1,0 +1,75 @@
+// vf_internal.h -- types shared by the library's translation units (not part
+// of the public ABI; include/vfilt.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vf {
+
+constexpr int kTX = 32;  // output pixels per tile row (one warp)
+
+enum { kVMF = 0, kBVDF = 1, kAMNFE = 2, kAMNFG = 3, kEVMF = 4 };
+enum { kExact = 0, kPoly = 1, kRational = 2 };
+
+// Approximant coefficients rounded to FP32, increasing powers.
+//   BVDF: a = arccos piece on [0, 0.5], b = 2 arcsin(tau/sqrt2) piece
+//   AMNF / EVMF polynomial: a; rational: a = numerator, b = denominator
+struct Coeffs {
+  float a[8];
+  float b[8];
+};
+
+// Everything a launch needs, passed by value as the kernel parameter.
+struct Launch {
+  const uint8_t* in;
+  uint8_t* out;
+  int height, width, channels;
+  int vec4_in, vec4_out;  // 32-bit pixel loads / stores allowed
+  long long in_pitch, out_pitch;
+  int tiles_x;            // tiles per tile row
+  float kappa_scale;      // n^(-kappa/3)
+  float exp_cutoff;
+  float ent_cutoff;
+  Coeffs c;
+  unsigned long long* stats;  // optional device counters
+};
+
+// Register aggregates (fully unrolled pair loop) or shared-memory aggregate
+// slots (rolled row-pair loop) for a window / criterion.
+constexpr bool uses_reg_path(int w, int crit) { return w == 3 || (w == 5 && crit != kBVDF); }
+
+// Shared memory bytes of one CTA of 32 x ty threads for window w.
+inline size_t smem_bytes(int w, int crit, int ty) {
+  size_t sw = kTX + w - 1, sh = ty + w - 1, threads = (size_t)kTX * ty;
+  size_t b = sw * sh * 20;
+  if (!uses_reg_path(w, crit)) b += (size_t)w * w * threads * 4;
+  b += threads * 4;  // EVMF list
+  return b;
+}
+
+// Per-(criterion, window) launchers, one translation unit each
+// (vf_k_<criterion>_w<w>.cu).  Return the CUDA error of the launch
+// (cudaErrorInvalidValue for a combination with no kernel).
+#define VF_DECLARE_LAUNCH(name)                                                         \
+  cudaError_t launch_##name##_w3(const Launch&, int, int, int, int, cudaStream_t);   \
+  cudaError_t launch_##name##_w5(const Launch&, int, int, int, int, cudaStream_t);   \
+  cudaError_t launch_##name##_w7(const Launch&, int, int, int, int, cudaStream_t);
+VF_DECLARE_LAUNCH(vmf)
+VF_DECLARE_LAUNCH(bvdf)
+VF_DECLARE_LAUNCH(amnfe)
+VF_DECLARE_LAUNCH(amnfg)
+VF_DECLARE_LAUNCH(evmf)
+#undef VF_DECLARE_LAUNCH
+
+// Dispatch on criterion and window (vf_dispatch.cpp).
+cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int degree, int ty,
+                          int grid, cudaStream_t s);
+
+// Host Remez exchange (FP64) of the library: minimax polynomial of degree
+// `degree` for function id (0 acos, 1 2 asin(t/sqrt2), 2 exp(-z), 3 z ln z)
+// on [lo, hi]; coefficients in increasing powers of the argument.
+bool remez_fit(int fn, int degree, double lo, double hi, double* coef, double* eps);
+
+}  // namespace vf

@@ -1,0 +1,9 @@
+// AMNF with the exponential kernel (Sec. 3.2, Eq. equ_amnf): 3 x 3 window kernels.
+#include "vf_launch.cuh"
+
+namespace vf {
+cudaError_t launch_amnfe_w3(const Launch& L, int approx, int degree, int ty, int grid,
+                          cudaStream_t s) {
+  return launch_apx<3, kAMNFE>(L, approx, degree, ty, grid, s);
+}
+}  // namespace vf

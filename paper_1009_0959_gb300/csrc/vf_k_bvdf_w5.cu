@@ -1,0 +1,9 @@
+// Basic vector directional filter (Sec. 3.1), exact and piecewise minimax arccos: 5 x 5 window kernels.
+#include "vf_launch.cuh"
+
+namespace vf {
+cudaError_t launch_bvdf_w5(const Launch& L, int approx, int degree, int ty, int grid,
+                          cudaStream_t s) {
+  return launch_apx<5, kBVDF>(L, approx, degree, ty, grid, s);
+}
+}  // namespace vf

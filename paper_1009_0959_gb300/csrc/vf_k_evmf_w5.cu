@@ -1,0 +1,9 @@
+// Entropy vector median filter (Sec. 3.3, Eq. equ_evf): 5 x 5 window kernels.
+#include "vf_launch.cuh"
+
+namespace vf {
+cudaError_t launch_evmf_w5(const Launch& L, int approx, int degree, int ty, int grid,
+                          cudaStream_t s) {
+  return launch_apx<5, kEVMF>(L, approx, degree, ty, grid, s);
+}
+}  // namespace vf

@@ -1,0 +1,534 @@
+// vf_kernels.cuh -- sm_103a kernels of the sliding-window vector filters.
+//
+// One CTA filters a tile of 32 x TY output pixels.  It stages the tile plus a
+// (w-1)/2 halo into shared memory once (coalesced 32-bit RGBX loads, borders
+// replicated), converted to FP32; every thread then owns one output pixel and
+// walks the n(n-1)/2 pairs of its window, each pairwise term computed once
+// and added to the aggregates of both samples (Sec. 3: y(r,c) = F(W(r,c))).
+//
+// Pair loop organisation: the window is processed as blocks of two rows
+// (a <= b); a block's samples are held in registers while its w*w (or
+// w(w-1)/2) pairs are formed.  For small windows (w = 3, and w = 5 with the
+// cheap distance terms) everything is unrolled and the n aggregates live in
+// registers; otherwise the row-pair loop stays rolled (keeping the code small
+// enough for the instruction cache) and each block's partial sums are added
+// to per-thread aggregate slots in shared memory.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vf_internal.h"
+
+namespace vf {
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Horner evaluation of sum_k c[k] z^k, LEN coefficients.
+template <int LEN>
+__device__ __forceinline__ float horner(const float* c, float z) {
+  float acc = c[LEN - 1];
+#pragma unroll
+  for (int k = LEN - 2; k >= 0; --k) acc = fmaf(acc, z, c[k]);
+  return acc;
+}
+
+__device__ __forceinline__ uint32_t load_px(const Launch& L, int gx, int gy) {
+  const uint8_t* p = L.in + (long long)gy * L.in_pitch + (long long)gx * L.channels;
+  if (L.vec4_in) return *reinterpret_cast<const uint32_t*>(p);
+  uint32_t v = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16);
+  if (L.channels == 4) v |= (uint32_t)p[3] << 24;
+  return v;
+}
+
+__device__ __forceinline__ void store_px(const Launch& L, int gx, int gy, uint32_t v) {
+  uint8_t* p = L.out + (long long)gy * L.out_pitch + (long long)gx * L.channels;
+  if (L.vec4_out) {
+    *reinterpret_cast<uint32_t*>(p) = v;
+    return;
+  }
+  p[0] = (uint8_t)v;
+  p[1] = (uint8_t)(v >> 8);
+  p[2] = (uint8_t)(v >> 16);
+  if (L.channels == 4) p[3] = (uint8_t)(v >> 24);
+}
+
+// ---------------------------------------------------------------- pairwise terms
+
+// Sec. 3.3 (first branch of Eq. equ_evf): Euclidean distance.  The squared
+// distance of two 8-bit colours is an exact integer in FP32.
+struct TermL2 {
+  __device__ __forceinline__ float operator()(float4 a, float4 b) const {
+    float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    return sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  }
+};
+
+// Sec. 3.2: city-block distance (exact integer in FP32).
+struct TermL1 {
+  __device__ __forceinline__ float operator()(float4 a, float4 b) const {
+    return fabsf(a.x - b.x) + fabsf(a.y - b.y) + fabsf(a.z - b.z);
+  }
+};
+
+// |a x b|^2 from exact integer components: each component is a difference of
+// two products < 2^24, exact in FP32 with one FMA.
+__device__ __forceinline__ float cross2(float4 a, float4 b) {
+  float cx = fmaf(a.y, b.z, -(a.z * b.y));
+  float cy = fmaf(a.z, b.x, -(a.x * b.z));
+  float cz = fmaf(a.x, b.y, -(a.y * b.x));
+  return fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+}
+
+// Sec. 3.1, exact angle A = arccos(a.b / (|a||b|)).  Evaluated as
+// atan2(|a x b|, a.b) from exact integer dot and cross products, which is the
+// same angle without the loss of arccos near 1.  .w holds 1/|x| (0 for the
+// zero vector); a pair with a zero vector has angle pi/2.
+struct TermAngleExact {
+  __device__ __forceinline__ float operator()(float4 a, float4 b) const {
+    float dot = fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+    float s = sqrt_approx(cross2(a, b));
+    float ang = atan2f(s, dot);
+    return (a.w * b.w == 0.0f) ? 1.57079632679f : ang;
+  }
+};
+
+// Sec. 3.1, approximate angle: z = cos; z < 0.5: the arccos approximant of
+// Table 1 (ARCCOS row); z >= 0.5: tau = sqrt(1 - z) and the approximant of
+// 2 arcsin(tau / sqrt 2) (ARCSIN row).  1 - z is formed as
+// |a x b|^2 / (|a|^2 |b|^2 (1 + z)) so that tau keeps full relative
+// precision for nearly parallel colours.
+template <int DEG>
+struct TermAngleApprox {
+  const float* lo;
+  const float* hi;
+  __device__ __forceinline__ float operator()(float4 a, float4 b) const {
+    float dot = fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+    float rr = a.w * b.w;  // 1 / (|a||b|), 0 for a zero vector
+    float z = fminf(dot * rr, 1.0f);
+    float plo = horner<DEG + 1>(lo, z);
+    float t2 = cross2(a, b) * (rr * rr) * rcp_approx(1.0f + z);
+    float phi = horner<DEG + 1>(hi, sqrt_approx(t2));
+    return z < 0.5f ? plo : phi;
+  }
+};
+
+// ---------------------------------------------------------------- window aggregates
+
+// Per-thread window view: the window of output pixel (px, py) of the tile is
+// rows py..py+W-1, columns px..px+W-1 of the staged tile (pitch sw).
+
+// w <= 5: all n aggregates in registers, fully unrolled.
+template <int W, class Term>
+__device__ __forceinline__ void aggregates_reg(const float4* tile, int sw, int px, int py,
+                                               const Term& term, float (&agg)[W * W]) {
+#pragma unroll
+  for (int i = 0; i < W * W; ++i) agg[i] = 0.0f;
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    float4 A[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) A[i] = tile[(py + a) * sw + px + i];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+      for (int j = i + 1; j < W; ++j) {
+        float t = term(A[i], A[j]);
+        agg[a * W + i] += t;
+        agg[a * W + j] += t;
+      }
+#pragma unroll
+    for (int b = a + 1; b < W; ++b) {
+      float4 B[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) B[j] = tile[(py + b) * sw + px + j];
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          float t = term(A[i], B[j]);
+          agg[a * W + i] += t;
+          agg[b * W + j] += t;
+        }
+    }
+  }
+}
+
+// Rolled row-pair loop (w = 7, and w = 5 for the costly angle term); aggregates in shared memory slots
+// sagg[i * stride] (stride = threads per CTA, so a warp's slots are
+// consecutive words).
+template <int W, class Term>
+__device__ __forceinline__ void aggregates_smem(const float4* tile, int sw, int px, int py,
+                                                const Term& term, float* sagg, int stride) {
+#pragma unroll
+  for (int i = 0; i < W * W; ++i) sagg[i * stride] = 0.0f;
+#pragma unroll 1
+  for (int a = 0; a < W; ++a) {
+    float4 A[W];
+    float ra[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      A[i] = tile[(py + a) * sw + px + i];
+      ra[i] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+      for (int j = i + 1; j < W; ++j) {
+        float t = term(A[i], A[j]);
+        ra[i] += t;
+        ra[j] += t;
+      }
+#pragma unroll 1
+    for (int b = a + 1; b < W; ++b) {
+      float4 B[W];
+      float rb[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        B[j] = tile[(py + b) * sw + px + j];
+        rb[j] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          float t = term(A[i], B[j]);
+          ra[i] += t;
+          rb[j] += t;
+        }
+#pragma unroll
+      for (int j = 0; j < W; ++j) sagg[(b * W + j) * stride] += rb[j];
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) sagg[(a * W + i) * stride] += ra[i];
+  }
+}
+
+// argmin_i agg[i], lowest index on an exact tie; optionally the near-tie test
+// against the best aggregate of a sample with a different colour.
+struct Selection {
+  int best;
+  bool near_tie;
+};
+
+template <int W, bool REG>
+__device__ __forceinline__ Selection select_min(const float* agg_reg, const float* sagg, int stride,
+                                                const float4* tile, int sw, int px, int py,
+                                                bool want_tie) {
+  constexpr int N = W * W;
+  int best = 0;
+  float bv = REG ? agg_reg[0] : sagg[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    float v = REG ? agg_reg[i] : sagg[i * stride];
+    if (v < bv) {
+      bv = v;
+      best = i;
+    }
+  }
+  Selection s{best, false};
+  if (want_tie) {
+    float4 xb = tile[(py + best / W) * sw + px + best % W];
+    float second = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float4 xi = tile[(py + i / W) * sw + px + i % W];
+      float v = REG ? agg_reg[i] : sagg[i * stride];
+      bool diff = xi.x != xb.x || xi.y != xb.y || xi.z != xb.z;
+      if (diff && v < second) second = v;
+    }
+    s.near_tie = second <= bv * (1.0f + 1e-5f);
+  }
+  return s;
+}
+
+// Selection over the window of (px, py) with pairwise term `term`; REG picks
+// register aggregates (fully unrolled) or shared-memory slots (rolled).
+template <int W, bool REG, class Term>
+__device__ __forceinline__ Selection window_select(const float4* tile, int sw, int px, int py,
+                                                   const Term& term, float* sagg, int stride,
+                                                   bool want_tie) {
+  if constexpr (REG) {
+    float agg[W * W];
+    aggregates_reg<W>(tile, sw, px, py, term, agg);
+    return select_min<W, true>(agg, nullptr, 0, tile, sw, px, py, want_tie);
+  } else {
+    aggregates_smem<W>(tile, sw, px, py, term, sagg, stride);
+    return select_min<W, false>(nullptr, sagg, stride, tile, sw, px, py, want_tie);
+  }
+}
+
+// ---------------------------------------------------------------- elementary functions
+
+// Sec. 3.2: exp(-u) with the cut-off (0 outside [0, T]).
+template <int APX, int DEG>
+__device__ __forceinline__ float expneg(const Launch& L, float u) {
+  float e;
+  if constexpr (APX == kExact) {
+    e = expf(-u);
+  } else if constexpr (APX == kPoly) {
+    e = horner<DEG + 1>(L.c.a, u);
+  } else {
+    e = horner<5>(L.c.a, u) * rcp_approx(horner<5>(L.c.b, u));
+  }
+  return (u > L.exp_cutoff) ? 0.0f : e;
+}
+
+// Sec. 3.3: z ln z with the cut-off (0 below T).
+template <int APX, int DEG>
+__device__ __forceinline__ float ent(const Launch& L, float z) {
+  float e;
+  if constexpr (APX == kExact) {
+    e = z * logf(z);
+  } else if constexpr (APX == kPoly) {
+    e = horner<DEG + 1>(L.c.a, z);
+  } else {
+    e = horner<5>(L.c.a, z) * rcp_approx(horner<5>(L.c.b, z));
+  }
+  return (z < L.ent_cutoff || z <= 0.0f) ? 0.0f : e;
+}
+
+// ---------------------------------------------------------------- the kernel
+
+struct TileSmem {
+  float4* px;     // SH x SW staged colours (FP32), .w per criterion
+  uint32_t* raw;  // SH x SW original packed pixels
+  float* agg;     // N x threads aggregate slots (w = 7)
+  int* list;      // threads: EVMF compacted pixel list
+  int sw, sh;
+};
+
+__device__ __forceinline__ TileSmem carve(int W, bool reg, int TY, int threads) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  TileSmem t;
+  t.sw = kTX + W - 1;
+  t.sh = TY + W - 1;
+  int cells = t.sw * t.sh;
+  t.px = reinterpret_cast<float4*>(smem);
+  t.raw = reinterpret_cast<uint32_t*>(smem + cells * 16);
+  unsigned char* p = smem + cells * 20;
+  t.agg = reinterpret_cast<float*>(p);
+  if (!reg) p += (size_t)W * W * threads * 4;
+  t.list = reinterpret_cast<int*>(p);
+  return t;
+}
+
+template <int CRIT>
+__device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, int x0, int y0, int R) {
+  const int cells = t.sw * t.sh;
+  for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
+    int ry = idx / t.sw, rx = idx - ry * t.sw;
+    int gy = min(max(y0 + ry - R, 0), L.height - 1);
+    int gx = min(max(x0 + rx - R, 0), L.width - 1);
+    uint32_t v = load_px(L, gx, gy);
+    float r = (float)(v & 255u), g = (float)((v >> 8) & 255u), b = (float)((v >> 16) & 255u);
+    float w = 0.0f;
+    if (CRIT == kBVDF) {
+      float n2 = fmaf(r, r, fmaf(g, g, b * b));
+      if (n2 > 0.0f) {
+        float y = rsqrtf(n2);
+        w = y * fmaf(-0.5f * n2 * y, y, 1.5f);  // one Newton step
+      }
+    }
+    t.px[idx] = make_float4(r, g, b, w);
+    t.raw[idx] = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_rgb(int r, int g, int b, uint32_t keep) {
+  return (uint32_t)r | ((uint32_t)g << 8) | ((uint32_t)b << 16) | (keep & 0xff000000u);
+}
+
+__device__ __forceinline__ int round_u8(float v) { return min(max(__float2int_rn(v), 0), 255); }
+
+__device__ __forceinline__ void block_stats(const Launch& L, int pixels, int ties, int switched) {
+  if (L.stats == nullptr) return;
+  // warp-level reduction, one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pixels += __shfl_xor_sync(0xffffffffu, pixels, o);
+    ties += __shfl_xor_sync(0xffffffffu, ties, o);
+    switched += __shfl_xor_sync(0xffffffffu, switched, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (pixels) atomicAdd(L.stats + 0, (unsigned long long)pixels);
+    if (ties) atomicAdd(L.stats + 1, (unsigned long long)ties);
+    if (switched) atomicAdd(L.stats + 2, (unsigned long long)switched);
+  }
+}
+
+// AMNF (Sec. 3.2, Eq. equ_amnf) of the window of (px, py).
+template <int W, bool REG, int CRIT, int APX, int DEG>
+__device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& t, int px, int py,
+                                               int stride, bool& tie) {
+  constexpr int N = W * W, C = N / 2;
+  TermL1 term;
+  float aggr[N];
+  float* sagg = t.agg + threadIdx.x;
+  if constexpr (REG) {
+    aggregates_reg<W>(t.px, t.sw, px, py, term, aggr);
+  } else {
+    aggregates_smem<W>(t.px, t.sw, px, py, term, sagg, stride);
+  }
+  const float4 xc = t.px[(py + W / 2) * t.sw + px + W / 2];
+  const uint32_t rawc = t.raw[(py + W / 2) * t.sw + px + W / 2];
+  float aggC = REG ? aggr[C] : sagg[C * stride];
+  if (aggC == 0.0f) {  // constant window: every h_i is 0, output the centre
+    tie = false;
+    return rawc;
+  }
+  float wsum = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
+    float ai = REG ? aggr[i] : sagg[i * stride];
+    float rh = rcp_approx(L.kappa_scale * ai);  // 1 / h_i
+    float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
+    float u;
+    if constexpr (CRIT == kAMNFE) {
+      u = (fabsf(dx) + fabsf(dy) + fabsf(dz)) * rh;  // ||(x_C - x_i) / h_i||_1
+    } else {
+      u = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (rh * rh);  // 0.5 ||.||_2^2
+    }
+    float wi = (rh * rh * rh) * expneg<APX, DEG>(L, u);
+    wsum += wi;
+    ax = fmaf(wi, xi.x, ax);
+    ay = fmaf(wi, xi.y, ay);
+    az = fmaf(wi, xi.z, az);
+  }
+  float rw = 1.0f / wsum;
+  float yx = ax * rw, yy = ay * rw, yz = az * rw;
+  if (L.stats) {
+    auto g = [](float v) { return fabsf(v - floorf(v) - 0.5f); };
+    tie = fminf(g(yx), fminf(g(yy), g(yz))) < 1e-3f;
+  }
+  return pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
+}
+
+// EVMF switch (Sec. 3.3, Eq. equ_evf) of the window of (px, py).
+template <int W, int APX, int DEG>
+__device__ __forceinline__ bool evmf_switch(const Launch& L, const TileSmem& t, int px, int py,
+                                            bool& tie) {
+  constexpr int N = W * W, C = N / 2;
+  float mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
+    mx += xi.x;
+    my += xi.y;
+    mz += xi.z;
+  }
+  // correctly rounded division: exact whenever the mean is an integer, so a
+  // centre equal to the mean gives P_C = 0 exactly (no switch), as in exact
+  // arithmetic; a reciprocal multiply would leave a spurious P_C > 0 = beta_C
+  mx = mx / (float)N;
+  my = my / (float)N;
+  mz = mz / (float)N;
+  float r[N];
+  float rsum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
+    float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
+    r[i] = sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    rsum += r[i];
+  }
+  tie = false;
+  if (rsum == 0.0f) return false;  // constant window: identity
+  const float rs = 1.0f / rsum;
+  float esum = 0.0f, eC = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float e = ent<APX, DEG>(L, r[i] * rs);
+    esum += e;
+    if (i == C) eC = e;
+  }
+  if (esum == 0.0f) return false;  // nothing left after the cut-off: identity
+  const float PC = r[C] * rs;
+  const float beta = eC / esum;
+  if (L.stats) tie = fabsf(PC - beta) <= 1e-5f * fmaxf(fabsf(PC), fabsf(beta));
+  return PC > beta;
+}
+
+template <int W, int CRIT, int APX, int DEG>
+__global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Launch L) {
+  constexpr int R = W / 2;
+  constexpr bool REG = uses_reg_path(W, CRIT);
+  const int TY = blockDim.x / kTX;
+  const TileSmem t = carve(W, REG, TY, blockDim.x);
+  const int tile = blockIdx.x;
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  const int x0 = txi * kTX, y0 = tyi * TY;
+
+  stage_tile<CRIT>(L, t, x0, y0, R);
+  __syncthreads();
+
+  const int px = threadIdx.x % kTX, py = threadIdx.x / kTX;
+  const int gx = x0 + px, gy = y0 + py;
+  const bool valid = gx < L.width && gy < L.height;
+  const int stride = blockDim.x;
+  float* sagg = t.agg + threadIdx.x;
+  const bool want_tie = L.stats != nullptr;
+  int ties = 0, switched = 0;
+
+  if constexpr (CRIT == kVMF || CRIT == kBVDF) {
+    Selection s;
+    if constexpr (CRIT == kVMF) {
+      s = window_select<W, REG>(t.px, t.sw, px, py, TermL2{}, sagg, stride, want_tie);
+    } else if constexpr (APX == kExact) {
+      s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleExact{}, sagg, stride, want_tie);
+    } else {
+      s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleApprox<DEG>{L.c.a, L.c.b}, sagg, stride,
+                           want_tie);
+    }
+    if (valid) {
+      store_px(L, gx, gy, t.raw[(py + s.best / W) * t.sw + px + s.best % W]);
+      ties = s.near_tie;
+    }
+  } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+    bool tie = false;
+    uint32_t v = amnf_pixel<W, REG, CRIT, APX, DEG>(L, t, px, py, stride, tie);
+    if (valid) {
+      store_px(L, gx, gy, v);
+      ties = tie;
+    }
+  } else {  // kEVMF: switch, then the vector median on the compacted list
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    bool tie = false;
+    bool sw = valid && evmf_switch<W, APX, DEG>(L, t, px, py, tie);
+    if (valid && !sw) store_px(L, gx, gy, t.raw[(py + R) * t.sw + px + R]);
+    if (sw) t.list[atomicAdd(&s_count, 1)] = threadIdx.x;
+    ties = valid && tie;
+    switched = sw;
+    __syncthreads();
+    const int count = s_count;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+      const int id = t.list[k];
+      const int qx = id % kTX, qy = id / kTX;
+      Selection s = window_select<W, REG>(t.px, t.sw, qx, qy, TermL2{}, sagg, stride, want_tie);
+      store_px(L, x0 + qx, y0 + qy, t.raw[(qy + s.best / W) * t.sw + qx + s.best % W]);
+      ties += s.near_tie;
+    }
+  }
+  block_stats(L, valid ? 1 : 0, ties, switched);
+}
+
+}  // namespace vf

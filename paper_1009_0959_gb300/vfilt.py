@@ -1,0 +1,190 @@
+"""Python binding of the C ABI in include/vfilt.h (argument marshalling only).
+
+Every filter step runs in the CUDA library libvfilt.so; this module only
+turns torch tensors into pointers, sizes and the current CUDA stream.  There
+is no fallback: if the library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvfilt.so")
+
+CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4}
+APPROX = {"exact": 0, "poly": 1, "rational": 2}
+PRECISION = {"fp32": 0, "fp16x2": 1, "bf16x2": 2}
+FUNCTIONS = {"acos_lo": 0, "acos_hi": 1, "exp": 2, "ent": 3}
+STATUS = {0: "VF_OK", 1: "VF_ERR_ARG", 2: "VF_ERR_ALIAS", 3: "VF_ERR_UNSUPPORTED",
+          4: "VF_ERR_CUDA", 5: "VF_ERR_TIMEOUT", 6: "VF_ERR_OOM"}
+
+STAT_PIXELS, STAT_NEAR_TIES, STAT_SWITCHED = 0, 1, 2
+
+
+class VFError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Params(ctypes.Structure):
+    """vf_params."""
+    _fields_ = [("window", ctypes.c_int), ("criterion", ctypes.c_int),
+                ("approx", ctypes.c_int), ("degree", ctypes.c_int),
+                ("precision", ctypes.c_int), ("kappa", ctypes.c_float),
+                ("exp_cutoff", ctypes.c_float), ("ent_cutoff", ctypes.c_float)]
+
+
+_lock = threading.Lock()
+_lib = None
+_tls = threading.local()
+
+
+def lib():
+    """The loaded libvfilt.so (raises if it is missing: no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libvfilt.so is not built (%s); run "
+                                   "paper_1009_0959_gb300.build.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            L.vf_create.argtypes = [ctypes.POINTER(P)]
+            L.vf_create.restype = I
+            L.vf_destroy.argtypes = [P]
+            L.vf_destroy.restype = None
+            L.vf_status_string.argtypes = [I]
+            L.vf_status_string.restype = ctypes.c_char_p
+            L.vf_last_error.argtypes = [P]
+            L.vf_last_error.restype = ctypes.c_char_p
+            L.vf_default_params.argtypes = [ctypes.POINTER(Params)]
+            L.vf_default_params.restype = None
+            L.vf_get_approximant.argtypes = [P, I, I, I, ctypes.c_double, ctypes.c_double, P,
+                                             ctypes.POINTER(I), P, ctypes.POINTER(I),
+                                             ctypes.POINTER(ctypes.c_double)]
+            L.vf_get_approximant.restype = I
+            L.vf_filter.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P, P]
+            L.vf_filter.restype = I
+            L.vf_filter_host.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P]
+            L.vf_filter_host.restype = I
+            _lib = L
+        return _lib
+
+
+def context():
+    """A per-thread library context (vf_ctx)."""
+    ctx = getattr(_tls, "ctx", None)
+    if ctx is None:
+        ctx = ctypes.c_void_p()
+        st = lib().vf_create(ctypes.byref(ctx))
+        if st != 0:
+            raise VFError(st, "vf_create failed")
+        _tls.ctx = ctx
+    return ctx
+
+
+def _check(st: int, ctx):
+    if st != 0:
+        raise VFError(st, lib().vf_last_error(ctx).decode())
+
+
+def make_params(window=3, criterion="vmf", approx="exact", degree=4, precision="fp32",
+                kappa=0.33, exp_cutoff=10.0, ent_cutoff=-1.0) -> Params:
+    p = Params()
+    lib().vf_default_params(ctypes.byref(p))
+    p.window = int(window)
+    p.criterion = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
+    p.approx = APPROX[approx] if isinstance(approx, str) else int(approx)
+    p.degree = int(degree)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.kappa, p.exp_cutoff, p.ent_cutoff = float(kappa), float(exp_cutoff), float(ent_cutoff)
+    return p
+
+
+def _image_args(t):
+    if t.dim() != 3 or t.shape[2] not in (3, 4):
+        raise ValueError("expected an H x W x C (C = 3 or 4) uint8 tensor")
+    if str(t.dtype) != "torch.uint8" or not t.is_cuda:
+        raise ValueError("expected a CUDA uint8 tensor")
+    if t.stride(2) != 1 or t.stride(1) != t.shape[2]:
+        raise ValueError("pixels must be interleaved and rows dense (pitch = stride(0))")
+    return t.data_ptr(), int(t.shape[0]), int(t.shape[1]), int(t.shape[2]), int(t.stride(0))
+
+
+def filter(inp, out=None, *, stream=None, stats=None, **params):
+    """d_out = F(W(d_in)) for an H x W x C uint8 CUDA tensor (vf_filter).
+
+    params: window, criterion, approx, degree, precision, kappa, exp_cutoff,
+    ent_cutoff.  `stream` is a torch.cuda.Stream (default: the current one);
+    `stats` an optional int64 CUDA tensor of 3 counters accumulated in place.
+    """
+    import torch
+    if out is None:
+        out = torch.empty_like(inp)
+    ip, h, w, c, ipitch = _image_args(inp)
+    op, h2, w2, c2, opitch = _image_args(out)
+    if (h, w, c) != (h2, w2, c2):
+        raise ValueError("input and output shapes differ")
+    p = make_params(**params)
+    s = stream if stream is not None else torch.cuda.current_stream(inp.device)
+    sp = None
+    if stats is not None:
+        if stats.dtype != torch.int64 or not stats.is_cuda or stats.numel() < 3:
+            raise ValueError("stats must be a CUDA int64 tensor of 3 counters")
+        sp = stats.data_ptr()
+    ctx = context()
+    _check(lib().vf_filter(ctx, ip, op, h, w, c, ipitch, opitch, ctypes.byref(p),
+                           ctypes.c_void_p(s.cuda_stream), sp), ctx)
+    return out
+
+
+def filter_host(inp, out=None, *, stream=None, **params):
+    """vf_filter_host on H x W x C uint8 CPU tensors (pinned or pageable):
+    the copies to and from the device and the filter all run in the library.
+    Returns `out` when the call has completed."""
+    import torch
+    if inp.is_cuda or inp.dim() != 3 or inp.dtype != torch.uint8:
+        raise ValueError("expected an H x W x C uint8 CPU tensor")
+    if out is None:
+        out = torch.empty_like(inp)
+    if inp.stride(2) != 1 or inp.stride(1) != inp.shape[2] or out.stride(1) != out.shape[2]:
+        raise ValueError("pixels must be interleaved and rows dense")
+    p = make_params(**params)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ctx = context()
+    _check(lib().vf_filter_host(ctx, inp.data_ptr(), out.data_ptr(), int(inp.shape[0]),
+                                int(inp.shape[1]), int(inp.shape[2]), int(inp.stride(0)),
+                                int(out.stride(0)), ctypes.byref(p),
+                                ctypes.c_void_p(s.cuda_stream)), ctx)
+    return out
+
+
+def filter_ptr(d_in: int, d_out: int, height: int, width: int, channels: int, in_pitch: int,
+               out_pitch: int, stream_handle: int = 0, stats_ptr=None, **params):
+    """vf_filter on raw device pointers (for tests of the ABI itself)."""
+    p = make_params(**params)
+    ctx = context()
+    return lib().vf_filter(ctx, d_in, d_out, height, width, channels, in_pitch, out_pitch,
+                           ctypes.byref(p), ctypes.c_void_p(stream_handle), stats_ptr)
+
+
+def get_approximant(fn: str, approx: str = "poly", degree: int = 4, lo: float = 0.0,
+                    hi: float = 1.0):
+    """(num, den, eps) of the approximant the library evaluates (host)."""
+    num = (ctypes.c_double * 8)()
+    den = (ctypes.c_double * 8)()
+    nl, dl = ctypes.c_int(), ctypes.c_int()
+    eps = ctypes.c_double()
+    ctx = context()
+    _check(lib().vf_get_approximant(ctx, FUNCTIONS[fn], APPROX[approx], int(degree), float(lo),
+                                    float(hi), num, ctypes.byref(nl), den, ctypes.byref(dl),
+                                    ctypes.byref(eps)), ctx)
+    return list(num[: nl.value]), list(den[: dl.value]), eps.value
+
+
+def status_string(code: int) -> str:
+    return lib().vf_status_string(int(code)).decode()

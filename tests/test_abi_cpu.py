@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every entry point its header
+declares; argument checks that need no GPU.  CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(vf_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def vf():
+    from paper_1009_0959_gb300 import build
+    build.build()
+    from paper_1009_0959_gb300 import vfilt
+    return vfilt
+
+
+def test_exports_every_declared_symbol(vf):
+    L = vf.lib()
+    declared = _declared()
+    assert len(declared) >= 7
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_status_strings(vf):
+    assert vf.status_string(0) == "ok"
+    assert "overlap" in vf.status_string(2)
+
+
+def test_argument_errors_without_gpu(vf):
+    """Rejected before any CUDA call: null pointers, bad sizes and enums,
+    overlapping ranges, unsupported windows."""
+    buf = (ctypes.c_uint8 * 4096)()
+    base = ctypes.addressof(buf)
+    assert vf.filter_ptr(0, base, 4, 4, 4, 16, 16) == 1                  # null input
+    assert vf.filter_ptr(base, base + 2048, 0, 4, 4, 16, 16) == 1        # height 0
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 5, 20, 20) == 1        # channels 5
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 8, 16) == 1         # pitch too small
+    assert vf.filter_ptr(base, base + 8, 4, 4, 4, 16, 16) == 2           # overlap
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 16, 16, window=9) == 3
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 16, 16, window=4) == 1
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 16, 16, criterion=7) == 1
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 16, 16, criterion="bvdf",
+                         approx="rational") == 3
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 16, 16, criterion="bvdf", approx="poly",
+                         degree=9) == 1
+    assert vf.filter_ptr(base, base + 2048, 4, 4, 4, 16, 16, criterion="amnfe",
+                         approx="rational", exp_cutoff=2.0) == 3
+
+
+def test_library_remez_matches_paper_table1(vf, golden):
+    """The library's own fit (independent of the oracle's) reproduces the
+    paper's Table 1 and Table 2 to the printed precision."""
+    import numpy as np
+    for key, fn in [("table1_arcsin", "acos_hi"), ("table1_arccos", "acos_lo")]:
+        g = golden[key]
+        num, den, eps = vf.get_approximant(fn, "poly", 4, *g["interval"])
+        assert den == []
+        assert eps == pytest.approx(g["eps"], rel=1e-4)
+        np.testing.assert_allclose(num, g["coef"], rtol=2e-5, atol=2e-10)
+    for d, row in golden["table2_exp"]["rows"].items():
+        num, _, eps = vf.get_approximant("exp", "poly", int(d), 0.0, 10.0)
+        assert eps == pytest.approx(row["eps"], rel=1e-4)
+        np.testing.assert_allclose(num, row["coef"], rtol=1e-5)
+
+
+def test_library_rationals_are_the_papers(vf, golden):
+    for key, fn in [("exp_rational", "exp"), ("ent_rational", "ent")]:
+        num, den, eps = vf.get_approximant(fn, "rational")
+        assert num == golden[key]["num"] and den == golden[key]["den"]
+        assert eps == golden[key]["eps"]

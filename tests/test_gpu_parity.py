@@ -1,0 +1,193 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Selection filters (VMF, BVDF, EVMF): the selected colour must equal the
+oracle's wherever the oracle's best aggregate is more than 1e-5 (relative)
+below the best aggregate of a different colour (and, for EVMF, where P_C and
+beta_C differ by more than 1e-5 relative).  The FP32 aggregates carry a
+relative error of a few 1e-7 (n - 1 terms, each within a few ulp), far inside
+that gap.  AMNF: the rounded output must be equal wherever the oracle's
+unrounded output is more than 1e-3 from a rounding boundary: the weighted
+mean's FP32 error is below 255 x (a few ulp) ~ 1e-4; within the band it may
+differ by one level.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import filters as F  # noqa: E402
+from paper_1009_0959_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SEL_GAP = 1e-5
+AMNF_GAP = 1e-3
+
+
+@pytest.fixture(scope="module")
+def vf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_0959_gb300 import build, vfilt
+    build.build()
+    return vfilt
+
+
+def run_gpu(vf, img, channels=4, **kw):
+    src = synth.to_rgbx(img) if channels == 4 else np.ascontiguousarray(img[..., :3])
+    t = torch.from_numpy(src).cuda()
+    out = vf.filter(t, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check(crit, oracle_out, diag, gpu_out):
+    o, g = oracle_out[..., :3].astype(int), gpu_out[..., :3].astype(int)
+    diff = np.any(o != g, axis=-1)
+    if crit in ("amnfe", "amnfg"):
+        safe = diag["gap"] > AMNF_GAP
+        assert np.abs(o - g).max() <= 1
+    else:
+        safe = diag["gap"] > SEL_GAP
+    bad = diff & safe
+    assert bad.sum() == 0, "%d mismatches outside the near-tie band (%d near ties)" % (
+        bad.sum(), (~safe).sum())
+    return int((~safe).sum())
+
+
+CASES = [("vmf", "exact", 0), ("bvdf", "exact", 0), ("bvdf", "poly", 2), ("bvdf", "poly", 4),
+         ("bvdf", "poly", 6), ("amnfe", "exact", 0), ("amnfe", "poly", 2), ("amnfe", "poly", 4),
+         ("amnfe", "poly", 6), ("amnfe", "rational", 4), ("amnfg", "exact", 0),
+         ("amnfg", "poly", 4), ("amnfg", "rational", 4), ("evmf", "exact", 0),
+         ("evmf", "poly", 3), ("evmf", "poly", 5), ("evmf", "rational", 4)]
+
+
+@pytest.mark.parametrize("w", [3, 5, 7])
+@pytest.mark.parametrize("crit,approx,deg", CASES)
+def test_parity_small(vf, crit, approx, deg, w):
+    """37 x 67 image: several 32 x 4 tiles plus a ragged column and row."""
+    clean, noisy = synth.noisy(37, 67, 0.2, 100 + w)
+    kw = dict(criterion=crit, window=w, approx=approx, degree=max(deg, 2))
+    out_o, d = F.filter_image(noisy, F.Config(crit, w, approx, max(deg, 2)))
+    out_g = run_gpu(vf, noisy, **kw)
+    check(crit, out_o, d, out_g)
+    # the fourth byte is carried through from the centre / selected pixel (0 here)
+    assert (out_g[..., 3] == 0).all()
+
+
+@pytest.mark.parametrize("crit,approx", [("vmf", "exact"), ("bvdf", "poly"), ("amnfe", "rational"),
+                                         ("evmf", "exact")])
+def test_parity_rgb_odd_pitch(vf, crit, approx):
+    """3-byte pixels with a row pitch of 3 W + 1 bytes (unaligned rows)."""
+    clean, noisy = synth.noisy(21, 45, 0.25, 7)
+    H, W = noisy.shape[:2]
+    buf = torch.zeros((H, W * 3 + 1), dtype=torch.uint8, device="cuda")
+    inp = buf.as_strided((H, W, 3), (W * 3 + 1, 3, 1))
+    inp.copy_(torch.from_numpy(noisy).cuda())
+    obuf = torch.zeros_like(buf)
+    out = obuf.as_strided((H, W, 3), (W * 3 + 1, 3, 1))
+    vf.filter(inp, out, criterion=crit, window=5, approx=approx, degree=4)
+    torch.cuda.synchronize()
+    out_o, d = F.filter_image(noisy, F.Config(crit, 5, approx, 4))
+    check(crit, out_o, d, out.cpu().numpy())
+    # the pad byte after each row is untouched
+    assert (obuf[:, -1] == 0).all()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (2, 3), (5, 70), (3, 33)])
+@pytest.mark.parametrize("w", [3, 7])
+@pytest.mark.parametrize("crit", ["vmf", "bvdf", "amnfg", "evmf"])
+def test_edge_shapes(vf, shape, w, crit):
+    """Images smaller than the window and than a tile (replicated borders)."""
+    clean, noisy = synth.noisy(shape[0], shape[1], 0.3, 9)
+    out_o, d = F.filter_image(noisy, F.Config(crit, w))
+    check(crit, out_o, d, run_gpu(vf, noisy, criterion=crit, window=w))
+
+
+def test_degenerate_colours(vf):
+    """Black pixels (zero vectors: cosine 0 by convention), constant and
+    two-colour regions, saturated values."""
+    img = np.zeros((24, 40, 3), np.uint8)
+    img[:, 20:] = 255
+    img[::5, ::7] = (255, 0, 0)
+    img[10:14, 5:9] = 0
+    img[3, 3] = (0, 0, 1)
+    for crit, approx in [("vmf", "exact"), ("bvdf", "exact"), ("bvdf", "poly"),
+                         ("amnfe", "exact"), ("amnfg", "poly"), ("evmf", "rational")]:
+        for w in (3, 5):
+            out_o, d = F.filter_image(img, F.Config(crit, w, approx, 4))
+            check(crit, out_o, d, run_gpu(vf, img, criterion=crit, window=w, approx=approx))
+
+
+@pytest.mark.parametrize("crit,approx,deg", [("vmf", "exact", 0), ("bvdf", "exact", 0),
+                                             ("bvdf", "poly", 4), ("amnfe", "rational", 4),
+                                             ("amnfg", "poly", 5), ("evmf", "exact", 0),
+                                             ("evmf", "poly", 4)])
+@pytest.mark.parametrize("w", [3, 5])
+def test_parity_full_size_sampled(vf, crit, approx, deg, w):
+    """1024 x 1024 at 15 % impulses, launched as the benchmark launches it;
+    the oracle checks a sample of rows (top and bottom borders, the middle)."""
+    clean, noisy = synth.noisy(1024, 1024, 0.15, 3)
+    out_g = run_gpu(vf, noisy, criterion=crit, window=w, approx=approx, degree=max(deg, 2))
+    cfg = F.Config(crit, w, approx, max(deg, 2))
+    for r0, r1 in [(0, 3), (510, 514), (1021, 1024)]:
+        out_o, d = F.filter_image(noisy, cfg, rows=(r0, r1))
+        sl = slice(r0, r1)
+        check(crit, out_o[sl], {k: v[sl] for k, v in d.items()}, out_g[sl])
+
+
+def test_stats_counters(vf):
+    clean, noisy = synth.noisy(64, 96, 0.15, 21)
+    st = torch.zeros(3, dtype=torch.int64, device="cuda")
+    run = synth.to_rgbx(noisy)
+    t = torch.from_numpy(run).cuda()
+    vf.filter(t, criterion="evmf", window=3, stats=st)
+    torch.cuda.synchronize()
+    pixels, ties, switched = st.tolist()
+    assert pixels == 64 * 96
+    _, d = F.filter_image(noisy, F.Config("evmf", 3))
+    ref = int(d["sw"].sum())
+    band = int((d["gap"] <= SEL_GAP).sum())
+    assert abs(switched - ref) <= band
+    assert ties >= 0
+
+
+def test_minimax_quality_bar(vf):
+    """Against the FP64 oracle's exact filter on the 256 x 256, 10 % case:
+    the degree-4 arccos (Table 1) changes at most 0.5 % of the selections and
+    costs at most 0.05 dB of PSNR; the paper's rationals likewise."""
+    from oracle import metrics as M
+    clean, noisy = synth.noisy(256, 256, 0.10, 1)
+    for crit, approx, deg in [("bvdf", "poly", 4), ("amnfe", "rational", 4),
+                              ("evmf", "rational", 4)]:
+        ex, _ = F.filter_image(noisy, F.Config(crit, 3), threads=4)
+        g = run_gpu(vf, noisy, criterion=crit, window=3, approx=approx, degree=deg)[..., :3]
+        assert M.changed_fraction(ex, g) <= 0.005
+        assert M.psnr(clean, ex) - M.psnr(clean, g) <= 0.05
+
+
+def test_evmf_centre_equals_mean(vf):
+    """Six samples (98,100,100), two (106,100,100) and the centre
+    (100,100,100): the mean equals the centre, P_C = 0 = beta_C, so the
+    identity branch is taken, although the vector median would pick
+    (98,100,100).  A rounded mean would make P_C > 0 and switch."""
+    img = np.zeros((3, 3, 3), np.uint8)
+    img[...] = (98, 100, 100)
+    img[1, 1] = (100, 100, 100)
+    img[0, 2] = img[2, 0] = (106, 100, 100)
+    big = np.zeros((5, 5, 3), np.uint8)
+    big[...] = (100, 100, 100)
+    big[1:4, 1:4] = img
+    out_o, d = F.filter_image(big, F.Config("evmf", 3))
+    assert d["sw"][2, 2] == 0 and tuple(out_o[2, 2]) == (100, 100, 100)
+    vmf, _ = F.filter_image(big, F.Config("vmf", 3))
+    assert tuple(vmf[2, 2]) == (98, 100, 100)
+    g = run_gpu(vf, big, criterion="evmf", window=3)
+    assert tuple(g[2, 2, :3]) == (100, 100, 100)
+
+
+def test_alias_rejected(vf):
+    t = torch.zeros((16, 16, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(vf.VFError) as e:
+        vf.filter(t, t)
+    assert e.value.name == "VF_ERR_ALIAS"
