@@ -101,6 +101,9 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline model
 
+MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 5): 18290}
+
+
 # FP32-pipe instructions per pair / per sample of each kernel, counted from the
 # kernel source (vf_kernels.cuh); MUFU (SFU) operations separately.  FFMA,
 # FADD, FMUL, FMNMX, FSETP/FSEL each count as one.
@@ -111,7 +114,10 @@ def ops_per_pixel(crit, approx, deg, w):
         return P * 8 + n, P          # 3 sub, mul + 2 fma, 2 agg adds; argmin
     if crit == "bvdf":
         if approx == "exact":
-            return None, None        # atan2f: library sequence, not counted
+            # atan2f is a library sequence with data-dependent branches: its
+            # count is measured, thread instructions (predicated on) per pixel
+            # from an ncu capture of the 6144 x 6144 case
+            return MEASURED_INST_PER_PIXEL.get((crit, approx, w)), None
         # dot 3, rr 1, z 2, cross 9, t2 3, 1+z 1, two Horner chains 2 deg,
         # select 2, 2 agg adds; rcp + sqrt on MUFU
         return P * (23 + 2 * deg) + n, 2 * P
