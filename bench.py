@@ -136,6 +136,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--case", default=None,
                     help="profiling: run one kernel, e.g. bvdf/poly4/w5, on a --size image")
     ap.add_argument("--size", type=int, default=6144)
@@ -323,12 +324,70 @@ def main():
                    "d2h_bytes_per_step": len(launches) * H * W * 4,
                    "call": "vf_filter_host (pinned host buffers, one step)"}
 
+    if not args.no_batch:
+        line["batched"] = bench_batch()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs, V, budget_s=15.0)
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+BATCH_CRITS = ["vmf", "bvdf", "amnfe", "amnfg", "evmf"]
+BATCH_MINIMAX = {"vmf": ("exact", 4), "bvdf": ("poly", 4), "amnfe": ("rational", 4),
+                 "amnfg": ("poly", 3), "evmf": ("poly", 5)}
+
+
+def bench_batch(reps=5):
+    """Batched form: 256 seeded images of uneven sizes (320x240 .. 1920x1080),
+    windows 3/5/7 and the five criteria round-robin, exact and minimax in
+    alternate groups of 15; one persistent launch replayed as a CUDA graph after
+    the autotuner picked its tile shape; compared with one vf_filter launch per
+    image on the same buffers."""
+    import torch
+
+    from paper_1009_0959_gb300 import synth, vfilt
+    items = synth.batch_images(256, 9)
+    dev = []
+    for i, (clean, noisy, p) in enumerate(items):
+        crit = BATCH_CRITS[i % 5]
+        approx, deg = ("exact", 4) if (i // 15) % 2 == 0 else BATCH_MINIMAX[crit]
+        params = dict(criterion=crit, window=(3, 5, 7)[i % 3], approx=approx, degree=deg)
+        t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+        dev.append((t, torch.empty_like(t), params))
+    mpix = sum(t.shape[0] * t.shape[1] for t, _, _ in dev) / 1e6
+    b = vfilt.Batch(dev)
+    tune = b.autotune()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    graph_ms = timed(lambda: b.graph_launch(stream))
+    launch_ms = timed(lambda: b.launch(stream))
+
+    def per_image():
+        for inp, out, params in dev:
+            vfilt.filter(inp, out, stream=stream, **params)
+    single_ms = timed(per_image)
+    b.close()
+    return {"workload": "256 images 320x240..1920x1080 (seed 9), w 3/5/7 and the five criteria "
+                        "round-robin, exact / minimax in alternate groups of 15",
+            "mpix": round(mpix, 2), "graph_ms": round(graph_ms, 3),
+            "mpix_s": round(mpix / graph_ms * 1e3, 1), "launch_ms": round(launch_ms, 3),
+            "per_image_launches_ms": round(single_ms, 3),
+            "speedup_vs_per_image": round(single_ms / graph_ms, 3), "autotune": tune,
+            "gpu_launches_per_run": 1}
 
 
 def run_case(args):

@@ -147,6 +147,56 @@ vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int h
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
                          void* stream);
 
+/* ---- batched form: many images in one persistent launch ------------------ */
+
+/* One image of a batch: device buffers (caller-owned, as in vf_filter) and its
+ * own filter parameters (window, criterion, approximation, degree...). */
+typedef struct {
+  const uint8_t* d_in;
+  uint8_t* d_out;
+  int height, width, channels;
+  size_t in_pitch, out_pitch;
+  vf_params params;
+} vf_image_desc;
+
+typedef struct vf_batch vf_batch;
+
+/* Validate `count` descriptors (each as vf_filter would; the first failure is
+ * returned) and build the work queue: all 32 x TY output tiles of all images,
+ * images ordered by decreasing cost per tile, with their approximant
+ * coefficients, copied to device memory that the batch owns (freed by
+ * vf_batch_destroy).  Synchronous.  The batch keeps the device pointers: the
+ * images must stay allocated while the batch is launched.
+ * Errors: those of vf_filter, VF_ERR_ARG for count < 1, VF_ERR_OOM. */
+vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf_batch** batch);
+
+/* Filter every image of the batch with ONE persistent kernel on `stream`:
+ * SMs x CTAs-per-SM CTAs pull tiles from a device counter (reset by a memset
+ * on the same stream) until the queue is empty.  Asynchronous; may be captured
+ * into a CUDA graph by the caller.  Launches of one batch on different streams
+ * must not overlap (they share the counter). */
+vf_status vf_batch_launch(vf_batch* b, void* stream);
+
+/* The same launch as a CUDA graph (memset node + kernel node), instantiated
+ * on the first call (and after vf_batch_autotune / vf_batch_configure) and
+ * replayed with cudaGraphLaunch on `stream`. */
+vf_status vf_batch_graph_launch(vf_batch* b, void* stream);
+
+/* Autotuner: times every tile shape (32 x TY outputs, TY = 2, 4, 8) with every
+ * resident CTA count (1 .. occupancy maximum) on the batch itself (one warm-up
+ * and three timed launches each, CUDA events on `stream`), keeps the fastest
+ * and reports it (any out pointer may be NULL).  Synchronous; writes the
+ * outputs (the same values each time). */
+vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas_per_sm,
+                            float* best_ms);
+
+/* Set the configuration by hand: tile_rows 2, 4 or 8; ctas_per_sm 0 (the
+ * occupancy maximum) up to that maximum.  Synchronous; not while a launch of
+ * the batch is in flight. */
+vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm);
+
+void vf_batch_destroy(vf_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -146,9 +146,13 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
   return VF_OK;
 }
 
-vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
-                    int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
-                    void* stream, unsigned long long* d_stats) {
+}  // extern "C"
+
+namespace vf {
+
+vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                         int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                         unsigned long long* d_stats, Launch* out, LaunchClass* cls) {
   if (!ctx) return VF_ERR_ARG;
   if (!d_in || !d_out || !p) return fail(ctx, VF_ERR_ARG, "null pointer");
   if (height < 1 || width < 1) return fail(ctx, VF_ERR_ARG, "image size must be >= 1 x 1");
@@ -194,7 +198,7 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
   L.ent_cutoff = p->ent_cutoff < 0.0f ? default_ent_cutoff(n) : p->ent_cutoff;
   L.stats = d_stats;
 
-  // coefficients of the approximant, rounded to FP32
+  // coefficients of the approximant, rounded to FP32, zero above the degree
   if (apx != kExact) {
     auto put = [](float* dst, const double* src, int len) {
       for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
@@ -229,18 +233,38 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
       }
     }
   }
+  *out = L;
+  cls->crit = crit;
+  cls->w = w;
+  cls->apx = apx;
+  cls->deg = apx == kPoly ? p->degree : (apx == kRational ? 4 : 0);
+  return VF_OK;
+}
 
+vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg) { return fail(ctx, s, msg); }
+
+}  // namespace vf
+
+extern "C" {
+
+vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                    int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                    void* stream, unsigned long long* d_stats) {
+  Launch L;
+  LaunchClass cls;
+  vf_status st = prepare_launch(ctx, d_in, d_out, height, width, channels, in_pitch, out_pitch, p,
+                                d_stats, &L, &cls);
+  if (st != VF_OK) return st;
   const int ty = ctx->tile_rows;
   L.tiles_x = (width + kTX - 1) / kTX;
   const int tiles_y = (height + ty - 1) / ty;
   const long long grid = (long long)L.tiles_x * tiles_y;
   if (grid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_filter(L, crit, w, apx, p->degree, ty, (int)grid, s);
+  cudaError_t e = launch_filter(L, cls.crit, cls.w, cls.apx, cls.deg, ty, (int)grid, s);
   if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
   return VF_OK;
 }
-
 
 vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height, int width,
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,

@@ -1,0 +1,358 @@
+// vf_batch.cu -- many images of uneven sizes, mixed windows and criteria in
+// one persistent launch (and as a CUDA graph), with an autotuner for the tile
+// shape and the number of resident CTAs.
+//
+// The host flattens the batch into one queue of 32 x TY output tiles, images
+// ordered by decreasing estimated cost per tile (longest-processing-time
+// first, so the tail of the queue holds the cheap tiles).  A grid of
+// (SMs x CTAs per SM) CTAs pulls tile indices from a global counter with one
+// atomicAdd per tile; no CTA ever waits on another.  A tile is mapped to its
+// image by binary search over the images' first tile indices, then run by the
+// same per-tile body as the single-image kernel (vf_kernels.cuh), selected by
+// the image's class (window x criterion x approximation).  Polynomials run
+// as degree 6 with zero-padded coefficients (fma(0, z, c) = c exactly, so the
+// result is bit-identical to the degree-specific kernel).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vf_kernels.cuh"
+
+namespace vf {
+
+// Kernel classes: window (3, 5, 7) x 12 criterion/approximation pairs.
+constexpr int kClassesPerWindow = 12;
+__host__ __device__ constexpr int class_of(int w, int crit, int apx) {
+  int k = 0;
+  switch (crit) {
+    case kVMF: k = 0; break;
+    case kBVDF: k = 1 + (apx != kExact); break;
+    case kAMNFE: k = 3 + apx; break;
+    case kAMNFG: k = 6 + apx; break;
+    default: k = 9 + apx; break;
+  }
+  return (w == 3 ? 0 : (w == 5 ? 1 : 2)) * kClassesPerWindow + k;
+}
+
+struct BatchImage {
+  Launch L;
+  int cls;
+};
+
+// Inside the batch kernel only 3 x 3 keeps its aggregates in registers: the
+// kernel's register budget is that of its largest body, and the 5 x 5
+// register bodies would force spills into every other class.
+constexpr bool batch_reg(int w) { return w == 3; }
+
+template <int W>
+__device__ __forceinline__ void run_class(int k, const Launch& L, int tile) {
+  constexpr bool RG = batch_reg(W);
+  switch (k) {
+    case 0: process_tile<W, kVMF, kExact, 0, RG>(L, tile); break;
+    case 1: process_tile<W, kBVDF, kExact, 0, RG>(L, tile); break;
+    case 2: process_tile<W, kBVDF, kPoly, 6, RG>(L, tile); break;
+    case 3: process_tile<W, kAMNFE, kExact, 0, RG>(L, tile); break;
+    case 4: process_tile<W, kAMNFE, kPoly, 6, RG>(L, tile); break;
+    case 5: process_tile<W, kAMNFE, kRational, 4, RG>(L, tile); break;
+    case 6: process_tile<W, kAMNFG, kExact, 0, RG>(L, tile); break;
+    case 7: process_tile<W, kAMNFG, kPoly, 6, RG>(L, tile); break;
+    case 8: process_tile<W, kAMNFG, kRational, 4, RG>(L, tile); break;
+    case 9: process_tile<W, kEVMF, kExact, 0, RG>(L, tile); break;
+    case 10: process_tile<W, kEVMF, kPoly, 6, RG>(L, tile); break;
+    default: process_tile<W, kEVMF, kRational, 4, RG>(L, tile); break;
+  }
+}
+
+// begin[i] = first tile of image i in the queue, begin[count] = total tiles.
+__global__ void __launch_bounds__(256, 2) batch_kernel(const BatchImage* __restrict__ imgs,
+                                                       const int* __restrict__ begin, int count,
+                                                       unsigned int* counter) {
+  __shared__ int s_item;
+  __shared__ BatchImage s_img;  // the current tile's image descriptor
+  const int total = begin[count];
+  for (;;) {
+    __syncthreads();  // the previous tile is done with shared memory and s_item
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) return;
+    int lo = 0, hi = count - 1;  // largest i with begin[i] <= item
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (begin[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int tile = item - begin[lo];
+    // stage the descriptor once per tile (word copy by the first warp)
+    static_assert(sizeof(BatchImage) % 4 == 0, "descriptor is copied as words");
+    if (threadIdx.x < 32) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(imgs + lo);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_img);
+      for (int k = threadIdx.x; k < (int)(sizeof(BatchImage) / 4); k += 32) dst[k] = src[k];
+    }
+    __syncthreads();
+    const Launch& L = s_img.L;
+    const int cls = s_img.cls;
+    const int wi = cls / kClassesPerWindow, k = cls - wi * kClassesPerWindow;
+    if (wi == 0) run_class<3>(k, L, tile);
+    else if (wi == 1) run_class<5>(k, L, tile);
+    else run_class<7>(k, L, tile);
+  }
+}
+
+// Relative cost of one output pixel per class (pairs x term cost), used only
+// to order the queue.
+static double pixel_cost(const LaunchClass& c) {
+  const double n = (double)c.w * c.w, pairs = n * (n - 1) / 2;
+  double term = 1.0;
+  switch (c.crit) {
+    case kVMF: term = 1.0; break;
+    case kBVDF: term = c.apx == kExact ? 7.0 : 3.5; break;
+    case kAMNFE:
+    case kAMNFG: term = 1.0; break;
+    default: term = 0.5; break;
+  }
+  return pairs * term;
+}
+
+}  // namespace vf
+
+using namespace vf;
+
+struct vf_batch {
+  vf_ctx* ctx = nullptr;
+  int device = 0, sms = 0;
+  std::vector<BatchImage> host;  // queue order
+  std::vector<double> cost;
+  BatchImage* d_imgs = nullptr;
+  int* d_begin = nullptr;
+  unsigned int* d_counter = nullptr;
+  int count = 0;
+  int ty = 4, ctas_per_sm = 0;  // 0: occupancy maximum
+  size_t smem = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+size_t batch_smem(const vf_batch* b, int ty) {
+  size_t m = 0;
+  for (const BatchImage& im : b->host) {
+    int wi = im.cls / kClassesPerWindow, k = im.cls % kClassesPerWindow;
+    int w = 3 + 2 * wi;
+    int crit = k == 0 ? kVMF : (k <= 2 ? kBVDF : (k <= 5 ? kAMNFE : (k <= 8 ? kAMNFG : kEVMF)));
+    m = std::max(m, smem_bytes(w, crit, ty, batch_reg(w)));
+  }
+  return m;
+}
+
+// Tile counts for TY = ty; uploads descriptors and the prefix array.
+vf_status upload(vf_batch* b, int ty) {
+  std::vector<int> begin(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) {
+    Launch& L = b->host[i].L;
+    L.tiles_x = (L.width + kTX - 1) / kTX;
+    long long tiles = (long long)L.tiles_x * ((L.height + ty - 1) / ty);
+    long long next = (long long)begin[i] + tiles;
+    if (next > 0x7fffffffLL) return set_error(b->ctx, VF_ERR_UNSUPPORTED, "batch too large");
+    begin[i + 1] = (int)next;
+  }
+  cudaError_t e = cudaMemcpy(b->d_imgs, b->host.data(), sizeof(BatchImage) * b->count,
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_begin, begin.data(), sizeof(int) * (b->count + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  b->ty = ty;
+  b->smem = batch_smem(b, ty);
+  return VF_OK;
+}
+
+vf_status drop_graph(vf_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  return VF_OK;
+}
+
+int resident_ctas(const vf_batch* b, int ty) {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel, kTX * ty,
+                                                    batch_smem(b, ty)) != cudaSuccess)
+    return 1;
+  return std::max(blocks, 1);
+}
+
+vf_status enqueue(vf_batch* b, cudaStream_t s) {
+  const int threads = kTX * b->ty;
+  int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : resident_ctas(b, b->ty);
+  const int grid = b->sms * per_sm;
+  if (b->smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)b->smem);
+    if (e != cudaSuccess) return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  batch_kernel<<<grid, threads, b->smem, s>>>(b->d_imgs, b->d_begin, b->count, b->d_counter);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf_batch** out) {
+  if (!ctx) return VF_ERR_ARG;
+  if (!descs || !out || count < 1) return set_error(ctx, VF_ERR_ARG, "empty batch");
+  *out = nullptr;
+  vf_batch* b = new (std::nothrow) vf_batch();
+  if (!b) return VF_ERR_OOM;
+  b->ctx = ctx;
+  b->count = count;
+  std::vector<std::pair<double, int>> order;
+  std::vector<BatchImage> imgs(count);
+  for (int i = 0; i < count; ++i) {
+    const vf_image_desc& d = descs[i];
+    LaunchClass c;
+    vf_status st = prepare_launch(ctx, d.d_in, d.d_out, d.height, d.width, d.channels,
+                                  d.in_pitch, d.out_pitch, &d.params, nullptr, &imgs[i].L, &c);
+    if (st != VF_OK) {
+      delete b;
+      return st;
+    }
+    imgs[i].cls = class_of(c.w, c.crit, c.apx);
+    order.push_back({-pixel_cost(c), i});
+  }
+  std::stable_sort(order.begin(), order.end());
+  for (auto& o : order) b->host.push_back(imgs[o.second]);
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_imgs, sizeof(BatchImage) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_begin, sizeof(int) * (count + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    vf_batch_destroy(b);
+    cudaGetLastError();
+    return set_error(ctx, e == cudaErrorMemoryAllocation ? VF_ERR_OOM : VF_ERR_CUDA,
+                     cudaGetErrorString(e));
+  }
+  vf_status st = upload(b, 4);
+  if (st != VF_OK) {
+    vf_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return VF_OK;
+}
+
+vf_status vf_batch_launch(vf_batch* b, void* stream) {
+  if (!b) return VF_ERR_ARG;
+  return enqueue(b, (cudaStream_t)stream);
+}
+
+vf_status vf_batch_graph_launch(vf_batch* b, void* stream) {
+  if (!b) return VF_ERR_ARG;
+  cudaError_t e = cudaSuccess;
+  if (!b->exec) {
+    if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    vf_status st = enqueue(b, b->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st != VF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e == cudaSuccess) {
+      b->graph = g;
+      e = cudaGraphInstantiate(&b->exec, g, 0);
+    }
+    if (e != cudaSuccess) {
+      drop_graph(b);
+      return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas_per_sm,
+                            float* best_ms) {
+  if (!b) return VF_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_error(b->ctx, VF_ERR_CUDA, "event creation failed");
+  }
+  float best = 1e30f;
+  int best_ty = b->ty, best_ctas = b->ctas_per_sm;
+  vf_status st = VF_OK;
+  const int tys[3] = {2, 4, 8};
+  for (int ti = 0; ti < 3 && st == VF_OK; ++ti) {
+    st = upload(b, tys[ti]);
+    if (st != VF_OK) break;
+    const int maxc = resident_ctas(b, tys[ti]);
+    for (int c = 1; c <= maxc && st == VF_OK; ++c) {
+      b->ctas_per_sm = c;
+      st = enqueue(b, s);  // warm-up
+      float ms_min = 1e30f;
+      for (int r = 0; r < 3 && st == VF_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = enqueue(b, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = set_error(b->ctx, VF_ERR_CUDA, "sync");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (st == VF_OK && ms_min < best) {
+        best = ms_min;
+        best_ty = tys[ti];
+        best_ctas = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != VF_OK) return st;
+  st = upload(b, best_ty);
+  b->ctas_per_sm = best_ctas;
+  drop_graph(b);
+  if (tile_rows) *tile_rows = best_ty;
+  if (ctas_per_sm) *ctas_per_sm = best_ctas;
+  if (best_ms) *best_ms = best;
+  return st;
+}
+
+vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm) {
+  if (!b) return VF_ERR_ARG;
+  if (tile_rows != 2 && tile_rows != 4 && tile_rows != 8)
+    return set_error(b->ctx, VF_ERR_ARG, "tile_rows must be 2, 4 or 8");
+  if (ctas_per_sm < 0 || ctas_per_sm > resident_ctas(b, tile_rows))
+    return set_error(b->ctx, VF_ERR_ARG, "more CTAs per SM than can be resident");
+  vf_status st = upload(b, tile_rows);
+  b->ctas_per_sm = ctas_per_sm;
+  drop_graph(b);
+  return st;
+}
+
+void vf_batch_destroy(vf_batch* b) {
+  if (!b) return;
+  drop_graph(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->d_imgs) cudaFree(b->d_imgs);
+  if (b->d_begin) cudaFree(b->d_begin);
+  if (b->d_counter) cudaFree(b->d_counter);
+  delete b;
+}
+
+}  // extern "C"

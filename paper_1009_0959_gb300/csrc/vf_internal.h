@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/vfilt.h"
+
 namespace vf {
 
 constexpr int kTX = 32;  // output pixels per tile row (one warp)
@@ -40,14 +42,16 @@ struct Launch {
 // slots (rolled row-pair loop) for a window / criterion.
 constexpr bool uses_reg_path(int w, int crit) { return w == 3 || (w == 5 && crit != kBVDF); }
 
-// Shared memory bytes of one CTA of 32 x ty threads for window w.
-inline size_t smem_bytes(int w, int crit, int ty) {
+// Shared memory bytes of one CTA of 32 x ty threads for window w (reg: the
+// aggregates live in registers, no shared-memory slots).
+inline size_t smem_bytes(int w, int crit, int ty, bool reg) {
   size_t sw = kTX + w - 1, sh = ty + w - 1, threads = (size_t)kTX * ty;
   size_t b = sw * sh * 20;
-  if (!uses_reg_path(w, crit)) b += (size_t)w * w * threads * 4;
+  if (!reg) b += (size_t)w * w * threads * 4;
   b += threads * 4;  // EVMF list
   return b;
 }
+inline size_t smem_bytes(int w, int crit, int ty) { return smem_bytes(w, crit, ty, uses_reg_path(w, crit)); }
 
 // Per-(criterion, window) launchers, one translation unit each
 // (vf_k_<criterion>_w<w>.cu).  Return the CUDA error of the launch
@@ -66,6 +70,20 @@ VF_DECLARE_LAUNCH(evmf)
 // Dispatch on criterion and window (vf_dispatch.cpp).
 cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int degree, int ty,
                           int grid, cudaStream_t s);
+
+// The kernel class of a request: criterion, window, approximation, degree.
+struct LaunchClass {
+  int crit, w, apx, deg;
+};
+
+// Argument checks, coefficients and the Launch block of one image (shared by
+// vf_filter and the batched calls).  d_stats may be null.
+vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                         int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
+                         unsigned long long* d_stats, Launch* out, LaunchClass* cls);
+
+// Record an error text in the context and return s.
+vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg);
 
 // Host Remez exchange (FP64) of the library: minimax polynomial of degree
 // `degree` for function id (0 acos, 1 2 asin(t/sqrt2), 2 exp(-z), 3 z ln z)

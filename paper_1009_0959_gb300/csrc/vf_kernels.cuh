@@ -116,8 +116,15 @@ struct TermAngleExact {
 // precision for nearly parallel colours.
 template <int DEG>
 struct TermAngleApprox {
-  const float* lo;
-  const float* hi;
+  float lo[DEG + 1];  // coefficients held in registers for the pair loop
+  float hi[DEG + 1];
+  __device__ __forceinline__ TermAngleApprox(const float* l, const float* h) {
+#pragma unroll
+    for (int k = 0; k <= DEG; ++k) {
+      lo[k] = l[k];
+      hi[k] = h[k];
+    }
+  }
   __device__ __forceinline__ float operator()(float4 a, float4 b) const {
     float dot = fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
     float rr = a.w * b.w;  // 1 / (|a||b|), 0 for a zero vector
@@ -421,18 +428,24 @@ __device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& 
   return pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
 }
 
-// EVMF switch (Sec. 3.3, Eq. equ_evf) of the window of (px, py).
+// EVMF switch (Sec. 3.3, Eq. equ_evf) of the window of (px, py).  The sample
+// loops run row by row; for w = 7 the row loop stays rolled so that the 49
+// staged samples are not all held in registers across the passes.
 template <int W, int APX, int DEG>
 __device__ __forceinline__ bool evmf_switch(const Launch& L, const TileSmem& t, int px, int py,
                                             bool& tie) {
   constexpr int N = W * W, C = N / 2;
+  constexpr int ROW_UNROLL = W <= 5 ? W : 1;
   float mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll ROW_UNROLL
+  for (int a = 0; a < W; ++a) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
-    mx += xi.x;
-    my += xi.y;
-    mz += xi.z;
+    for (int i = 0; i < W; ++i) {
+      float4 xi = t.px[(py + a) * t.sw + px + i];
+      mx += xi.x;
+      my += xi.y;
+      mz += xi.z;
+    }
   }
   // correctly rounded division: exact whenever the mean is an integer, so a
   // centre equal to the mean gives P_C = 0 exactly (no switch), as in exact
@@ -440,39 +453,45 @@ __device__ __forceinline__ bool evmf_switch(const Launch& L, const TileSmem& t, 
   mx = mx / (float)N;
   my = my / (float)N;
   mz = mz / (float)N;
-  float r[N];
+  // pass 2: r_i = ||x_i - xbar||_2 and their sum; pass 3 recomputes r_i (one
+  // sqrt per sample) rather than holding n of them in registers
   float rsum = 0.0f;
+#pragma unroll ROW_UNROLL
+  for (int a = 0; a < W; ++a) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
-    float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
-    r[i] = sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    rsum += r[i];
+    for (int i = 0; i < W; ++i) {
+      float4 xi = t.px[(py + a) * t.sw + px + i];
+      float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
+      rsum += sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
   }
   tie = false;
   if (rsum == 0.0f) return false;  // constant window: identity
   const float rs = 1.0f / rsum;
-  float esum = 0.0f, eC = 0.0f;
+  float esum = 0.0f;
+#pragma unroll ROW_UNROLL
+  for (int a = 0; a < W; ++a) {
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float e = ent<APX, DEG>(L, r[i] * rs);
-    esum += e;
-    if (i == C) eC = e;
+    for (int i = 0; i < W; ++i) {
+      float4 xi = t.px[(py + a) * t.sw + px + i];
+      float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
+      esum += ent<APX, DEG>(L, sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * rs);
+    }
   }
   if (esum == 0.0f) return false;  // nothing left after the cut-off: identity
-  const float PC = r[C] * rs;
-  const float beta = eC / esum;
+  const float4 xc = t.px[(py + C / W) * t.sw + px + C % W];
+  const float dx = xc.x - mx, dy = xc.y - my, dz = xc.z - mz;
+  const float PC = sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * rs;
+  const float beta = ent<APX, DEG>(L, PC) / esum;
   if (L.stats) tie = fabsf(PC - beta) <= 1e-5f * fmaxf(fabsf(PC), fabsf(beta));
   return PC > beta;
 }
 
-template <int W, int CRIT, int APX, int DEG>
-__global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Launch L) {
+template <int W, int CRIT, int APX, int DEG, bool REG = uses_reg_path(W, CRIT)>
+__device__ __forceinline__ void process_tile(const Launch& L, int tile) {
   constexpr int R = W / 2;
-  constexpr bool REG = uses_reg_path(W, CRIT);
   const int TY = blockDim.x / kTX;
   const TileSmem t = carve(W, REG, TY, blockDim.x);
-  const int tile = blockIdx.x;
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kTX, y0 = tyi * TY;
 
@@ -494,7 +513,7 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Lau
     } else if constexpr (APX == kExact) {
       s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleExact{}, sagg, stride, want_tie);
     } else {
-      s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleApprox<DEG>{L.c.a, L.c.b}, sagg, stride,
+      s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleApprox<DEG>(L.c.a, L.c.b), sagg, stride,
                            want_tie);
     }
     if (valid) {
@@ -529,6 +548,12 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Lau
     }
   }
   block_stats(L, valid ? 1 : 0, ties, switched);
+}
+
+// One CTA per tile of one image.
+template <int W, int CRIT, int APX, int DEG>
+__global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Launch L) {
+  process_tile<W, CRIT, APX, DEG>(L, blockIdx.x);
 }
 
 }  // namespace vf

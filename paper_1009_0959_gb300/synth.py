@@ -119,11 +119,13 @@ def piecewise_smooth(h: int, w: int, seed: int, *, x0: int = 0, canvas_w: int | 
 
 def impulse_uncorrelated(img: np.ndarray, p: float, seed: int) -> np.ndarray:
     """Eq. eq_noise, uncorrelated model: each channel k is replaced by a random
-    value r_k (uniform on 0..255) with probability phi_k = p."""
+    value r_k (uniform on 0..255) with probability phi_k = p.  One 64-bit draw
+    per channel: the top 53 bits decide the replacement, the low 8 bits are
+    the value."""
     h, w, _ = img.shape
-    idx = np.arange(h * w * 3, dtype=np.uint64)
-    hit = rand_uniform(seed, _S_NOISE_SEL, idx).reshape(h, w, 3) < p
-    val = rand_int(seed, _S_NOISE_VAL, idx, 0, 255).reshape(h, w, 3).astype(np.uint8)
+    u = rand_u64(seed, _S_NOISE_SEL, np.arange(h * w * 3, dtype=np.uint64))
+    hit = ((u >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 < p).reshape(h, w, 3)
+    val = (u & np.uint64(255)).astype(np.uint8).reshape(h, w, 3)
     out = img[..., :3].copy()
     out[hit] = val[hit]
     return out
@@ -192,6 +194,34 @@ def batch_sizes(count: int, seed: int, lo=(240, 320), hi=(1080, 1920)):
     hs = rand_int(seed, _S_SIZES, np.arange(count), lo[0], hi[0])
     ws = rand_int(seed, _S_SIZES, np.arange(count, 2 * count), lo[1], hi[1])
     return [(int(a), int(b)) for a, b in zip(hs, ws)]
+
+
+def batch_images(count: int, seed: int, lo=(240, 320), hi=(1080, 1920), p_lo: float = 0.05,
+                 p_hi: float = 0.30, scenes: int = 4):
+    """`count` (clean, noisy, p) triples of uneven sizes (batch_sizes), each cut
+    at a seeded offset out of one of `scenes` hi-sized scenes, with
+    uncorrelated impulses at a seeded rate in [p_lo, p_hi]."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    sizes = batch_sizes(count, seed, lo, hi)
+    r = rand_uniform(seed, _S_SCENE, np.arange(1000, 1000 + 4 * count)).reshape(count, 4)
+    # numpy releases the GIL on large arrays: images are independent, so make
+    # them in parallel (the result does not depend on the order)
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        canvas = list(ex.map(lambda c: piecewise_smooth(hi[0], hi[1], seed * 1000 + c),
+                             range(scenes)))
+
+        def one(i):
+            h, w = sizes[i]
+            k = int(r[i, 0] * scenes)
+            y0 = int(r[i, 1] * (hi[0] - h + 1))
+            x0 = int(r[i, 2] * (hi[1] - w + 1))
+            clean = np.ascontiguousarray(canvas[k][y0:y0 + h, x0:x0 + w])
+            p = p_lo + (p_hi - p_lo) * float(r[i, 3])
+            return clean, impulse_uncorrelated(clean, p, seed * 100003 + i), p
+
+        return list(ex.map(one, range(count)))
 
 
 def video_frame(h: int, w: int, frame: int, frames: int, seed: int, pan: int = 4,

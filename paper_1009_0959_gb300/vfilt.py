@@ -38,6 +38,14 @@ class Params(ctypes.Structure):
                 ("exp_cutoff", ctypes.c_float), ("ent_cutoff", ctypes.c_float)]
 
 
+class ImageDesc(ctypes.Structure):
+    """vf_image_desc."""
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p),
+                ("height", ctypes.c_int), ("width", ctypes.c_int), ("channels", ctypes.c_int),
+                ("in_pitch", ctypes.c_size_t), ("out_pitch", ctypes.c_size_t),
+                ("params", Params)]
+
+
 _lock = threading.Lock()
 _lib = None
 _tls = threading.local()
@@ -71,6 +79,19 @@ def lib():
             L.vf_filter.restype = I
             L.vf_filter_host.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P]
             L.vf_filter_host.restype = I
+            L.vf_batch_create.argtypes = [P, P, I, ctypes.POINTER(P)]
+            L.vf_batch_create.restype = I
+            L.vf_batch_launch.argtypes = [P, P]
+            L.vf_batch_launch.restype = I
+            L.vf_batch_graph_launch.argtypes = [P, P]
+            L.vf_batch_graph_launch.restype = I
+            L.vf_batch_autotune.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                            ctypes.POINTER(ctypes.c_float)]
+            L.vf_batch_autotune.restype = I
+            L.vf_batch_configure.argtypes = [P, I, I]
+            L.vf_batch_configure.restype = I
+            L.vf_batch_destroy.argtypes = [P]
+            L.vf_batch_destroy.restype = None
             _lib = L
         return _lib
 
@@ -161,6 +182,63 @@ def filter_host(inp, out=None, *, stream=None, **params):
                                 int(out.stride(0)), ctypes.byref(p),
                                 ctypes.c_void_p(s.cuda_stream)), ctx)
     return out
+
+
+class Batch:
+    """vf_batch: many (input, output, params) images in one persistent launch.
+
+    images: list of (inp, out, params_dict) with H x W x C uint8 CUDA tensors.
+    The tensors must stay alive as long as the batch is used."""
+
+    def __init__(self, images):
+        descs = (ImageDesc * len(images))()
+        self._keep = []
+        for i, (inp, out, params) in enumerate(images):
+            ip, h, w, c, ipitch = _image_args(inp)
+            op, h2, w2, c2, opitch = _image_args(out)
+            if (h, w, c) != (h2, w2, c2):
+                raise ValueError("input and output shapes differ")
+            d = descs[i]
+            d.d_in, d.d_out, d.height, d.width, d.channels = ip, op, h, w, c
+            d.in_pitch, d.out_pitch = ipitch, opitch
+            d.params = make_params(**params)
+            self._keep += [inp, out]
+        self.ctx = context()
+        self.handle = ctypes.c_void_p()
+        _check(lib().vf_batch_create(self.ctx, descs, len(images), ctypes.byref(self.handle)),
+               self.ctx)
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def launch(self, stream=None):
+        _check(lib().vf_batch_launch(self.handle, self._stream(stream)), self.ctx)
+
+    def graph_launch(self, stream=None):
+        _check(lib().vf_batch_graph_launch(self.handle, self._stream(stream)), self.ctx)
+
+    def autotune(self, stream=None):
+        ty, ctas, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(lib().vf_batch_autotune(self.handle, self._stream(stream), ctypes.byref(ty),
+                                       ctypes.byref(ctas), ctypes.byref(ms)), self.ctx)
+        return {"tile_rows": ty.value, "ctas_per_sm": ctas.value, "ms": ms.value}
+
+    def configure(self, tile_rows=4, ctas_per_sm=0):
+        _check(lib().vf_batch_configure(self.handle, int(tile_rows), int(ctas_per_sm)), self.ctx)
+
+    def close(self):
+        if self.handle:
+            lib().vf_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def filter_ptr(d_in: int, d_out: int, height: int, width: int, channels: int, in_pitch: int,
