@@ -102,6 +102,8 @@ class Clocks:
 # ---------------------------------------------------------------- roofline model
 
 MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 5): 18290}
+# DRAM bytes (read + write) per output pixel from the same ncu capture
+MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 5): 7.29}
 
 
 # FP32-pipe instructions per pair / per sample of each kernel, counted from the
@@ -286,6 +288,11 @@ def main():
             "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (recipe unit counts and max "
                            "clock)" % sm_max,
             "traffic": None}
+    dram = MEASURED_DRAM_BYTES_PER_PIXEL.get((c, a, int(wtag[1:])))
+    if dram is not None:
+        roof["traffic"] = round(dram * H * W)
+        roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled "
+                                "from a 6144 x 6144 capture by pixels; algorithmic 8 B/px")
     if fp32 is not None:
         ach = fp32 * H * W / (kern_ms[dom] / 1e3) / 1e12
         roof.update({"achieved": round(ach, 3), "frac": round(ach / peak_tinst, 4),
