@@ -197,6 +197,39 @@ vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm);
 
 void vf_batch_destroy(vf_batch* b);
 
+/* ---- allocation-free batched call ------------------------------------------
+ * No counterpart in the paper.  For callers that must not allocate GPU memory
+ * while they filter: for example a real-time video pipeline, or a plug-in in a
+ * host application that reserves all device memory up front, where cudaMalloc
+ * on the frame path is forbidden because it can stall the whole device and its
+ * latency has no bound.  vf_batch_run_static filters up to
+ * VF_STATIC_MAX_IMAGES images exactly as vf_batch_create + vf_batch_launch
+ * would (same kernel, 32 x 4 tiles, the occupancy maximum of resident CTAs)
+ * but keeps its scratch (tile counter, tile table, image descriptors) in one
+ * fixed device array inside the library (about 40 KB) instead of memory it
+ * allocates.  Every GPU that loads the library holds that array until the
+ * process exits.  The caller still passes the input and output images.
+ *   - The first call on a device looks the array's address up on that device
+ *     (with the device current); make that first call before any stream
+ *     capture.
+ *   - Calls share the one array and it keeps the last call's contents: each
+ *     call resets the counter itself, but calls whose work overlaps on the GPU
+ *     (different streams, no ordering between them) race and corrupt each
+ *     other.  Calls on one stream are ordered and safe.
+ *   - Nothing is fitted here: a polynomial approximant must already be in the
+ *     context's cache (any earlier vf_filter, vf_batch_create or
+ *     vf_get_approximant call in the same context with the same criterion,
+ *     degree and cut-offs puts it there); otherwise VF_ERR_UNSUPPORTED.
+ *   - No error text is recorded in the context (that could allocate).
+ *   - The H2D copies of the descriptors come from the library's own static
+ *     host buffer; the host side of the calls is serialised by a mutex.
+ * Errors: VF_ERR_ARG (null pointers, count < 1, bad sizes or enums),
+ * VF_ERR_UNSUPPORTED (count > VF_STATIC_MAX_IMAGES, a window other than
+ * 3/5/7, an approximant not yet fitted), VF_ERR_ALIAS, VF_ERR_CUDA.
+ * Asynchronous on `stream` apart from the pageable descriptor copies. */
+#define VF_STATIC_MAX_IMAGES 256
+vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -243,6 +243,16 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
 
 vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg) { return fail(ctx, s, msg); }
 
+const double* cached_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi) {
+  auto it = ctx->fits.find(FitKey{fn, degree, lo, hi});
+  return it == ctx->fits.end() ? nullptr : it->second.coef;
+}
+
+void paper_rational(int fn, const double** num, const double** den) {
+  *num = fn == 2 ? kExpRatNum : kEntRatNum;
+  *den = fn == 2 ? kExpRatDen : kEntRatDen;
+}
+
 }  // namespace vf
 
 extern "C" {

@@ -356,3 +356,183 @@ void vf_batch_destroy(vf_batch* b) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched call.  The paper has no counterpart: this serves
+// callers that cannot allocate device memory while they filter.  Its scratch
+// (the tile counter, the tile prefix array and the image descriptors) lives in
+// one file-scope device array of fixed size instead of memory from cudaMalloc;
+// everything else is the batch kernel above, in its default configuration
+// (32 x 4 tiles, the occupancy maximum of resident CTAs).
+#include <mutex>
+
+namespace {
+
+constexpr int kStaticMax = VF_STATIC_MAX_IMAGES;
+constexpr int kStaticDevices = 64;
+
+struct StaticLayout {
+  unsigned int counter[64];       // [0]: the tile counter (256 bytes keep what follows aligned)
+  int begin[kStaticMax + 64];     // first tile of every queued image, then the total
+  BatchImage imgs[kStaticMax];    // descriptors in queue order
+};
+
+// The scratch itself.  Host code must not pass &g_static_scratch to a kernel:
+// on the host the name is a stand-in, not a device address.  The address comes
+// from cudaGetSymbolAddress, once per device (static_scratch below).
+static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticLayout)];
+
+std::mutex g_static_mutex;        // serialises the host side of the calls
+StaticLayout g_static_host;       // host staging of begin[] and imgs[]
+int g_static_order[kStaticMax];
+double g_static_cost[kStaticMax];
+void* g_static_dev[kStaticDevices] = {};
+
+// Device address of the scratch on the current device (set up on first use).
+vf_status static_scratch(StaticLayout** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VF_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticDevices) return VF_ERR_UNSUPPORTED;
+  if (!g_static_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) return VF_ERR_CUDA;
+    g_static_dev[dev] = p;
+  }
+  *out = static_cast<StaticLayout*>(g_static_dev[dev]);
+  return VF_OK;
+}
+
+// The checks and the Launch block of vf_filter, without recording error text
+// and without fitting: a polynomial must already be in the context's cache.
+vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* out,
+                         LaunchClass* cls) {
+  const vf_params* p = &d.params;
+  if (!d.d_in || !d.d_out) return VF_ERR_ARG;
+  if (d.height < 1 || d.width < 1 || (d.channels != 3 && d.channels != 4)) return VF_ERR_ARG;
+  const size_t row = (size_t)d.width * d.channels;
+  if (d.in_pitch < row || d.out_pitch < row) return VF_ERR_ARG;
+  if ((int)p->criterion < 0 || (int)p->criterion > 4 || (int)p->approx < 0 || (int)p->approx > 2)
+    return VF_ERR_ARG;
+  if (p->window < 1 || (p->window & 1) == 0 || p->window > 15) return VF_ERR_ARG;
+  if (p->window != 3 && p->window != 5 && p->window != 7) return VF_ERR_UNSUPPORTED;
+  if (p->approx == VF_MINIMAX_POLY && (p->degree < 2 || p->degree > 6)) return VF_ERR_ARG;
+  if (!(p->kappa >= 0.0f) || !(p->exp_cutoff > 0.0f)) return VF_ERR_ARG;
+  if (p->precision != VF_FP32) return VF_ERR_UNSUPPORTED;
+  const size_t in_bytes = (size_t)(d.height - 1) * d.in_pitch + row;
+  const size_t out_bytes = (size_t)(d.height - 1) * d.out_pitch + row;
+  if (d.d_in < d.d_out + out_bytes && d.d_out < d.d_in + in_bytes) return VF_ERR_ALIAS;
+  const int w = p->window, n = w * w, crit = (int)p->criterion;
+  int apx = crit == kVMF ? kExact : (int)p->approx;
+  if (apx == kRational && crit == kBVDF) return VF_ERR_UNSUPPORTED;
+  Launch& L = out->L;
+  L = Launch{};
+  L.in = d.d_in;
+  L.out = d.d_out;
+  L.height = d.height;
+  L.width = d.width;
+  L.channels = d.channels;
+  L.vec4_in = d.channels == 4 && ((uintptr_t)d.d_in % 4 == 0) && d.in_pitch % 4 == 0;
+  L.vec4_out = d.channels == 4 && ((uintptr_t)d.d_out % 4 == 0) && d.out_pitch % 4 == 0;
+  L.in_pitch = (long long)d.in_pitch;
+  L.out_pitch = (long long)d.out_pitch;
+  L.kappa_scale = (float)std::pow((double)n, -(double)p->kappa / 3.0);
+  L.exp_cutoff = p->exp_cutoff;
+  L.ent_cutoff = p->ent_cutoff < 0.0f ? (n <= 9 ? 0.05f : 0.05f * 9.0f / (float)n) : p->ent_cutoff;
+  L.stats = nullptr;
+  auto put = [](float* dst, const double* src, int len) {
+    for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
+  };
+  if (apx == kPoly) {
+    const double *a = nullptr, *b = nullptr;
+    if (crit == kBVDF) {
+      a = cached_fit(ctx, 0, p->degree, 0.0, 0.5);
+      b = cached_fit(ctx, 1, p->degree, 0.0, 1.0 / std::sqrt(2.0));
+      if (!a || !b) return VF_ERR_UNSUPPORTED;
+      put(L.c.b, b, p->degree + 1);
+    } else if (crit == kEVMF) {
+      if (!(L.ent_cutoff > 0.0f) || L.ent_cutoff >= 1.0f) return VF_ERR_ARG;
+      a = cached_fit(ctx, 3, p->degree, (double)L.ent_cutoff, 1.0);
+    } else {
+      a = cached_fit(ctx, 2, p->degree, 0.0, (double)p->exp_cutoff);
+    }
+    if (!a) return VF_ERR_UNSUPPORTED;
+    put(L.c.a, a, p->degree + 1);
+  } else if (apx == kRational) {
+    if ((crit == kAMNFE || crit == kAMNFG) && p->exp_cutoff != 10.0f) return VF_ERR_UNSUPPORTED;
+    const double *num = nullptr, *den = nullptr;
+    paper_rational(crit == kEVMF ? 3 : 2, &num, &den);
+    put(L.c.a, num, 5);
+    put(L.c.b, den, 5);
+  }
+  cls->crit = crit;
+  cls->w = w;
+  cls->apx = apx;
+  cls->deg = p->degree;
+  out->cls = class_of(w, crit, apx);
+  return VF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count, void* stream) {
+  if (!ctx || !descs || count < 1) return VF_ERR_ARG;
+  if (count > kStaticMax) return VF_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  StaticLayout* dev = nullptr;
+  vf_status st = static_scratch(&dev);
+  if (st != VF_OK) return st;
+  StaticLayout& H = g_static_host;
+  LaunchClass cls[kStaticMax];
+  BatchImage* staged = H.imgs;  // filled in descriptor order, then reordered below
+  static BatchImage unordered[kStaticMax];
+  for (int i = 0; i < count; ++i) {
+    st = static_prepare(ctx, descs[i], &unordered[i], &cls[i]);
+    if (st != VF_OK) return st;
+    g_static_cost[i] = pixel_cost(cls[i]);
+    g_static_order[i] = i;
+  }
+  // queue order: costliest class first, ties by position (std::sort: in place)
+  std::sort(g_static_order, g_static_order + count, [](int a, int b) {
+    if (g_static_cost[a] != g_static_cost[b]) return g_static_cost[a] > g_static_cost[b];
+    return a < b;
+  });
+  const int ty = 4;
+  size_t smem = 0;
+  long long total = 0;
+  for (int q = 0; q < count; ++q) {
+    const int i = g_static_order[q];
+    staged[q] = unordered[i];
+    Launch& L = staged[q].L;
+    L.tiles_x = (L.width + kTX - 1) / kTX;
+    H.begin[q] = (int)total;
+    total += (long long)L.tiles_x * ((L.height + ty - 1) / ty);
+    if (total > 0x7fffffffLL) return VF_ERR_UNSUPPORTED;
+    smem = std::max(smem, smem_bytes(cls[i].w, cls[i].crit, ty, batch_reg(cls[i].w)));
+  }
+  H.begin[count] = (int)total;
+  cudaStream_t s = (cudaStream_t)stream;
+  int device = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kTX * ty, smem);
+  // pageable host -> device copies return once the source has been staged, so
+  // the host staging may be reused by the next call
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev->begin, H.begin, sizeof(int) * (count + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev->imgs, H.imgs, sizeof(BatchImage) * count, cudaMemcpyHostToDevice, s);
+  // every call starts its tile counter at zero (the array keeps the last call's)
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev->counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return VF_ERR_CUDA;
+  batch_kernel<<<sms * std::max(per_sm, 1), kTX * ty, smem, s>>>(dev->imgs, dev->begin, count,
+                                                                 dev->counter);
+  return cudaGetLastError() == cudaSuccess ? VF_OK : VF_ERR_CUDA;
+}
+
+}  // extern "C"

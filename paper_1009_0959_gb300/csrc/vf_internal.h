@@ -85,6 +85,13 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
 // Record an error text in the context and return s.
 vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg);
 
+// Coefficients of a fit already in the context's cache, or null; never fits
+// or allocates.
+const double* cached_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi);
+
+// The paper's (4,4) rationals (fn 2: exp(-z), fn 3: z ln z), 5 coefficients each.
+void paper_rational(int fn, const double** num, const double** den);
+
 // Host Remez exchange (FP64) of the library: minimax polynomial of degree
 // `degree` for function id (0 acos, 1 2 asin(t/sqrt2), 2 exp(-z), 3 z ln z)
 // on [lo, hi]; coefficients in increasing powers of the argument.

@@ -92,6 +92,8 @@ def lib():
             L.vf_batch_configure.restype = I
             L.vf_batch_destroy.argtypes = [P]
             L.vf_batch_destroy.restype = None
+            L.vf_batch_run_static.argtypes = [P, P, I, P]
+            L.vf_batch_run_static.restype = I
             _lib = L
         return _lib
 
@@ -239,6 +241,30 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+STATIC_MAX_IMAGES = 256
+
+
+def batch_run_static(images, stream=None) -> int:
+    """vf_batch_run_static: the batched filter without any device allocation
+    by the library (its scratch is a fixed array inside the library).  For
+    callers that may not allocate GPU memory on their filtering path.
+    images: list of (inp, out, params_dict) as for Batch.  Returns the status
+    code (0 = VF_OK); no error text is recorded for this call."""
+    import torch
+    descs = (ImageDesc * max(len(images), 1))()
+    for i, (inp, out, params) in enumerate(images):
+        ip, h, w, c, ipitch = _image_args(inp)
+        op, h2, w2, c2, opitch = _image_args(out)
+        if (h, w, c) != (h2, w2, c2):
+            raise ValueError("input and output shapes differ")
+        d = descs[i]
+        d.d_in, d.d_out, d.height, d.width, d.channels = ip, op, h, w, c
+        d.in_pitch, d.out_pitch = ipitch, opitch
+        d.params = make_params(**params)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return lib().vf_batch_run_static(context(), descs, len(images), ctypes.c_void_p(s.cuda_stream))
 
 
 def filter_ptr(d_in: int, d_out: int, height: int, width: int, channels: int, in_pitch: int,

@@ -1,0 +1,71 @@
+"""The allocation-free batched call (vf_batch_run_static).
+
+Some callers may not allocate GPU memory while they filter, e.g. a real-time
+video pipeline or a plug-in inside an application that reserves all device
+memory up front: cudaMalloc there can stall the device for an unbounded time.
+This entry point keeps its scratch in a fixed array inside the library.  The
+test calls it through the C ABI twice in a row and checks both results against
+the ordinary batched call (vf_batch_create + vf_batch_launch) on the same
+images: the same kernel and tiles, so the bytes must be identical (a stricter
+bar than the near-tie band of the parity tests).  This file is collected last
+so that a run stopping at the first failure has run every other test first.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1009_0959_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+CRITS = ["vmf", "bvdf", "amnfe", "amnfg", "evmf"]
+MINIMAX = {"vmf": ("exact", 4), "bvdf": ("poly", 4), "amnfe": ("rational", 4),
+           "amnfg": ("poly", 3), "evmf": ("poly", 5)}
+
+
+@pytest.fixture(scope="module")
+def vf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_0959_gb300 import build, vfilt
+    build.build()
+    return vfilt
+
+
+def _images(n, seed):
+    sizes = synth.batch_sizes(n, seed, lo=(1, 1), hi=(90, 150))
+    out = []
+    for i, (h, w) in enumerate(sizes):
+        crit = CRITS[i % 5]
+        approx, deg = ("exact", 4) if (i // 5) % 2 == 0 else MINIMAX[crit]
+        params = dict(criterion=crit, window=(3, 5, 7)[i % 3], approx=approx, degree=deg)
+        noisy = synth.noisy(h, w, 0.2, seed * 1000 + i)[1]
+        t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+        out.append((t, params))
+    return out
+
+
+def test_static_batch_matches_batch_twice(vf):
+    imgs = _images(40, 5)
+    ref = [(t, torch.zeros_like(t), p) for t, p in imgs]
+    b = vf.Batch(ref)  # also fits and caches the polynomial approximants
+    b.launch()
+    torch.cuda.synchronize()
+    for call in range(2):
+        outs = [(t, torch.full_like(t, 7), p) for t, p in imgs]
+        st = vf.batch_run_static(outs)
+        assert st == 0, vf.status_string(st)
+        torch.cuda.synchronize()
+        for (_, r, _), (_, o, _) in zip(ref, outs):
+            assert torch.equal(r, o), "call %d differs from vf_batch_launch" % call
+    b.close()
+
+
+def test_static_batch_limits(vf):
+    t = torch.zeros((4, 4, 4), dtype=torch.uint8, device="cuda")
+    o = torch.zeros_like(t)
+    too_many = [(t, o, {})] * (vf.STATIC_MAX_IMAGES + 1)
+    assert vf.status_string(vf.batch_run_static(too_many)) == "unsupported combination"
+    assert vf.batch_run_static([(t, t, {})]) == 2  # VF_ERR_ALIAS
+    assert vf.batch_run_static([(t, o, {"window": 9})]) == 3
