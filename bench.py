@@ -139,6 +139,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the packed-precision measurement")
     ap.add_argument("--case", default=None,
                     help="profiling: run one kernel, e.g. bvdf/poly4/w5, on a --size image")
     ap.add_argument("--size", type=int, default=6144)
@@ -333,6 +335,8 @@ def main():
 
     if not args.no_batch:
         line["batched"] = bench_batch()
+    if not args.no_precision:
+        line["precision"] = bench_precision()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs, V, budget_s=15.0)
     if rank == 0:
@@ -395,6 +399,67 @@ def bench_batch(reps=5):
             "per_image_launches_ms": round(single_ms, 3),
             "speedup_vs_per_image": round(single_ms / graph_ms, 3), "autotune": tune,
             "gpu_launches_per_run": 1}
+
+
+def bench_precision(reps=3):
+    """Precision form: one 4096 x 4096 image, 20 % impulses, windows 5 and 7;
+    FP32 / FP16x2 / BF16x2 pair terms (FP32 aggregation) for VMF, BVDF
+    (degree-4 minimax; the FP32 exact path for reference), AMNFE (rational)
+    and EVMF (rational).  Mpix/s per variant from CUDA events; quality against
+    the FP64 oracle's exact filter on 48 sampled rows (16 bands of 3): changed
+    fraction, PSNR and NCD difference (vs the clean image)."""
+    import numpy as np
+    import torch
+
+    from oracle import filters as F
+    from oracle import metrics as M
+    from paper_1009_0959_gb300 import synth, vfilt
+    n = 4096
+    clean, noisy = synth.noisy(n, n, 0.20, 8)
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    out = torch.empty_like(t)
+    bands = [(k * n // 16 + (n // 32), k * n // 16 + (n // 32) + 3) for k in range(16)]
+    rows = np.concatenate([np.arange(a, b) for a, b in bands])
+    threads = os.cpu_count() or 1
+    ref = {}
+    for crit in ("vmf", "bvdf", "amnfe", "evmf"):
+        for w in (5, 7):
+            o = np.zeros_like(noisy)
+            cfg = F.Config(crit, w)
+            for a, b in bands:
+                oo, _ = F.filter_image(noisy, cfg, threads=threads, rows=(a, b))
+                o[a:b] = oo[a:b]
+            ref[(crit, w)] = o[rows]
+    variants = []
+    for w in (5, 7):
+        for crit, approx in (("vmf", "exact"), ("bvdf", "poly"), ("amnfe", "rational"),
+                             ("evmf", "rational")):
+            for prec in ("fp32", "fp16x2", "bf16x2"):
+                variants.append((crit, approx, w, prec))
+        variants.append(("bvdf", "exact", w, "fp32"))
+    res = {}
+    stream = torch.cuda.current_stream()
+    crow = clean[rows]
+    for crit, approx, w, prec in variants:
+        kw = dict(criterion=crit, window=w, approx=approx, degree=4, precision=prec)
+        vfilt.filter(t, out, stream=stream, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            vfilt.filter(t, out, stream=stream, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        g = out.cpu().numpy()[rows][..., :3]
+        r = ref[(crit, w)]
+        res["%s/%s/w%d/%s" % (crit, approx, w, prec)] = {
+            "mpix_s": round(n * n / ms / 1e3, 1), "ms": round(ms, 3),
+            "changed_vs_oracle": round(M.changed_fraction(r, g), 5),
+            "psnr_drop_db": round(M.psnr(crow, r) - M.psnr(crow, g), 4),
+            "ncd_diff": round(M.ncd(crow, g) - M.ncd(crow, r), 6)}
+    return {"workload": "4096x4096 RGBX, 20 %% impulses (seed 8), w 5/7; quality on %d rows "
+                        "against the FP64 oracle's exact filter" % len(rows), "variants": res}
 
 
 def run_case(args):

@@ -169,8 +169,8 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   if (p->approx == VF_MINIMAX_POLY && (p->degree < 2 || p->degree > 6))
     return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
   if (!(p->kappa >= 0.0f) || !(p->exp_cutoff > 0.0f)) return fail(ctx, VF_ERR_ARG, "bad kappa/cut-off");
-  if (p->precision != VF_FP32)
-    return fail(ctx, VF_ERR_UNSUPPORTED, "packed precision is not built for this criterion");
+  if (p->precision != VF_FP32 && p->criterion == VF_BVDF && p->approx != VF_MINIMAX_POLY)
+    return fail(ctx, VF_ERR_UNSUPPORTED, "packed BVDF runs the minimax polynomial only");
   const size_t in_bytes = (size_t)(height - 1) * in_pitch + (size_t)width * channels;
   const size_t out_bytes = (size_t)(height - 1) * out_pitch + (size_t)width * channels;
   if (overlap(d_in, in_bytes, d_out, out_bytes))
@@ -238,6 +238,7 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   cls->w = w;
   cls->apx = apx;
   cls->deg = apx == kPoly ? p->degree : (apx == kRational ? 4 : 0);
+  cls->precision = (int)p->precision;
   return VF_OK;
 }
 
@@ -266,12 +267,16 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
                                 d_stats, &L, &cls);
   if (st != VF_OK) return st;
   const int ty = ctx->tile_rows;
-  L.tiles_x = (width + kTX - 1) / kTX;
+  const int cols = cls.precision == VF_FP32 ? kTX : kPackedTileCols;
+  L.tiles_x = (width + cols - 1) / cols;
   const int tiles_y = (height + ty - 1) / ty;
   const long long grid = (long long)L.tiles_x * tiles_y;
   if (grid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_filter(L, cls.crit, cls.w, cls.apx, cls.deg, ty, (int)grid, s);
+  cudaError_t e = cls.precision == VF_FP32
+                      ? launch_filter(L, cls.crit, cls.w, cls.apx, cls.deg, ty, (int)grid, s)
+                      : launch_packed(L, cls.precision, cls.crit, cls.w, cls.apx, cls.deg, ty,
+                                      (int)grid, s);
   if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
   return VF_OK;
 }

@@ -221,6 +221,8 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
     LaunchClass c;
     vf_status st = prepare_launch(ctx, d.d_in, d.d_out, d.height, d.width, d.channels,
                                   d.in_pitch, d.out_pitch, &d.params, nullptr, &imgs[i].L, &c);
+    if (st == VF_OK && c.precision != VF_FP32)
+      st = set_error(ctx, VF_ERR_UNSUPPORTED, "the batched form runs in FP32 only");
     if (st != VF_OK) {
       delete b;
       return st;

@@ -25,4 +25,18 @@ cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int
 
 #undef VF_CASE
 
+cudaError_t launch_packed(const Launch& L, int precision, int criterion, int w, int approx,
+                          int degree, int ty, int grid, cudaStream_t s) {
+  if (precision == 1) {
+    if (w == 3) return launch_packed_fp16_w3(L, criterion, approx, degree, ty, grid, s);
+    if (w == 5) return launch_packed_fp16_w5(L, criterion, approx, degree, ty, grid, s);
+    if (w == 7) return launch_packed_fp16_w7(L, criterion, approx, degree, ty, grid, s);
+  } else if (precision == 2) {
+    if (w == 3) return launch_packed_bf16_w3(L, criterion, approx, degree, ty, grid, s);
+    if (w == 5) return launch_packed_bf16_w5(L, criterion, approx, degree, ty, grid, s);
+    if (w == 7) return launch_packed_bf16_w7(L, criterion, approx, degree, ty, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace vf

@@ -67,13 +67,27 @@ VF_DECLARE_LAUNCH(amnfg)
 VF_DECLARE_LAUNCH(evmf)
 #undef VF_DECLARE_LAUNCH
 
+// Packed-precision launchers (vf_p_<fp16|bf16>_w<w>.cu); one CTA covers
+// 64 x ty outputs.
+#define VF_DECLARE_PACKED(name)                                                            \
+  cudaError_t launch_packed_##name##_w3(const Launch&, int, int, int, int, int, cudaStream_t); \
+  cudaError_t launch_packed_##name##_w5(const Launch&, int, int, int, int, int, cudaStream_t); \
+  cudaError_t launch_packed_##name##_w7(const Launch&, int, int, int, int, int, cudaStream_t);
+VF_DECLARE_PACKED(fp16)
+VF_DECLARE_PACKED(bf16)
+#undef VF_DECLARE_PACKED
+constexpr int kPackedTileCols = 64;
+
 // Dispatch on criterion and window (vf_dispatch.cpp).
 cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int degree, int ty,
                           int grid, cudaStream_t s);
+// precision 1 = FP16x2, 2 = BF16x2
+cudaError_t launch_packed(const Launch& L, int precision, int criterion, int w, int approx,
+                          int degree, int ty, int grid, cudaStream_t s);
 
 // The kernel class of a request: criterion, window, approximation, degree.
 struct LaunchClass {
-  int crit, w, apx, deg;
+  int crit, w, apx, deg, precision;
 };
 
 // Argument checks, coefficients and the Launch block of one image (shared by
