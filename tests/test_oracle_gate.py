@@ -1,0 +1,86 @@
+"""Pins of the FP64 gate oracle: finite differences, closed forms of the
+convolution, BCE identities.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import gate as G
+from paper_1009_0959_gb300 import synth
+
+
+def test_conv_delta_kernel_is_identity():
+    rng = np.random.default_rng(0)
+    x = rng.random((3, 7, 9))
+    W = np.zeros((3, 3, 3, 3))
+    for c in range(3):
+        W[c, c, 1, 1] = 1.0
+    np.testing.assert_allclose(G.conv3x3(x, W, np.zeros(3)), x)
+
+
+def test_conv_shift_and_zero_padding():
+    """A kernel with its single 1 at (u, v) = (0, 2) reads x[y-1, x+1]; rows
+    and columns outside the image read 0."""
+    x = np.arange(20, dtype=np.float64).reshape(1, 4, 5)
+    W = np.zeros((1, 1, 3, 3))
+    W[0, 0, 0, 2] = 1.0
+    z = G.conv3x3(x, W, np.array([0.5]))[0]
+    ref = np.full((4, 5), 0.5)
+    ref[1:, :4] += x[0, :3, 1:]
+    np.testing.assert_allclose(z, ref)
+
+
+def test_conv_grads_adjoint():
+    """<dz, conv(x)> is linear in x and W: its gradients are the adjoints."""
+    rng = np.random.default_rng(1)
+    x = rng.random((2, 5, 6))
+    W = rng.normal(size=(3, 2, 3, 3))
+    dz = rng.normal(size=(3, 5, 6))
+    dW, db, dx = G.conv3x3_grads(x, W, dz)
+    f = lambda xx, WW: np.sum(dz * G.conv3x3(xx, WW, np.zeros(3)))  # noqa: E731
+    np.testing.assert_allclose(np.sum(dx * x), f(x, W), rtol=1e-12)
+    np.testing.assert_allclose(np.sum(dW * W), f(x, W), rtol=1e-12)
+    np.testing.assert_allclose(db, dz.reshape(3, -1).sum(1))
+
+
+def test_gradient_matches_finite_differences():
+    clean, noisy = synth.noisy(6, 7, 0.3, 3)
+    t = G.target_mask(clean, noisy)
+    theta = G.init(5) * 0.7
+    theta[G.NPARAM - 1] = 0.1
+    cache = [G.forward(noisy, theta)]
+    g = G.backward(cache, [t], theta)
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.choice(432, 8, replace=False), [432 + 3],
+                          448 + rng.choice(2304, 8, replace=False), [2752 + 5],
+                          2768 + rng.choice(144, 6, replace=False), [2912]])
+    h = 1e-6
+    for k in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        num = (G.loss([G.forward(noisy, tp)], [t]) - G.loss([G.forward(noisy, tm)], [t])) / (2 * h)
+        assert abs(num - g[k]) <= 1e-6 * max(1.0, abs(num)) + 1e-9, (k, num, g[k])
+
+
+def test_bce_closed_forms():
+    """All-zero weights: p = sigmoid(b3) everywhere; the loss is the BCE of a
+    constant; the b3 gradient is mean(p - t)."""
+    clean, noisy = synth.noisy(5, 5, 0.4, 4)
+    t = G.target_mask(clean, noisy)
+    theta = np.zeros(G.NPARAM)
+    theta[-1] = 0.3
+    c = G.forward(noisy, theta)
+    p = 1 / (1 + np.exp(-0.3))
+    np.testing.assert_allclose(c["p"], p)
+    np.testing.assert_allclose(G.loss([c], [t]), -np.mean(t * np.log(p) + (1 - t) * np.log(1 - p)))
+    g = G.backward([c], [t], theta)
+    assert g[-1] == pytest.approx(np.mean(p - t))
+    assert np.all(g[:-1] == 0.0)
+
+
+def test_bf16_round():
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -3.14159, 1e-3])
+    r = G.bf16_round(vals)
+    np.testing.assert_array_equal(r[:2], [1.0, 1.0])       # tie to even
+    assert r[2] == 1.0 + 2 ** -7                              # rounds up
+    assert abs(r[3] + 3.14159) <= 2 ** -7 * 4
+    assert abs(r[4] - 1e-3) <= 1e-3 * 2 ** -8
