@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (oracle side).  The network is not in the paper; it
 is a learned stand-in for the detection step of switching filters such as the
 EVMF (Sec. 3.3, whose entropy switch decides which pixels get filtered):
 
-  x0 = RGB / 255                                    (3 x H x W)
+  x0 = RGB / 255 - 1/2                              (3 x H x W, centred)
   z1 = conv3x3(x0; W1, b1),  a1 = max(z1, 0)        (16 channels)
   z2 = conv3x3(a1; W2, b2),  a2 = max(z2, 0)        (16 channels)
   z3 = conv3x3(a2; W3, b3)                          (1 channel, the logit)
@@ -86,7 +86,7 @@ def conv3x3_grads(x, W, dz):
 def forward(img, theta):
     """img: H x W x 3 (or 4) uint8.  Returns the cache of every layer."""
     p = unflatten(theta)
-    x0 = np.transpose(np.asarray(img)[..., :3].astype(np.float64) / 255.0, (2, 0, 1))
+    x0 = np.transpose(np.asarray(img)[..., :3].astype(np.float64) / 255.0 - 0.5, (2, 0, 1))
     z1 = conv3x3(x0, p["W1"], p["b1"])
     a1 = np.maximum(z1, 0.0)
     z2 = conv3x3(a1, p["W2"], p["b2"])
