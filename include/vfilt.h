@@ -230,6 +230,75 @@ void vf_batch_destroy(vf_batch* b);
 #define VF_STATIC_MAX_IMAGES 256
 vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count, void* stream);
 
+/* ---- learned impulse gate (not in the paper) --------------------------------
+ * A small convolutional detector that decides which pixels get the window
+ * filter, as the EVMF switch (Sec. 3.3, Eq. equ_evf) decides it with an
+ * entropy test.  Network: x0 = RGB / 255 - 1/2; z1 = conv3x3(x0) (16 channels),
+ * ReLU; z2 = conv3x3 (16 -> 16), ReLU; z3 = conv3x3 (16 -> 1); p = sigmoid(z3);
+ * zero padding at every layer.  Parameters: a flat FP32 vector of
+ * VF_GATE_NPARAM values in the order W1[16][3][3][3], b1[16],
+ * W2[16][16][3][3], b2[16], W3[1][16][3][3], b3[1].  The kernels use BF16
+ * copies of the weights with FP32 activations and accumulation; training
+ * updates FP32 master weights with Adam (beta1 0.9, beta2 0.999, eps 1e-8)
+ * on the mean binary cross-entropy against 0/1 targets.  Training is
+ * deterministic (no floating-point atomics): the same seed, data and steps
+ * give the same bits, also across vf_gate_save / vf_gate_load. */
+#define VF_GATE_NPARAM 2913
+
+typedef struct vf_gate vf_gate;
+
+/* New gate with He-normal weights drawn from `seed` (zero biases) and zeroed
+ * Adam state; device memory owned by the gate.  Synchronous. */
+vf_status vf_gate_create(vf_ctx* ctx, unsigned long long seed, vf_gate** gate);
+/* Host FP32 parameters in / out (n must be VF_GATE_NPARAM).  Setting resets
+ * the Adam state and the step count.  Synchronous. */
+vf_status vf_gate_set_params(vf_gate* g, const float* params, int n);
+vf_status vf_gate_get_params(vf_gate* g, float* params, int n);
+
+/* Batch of `count` equally sized images (device, 3 or 4 bytes per pixel, rows
+ * `pitch` bytes apart, image k starting at d_imgs + k * height * pitch) with
+ * 0/1 targets (device bytes, count x height x width, dense).
+ *   vf_gate_gradient    writes the gradient of the mean BCE to d_grad
+ *                       (VF_GATE_NPARAM floats, device), the loss to d_loss
+ *                       and the probabilities to d_prob (count x H x W
+ *                       floats); any of the three may be NULL
+ *   vf_gate_train_step  the same forward / backward, then one Adam step with
+ *                       learning rate lr; d_loss (device float) may be NULL
+ * Asynchronous on `stream`.  The gate keeps activation scratch sized for the
+ * largest batch seen (VF_ERR_OOM if it cannot grow). */
+vf_status vf_gate_gradient(vf_gate* g, const uint8_t* d_imgs, const uint8_t* d_targets, int count,
+                           int height, int width, int channels, size_t pitch, float* d_grad,
+                           float* d_loss, float* d_prob, void* stream);
+vf_status vf_gate_train_step(vf_gate* g, const uint8_t* d_imgs, const uint8_t* d_targets,
+                             int count, int height, int width, int channels, size_t pitch,
+                             float lr, float* d_loss, void* stream);
+
+/* Fused inference over one image: d_flags[y * flag_pitch + x] = 1 where the
+ * impulse probability exceeds `threshold` (0 < threshold < 1), else 0; d_prob
+ * (height x width floats, dense) receives the probabilities.  Either output
+ * may be NULL (not both).  Asynchronous on `stream`. */
+vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, int channels,
+                        size_t pitch, float threshold, uint8_t* d_flags, size_t flag_pitch,
+                        float* d_prob, void* stream);
+
+/* vf_filter restricted to the pixels whose flag byte is non-zero; all other
+ * pixels are copied from d_in.  VMF, BVDF, AMNFE and AMNFG in FP32 (EVMF has
+ * its own switch: VF_ERR_UNSUPPORTED).  Otherwise as vf_filter; the third
+ * counter (VF_STAT_SWITCHED) counts the flagged pixels. */
+vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                          int channels, size_t in_pitch, size_t out_pitch, const uint8_t* d_flags,
+                          size_t flag_pitch, const vf_params* p, void* stream,
+                          unsigned long long* d_stats);
+
+/* Checkpoint: magic "VFGATE01", version 1, VF_GATE_NPARAM, step, seed,
+ * FP32 master weights, Adam first and second moments, CRC-32 of all that.
+ * Load restores weights, moments, step and seed (VF_ERR_ARG on a bad file
+ * or CRC).  Synchronous. */
+vf_status vf_gate_save(vf_gate* g, const char* path);
+vf_status vf_gate_load(vf_gate* g, const char* path);
+unsigned long long vf_gate_step_count(const vf_gate* g);
+void vf_gate_destroy(vf_gate* g);
+
 #ifdef __cplusplus
 }
 #endif

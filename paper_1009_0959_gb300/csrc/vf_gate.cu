@@ -1,0 +1,695 @@
+// vf_gate.cu -- the learned impulse detector ("gate"): a 3-layer 3x3
+// convolutional network (3 -> 16 -> 16 -> 1 channels, ReLU, sigmoid) that
+// flags the pixels worth filtering, its training kernels (forward, backward,
+// Adam) and its fused inference kernel.  Not in the paper: it is a learned
+// stand-in for the detection step of switching filters (Sec. 3.3's EVMF
+// switch decides the same thing with an entropy test).
+//
+// Arithmetic: BF16 weights (rounded from FP32 master weights after every
+// update), FP32 activations and FP32 accumulation.  Convolutions are
+// cross-correlations with zero padding, input x0 = RGB / 255 - 1/2.
+// Determinism: weight gradients are reduced per CTA into a partial buffer and
+// the partials are summed in a fixed order by a second kernel (no floating
+// point atomics), so training is bit-reproducible and resumable.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vf_internal.h"
+
+namespace vf {
+cudaError_t launch_gated_w3(const Launch&, const uint8_t*, long long, int, int, int, int, int,
+                            cudaStream_t);
+cudaError_t launch_gated_w5(const Launch&, const uint8_t*, long long, int, int, int, int, int,
+                            cudaStream_t);
+cudaError_t launch_gated_w7(const Launch&, const uint8_t*, long long, int, int, int, int, int,
+                            cudaStream_t);
+}  // namespace vf
+
+namespace {
+
+constexpr int kC = 16;  // hidden channels
+constexpr int OFF_W1 = 0, OFF_B1 = 432, OFF_W2 = 448, OFF_B2 = 2752, OFF_W3 = 2768,
+              OFF_B3 = 2912, NPARAM = 2913;
+static_assert(NPARAM == VF_GATE_NPARAM, "parameter count");
+constexpr int kThreads = 256;
+constexpr int kWgradBlocks = 64;  // pixel chunks of the weight-gradient reduction
+
+struct Images {
+  const uint8_t* img;  // image k at img + k * stride; rows `pitch` bytes apart
+  long long stride, pitch;
+  int count, H, W, channels;
+};
+
+__device__ __forceinline__ float pixel_channel(const Images& I, int b, int y, int x, int c) {
+  return (float)I.img[b * I.stride + (long long)y * I.pitch + (long long)x * I.channels + c] *
+             (1.0f / 255.0f) -
+         0.5f;
+}
+
+__device__ __forceinline__ void load_weights(const __nv_bfloat16* wb, float* w, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) w[k] = __bfloat162float(wb[k]);
+}
+
+// Activation a[c](b, y, x) of the layer feeding a convolution: x0 from the
+// image (layer 1) or relu(z) of the previous layer; 0 outside the image.
+template <bool FROM_IMG>
+__device__ __forceinline__ float act(const Images& I, const float* z, int cin, int b, int c,
+                                     int y, int x) {
+  if (y < 0 || y >= I.H || x < 0 || x >= I.W) return 0.0f;
+  if constexpr (FROM_IMG) {
+    return pixel_channel(I, b, y, x, c);
+  } else {
+    return fmaxf(z[(((long long)b * cin + c) * I.H + y) * I.W + x], 0.0f);
+  }
+}
+
+// z_out[b][o][y][x] = bias[o] + sum_c sum_{u,v} W[o][c][u][v] a[c](y+u-1, x+v-1)
+template <int CIN, int COUT, bool FROM_IMG>
+__global__ void __launch_bounds__(kThreads) conv_fwd(Images I, const __nv_bfloat16* wb,
+                                                     int off_w, int off_b, const float* zin,
+                                                     float* zout) {
+  __shared__ float w[COUT * CIN * 9 + COUT];
+  load_weights(wb + off_w, w, COUT * CIN * 9);
+  load_weights(wb + off_b, w + COUT * CIN * 9, COUT);
+  __syncthreads();
+  const long long total = (long long)I.count * I.H * I.W;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int b = (int)(idx / ((long long)I.H * I.W));
+  const int rem = (int)(idx - (long long)b * I.H * I.W);
+  const int y = rem / I.W, x = rem - y * I.W;
+  float acc[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc[o] = w[COUT * CIN * 9 + o];
+  for (int c = 0; c < CIN; ++c)
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const float a = act<FROM_IMG>(I, zin, CIN, b, c, y + u - 1, x + v - 1);
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) acc[o] = fmaf(w[((o * CIN + c) * 3 + u) * 3 + v], a, acc[o]);
+      }
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) zout[(((long long)b * COUT + o) * I.H + y) * I.W + x] = acc[o];
+}
+
+// Sigmoid, per-pixel BCE (logit form) and dL/dz3 = (p - t) / N.
+__global__ void __launch_bounds__(kThreads) bce_head(Images I, const float* z3,
+                                                     const uint8_t* target, float* dz3,
+                                                     float* prob, float* loss_part) {
+  __shared__ float red[kThreads];
+  const long long total = (long long)I.count * I.H * I.W;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (idx < total) {
+    const float z = z3[idx];
+    const float p = 1.0f / (1.0f + expf(-z));
+    if (prob) prob[idx] = p;
+    if (target) {
+      const float t = target[idx] ? 1.0f : 0.0f;
+      l = fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))) - t * z;
+      dz3[idx] = (p - t) / (float)total;
+    }
+  }
+  red[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss_part) loss_part[blockIdx.x] = red[0];
+}
+
+// Fixed-order sum of n partials into out[0] (one CTA).
+__global__ void __launch_bounds__(kThreads) sum_partials(const float* part, int n, float scale,
+                                                         float* out) {
+  __shared__ float red[kThreads];
+  float s = 0.0f;
+  for (int k = threadIdx.x; k < n; k += kThreads) s += part[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0] * scale;
+}
+
+// Weight gradients of one convolution: block (chunk, o * CIN + c) accumulates
+// dW[o][c][.][.] (and db[o] when c = 0) over its chunk of pixels into
+// part[chunk][...] (a full parameter vector per chunk).
+template <int CIN, int COUT, bool FROM_IMG>
+__global__ void __launch_bounds__(kThreads) conv_wgrad(Images I, const float* zin,
+                                                       const float* dz, int off_w, int off_b,
+                                                       float* part) {
+  __shared__ float red[10][kThreads];
+  const int o = blockIdx.y / CIN, c = blockIdx.y - o * CIN;
+  const long long total = (long long)I.count * I.H * I.W;
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  const long long p0 = (long long)blockIdx.x * per, p1 = min(total, p0 + per);
+  float g[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) g[k] = 0.0f;
+  for (long long idx = p0 + threadIdx.x; idx < p1; idx += kThreads) {
+    const int b = (int)(idx / ((long long)I.H * I.W));
+    const int rem = (int)(idx - (long long)b * I.H * I.W);
+    const int y = rem / I.W, x = rem - y * I.W;
+    const float d = dz[(((long long)b * COUT + o) * I.H + y) * I.W + x];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        g[u * 3 + v] = fmaf(d, act<FROM_IMG>(I, zin, CIN, b, c, y + u - 1, x + v - 1), g[u * 3 + v]);
+    g[9] += d;
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) red[k][threadIdx.x] = g[k];
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+#pragma unroll
+      for (int k = 0; k < 10; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x < 9)
+    part[(long long)blockIdx.x * NPARAM + off_w + (o * CIN + c) * 9 + threadIdx.x] =
+        red[threadIdx.x][0];
+  if (threadIdx.x == 9 && c == 0) part[(long long)blockIdx.x * NPARAM + off_b + o] = red[9][0];
+}
+
+// dz_prev[c](q) = [z_prev[c](q) > 0] * sum_o sum_{u,v} W[o][c][u][v] dz[o](q - (u,v) + 1)
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kThreads) conv_igrad(Images I, const __nv_bfloat16* wb,
+                                                       int off_w, const float* dz,
+                                                       const float* zprev, float* dzprev) {
+  __shared__ float w[COUT * CIN * 9];
+  load_weights(wb + off_w, w, COUT * CIN * 9);
+  __syncthreads();
+  const long long total = (long long)I.count * I.H * I.W;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int b = (int)(idx / ((long long)I.H * I.W));
+  const int rem = (int)(idx - (long long)b * I.H * I.W);
+  const int y = rem / I.W, x = rem - y * I.W;
+  float acc[CIN];
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) acc[c] = 0.0f;
+  for (int o = 0; o < COUT; ++o)
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const int yy = y - u + 1, xx = x - v + 1;
+        if (yy < 0 || yy >= I.H || xx < 0 || xx >= I.W) continue;
+        const float d = dz[(((long long)b * COUT + o) * I.H + yy) * I.W + xx];
+#pragma unroll
+        for (int c = 0; c < CIN; ++c) acc[c] = fmaf(w[((o * CIN + c) * 3 + u) * 3 + v], d, acc[c]);
+      }
+#pragma unroll
+  for (int c = 0; c < CIN; ++c) {
+    const long long k = (((long long)b * CIN + c) * I.H + y) * I.W + x;
+    dzprev[k] = zprev[k] > 0.0f ? acc[c] : 0.0f;
+  }
+}
+
+// grad[k] = sum over chunks (fixed order), k = 0 .. NPARAM-1
+__global__ void reduce_grads(const float* part, int chunks, float* grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NPARAM) return;
+  float s = 0.0f;
+  for (int j = 0; j < chunks; ++j) s += part[(long long)j * NPARAM + k];
+  grad[k] = s;
+}
+
+// Adam (Kingma & Ba, 2015) on the FP32 masters, then the BF16 copy.
+__global__ void adam(float* theta, float* m, float* v, const float* grad, __nv_bfloat16* wb,
+                     float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NPARAM) return;
+  const float g = grad[k];
+  const float mk = b1 * m[k] + (1.0f - b1) * g;
+  const float vk = b2 * v[k] + (1.0f - b2) * g * g;
+  m[k] = mk;
+  v[k] = vk;
+  const float t = theta[k] - lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+  theta[k] = t;
+  wb[k] = __float2bfloat16_rn(t);
+}
+
+__global__ void to_bf16(const float* theta, __nv_bfloat16* wb) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < NPARAM) wb[k] = __float2bfloat16_rn(theta[k]);
+}
+
+// ---- fused inference: 32 x 8 outputs per CTA, the three layers in shared
+// memory (halo 3 / 2 / 1), activations outside the image are 0 at every layer
+constexpr int IX = 32, IY = 8;
+constexpr int S0X = IX + 6, S0Y = IY + 6;  // input region
+constexpr int S1X = IX + 4, S1Y = IY + 4;  // layer-1 outputs
+constexpr int S2X = IX + 2, S2Y = IY + 2;  // layer-2 outputs
+constexpr size_t kInferSmem =
+    sizeof(float) * (NPARAM + 3 * S0Y * S0X + kC * S1Y * S1X + kC * S2Y * S2X);
+
+__global__ void __launch_bounds__(IX * IY) gate_infer(Images I, const __nv_bfloat16* wb,
+                                                      float logit_threshold, uint8_t* flags,
+                                                      long long flag_pitch, float* prob,
+                                                      int tiles_x) {
+  extern __shared__ float sm[];
+  float* w = sm;                       // weights, W2 and W3 as [c][u][v][o] for broadcast
+  float* s0 = w + NPARAM;              // [3][S0Y][S0X]
+  float* s1 = s0 + 3 * S0Y * S0X;      // [16][S1Y][S1X]
+  float* s2 = s1 + kC * S1Y * S1X;     // [16][S2Y][S2X]
+  const int x0 = (blockIdx.x % tiles_x) * IX, y0 = (blockIdx.x / tiles_x) * IY;
+  for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) {
+    int dst = k;
+    if (k >= OFF_W2 && k < OFF_B2) {  // [o][c][u][v] -> [c][u][v][o]
+      int r = k - OFF_W2, o = r / 144, cuv = r - o * 144;
+      dst = OFF_W2 + cuv * kC + o;
+    }
+    w[dst] = __bfloat162float(wb[k]);
+  }
+  for (int k = threadIdx.x; k < 3 * S0Y * S0X; k += blockDim.x) {
+    int c = k / (S0Y * S0X), r = k - c * S0Y * S0X, ry = r / S0X, rx = r - ry * S0X;
+    int gy = y0 - 3 + ry, gx = x0 - 3 + rx;
+    s0[k] = (gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) ? pixel_channel(I, 0, gy, gx, c) : 0.0f;
+  }
+  __syncthreads();
+  // layer 1 on the S1 region
+  for (int k = threadIdx.x; k < S1Y * S1X; k += blockDim.x) {
+    int ry = k / S1X, rx = k - ry * S1X;
+    int gy = y0 - 2 + ry, gx = x0 - 2 + rx;
+    bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+    float acc[kC];
+#pragma unroll
+    for (int o = 0; o < kC; ++o) acc[o] = w[OFF_B1 + o];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          float a = s0[(c * S0Y + ry + u) * S0X + rx + v];
+#pragma unroll
+          for (int o = 0; o < kC; ++o) acc[o] = fmaf(w[OFF_W1 + ((o * 3 + c) * 3 + u) * 3 + v], a, acc[o]);
+        }
+#pragma unroll
+    for (int o = 0; o < kC; ++o) s1[(o * S1Y + ry) * S1X + rx] = in ? fmaxf(acc[o], 0.0f) : 0.0f;
+  }
+  __syncthreads();
+  // layer 2 on the S2 region
+  for (int k = threadIdx.x; k < S2Y * S2X; k += blockDim.x) {
+    int ry = k / S2X, rx = k - ry * S2X;
+    int gy = y0 - 1 + ry, gx = x0 - 1 + rx;
+    bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+    float acc[kC];
+#pragma unroll
+    for (int o = 0; o < kC; ++o) acc[o] = w[OFF_B2 + o];
+    for (int c = 0; c < kC; ++c)
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          float a = s1[(c * S1Y + ry + u) * S1X + rx + v];
+          const float* wc = w + OFF_W2 + ((c * 3 + u) * 3 + v) * kC;
+#pragma unroll
+          for (int o = 0; o < kC; ++o) acc[o] = fmaf(wc[o], a, acc[o]);
+        }
+#pragma unroll
+    for (int o = 0; o < kC; ++o) s2[(o * S2Y + ry) * S2X + rx] = in ? fmaxf(acc[o], 0.0f) : 0.0f;
+  }
+  __syncthreads();
+  // layer 3: one output per thread
+  const int tx = threadIdx.x % IX, ty = threadIdx.x / IX;
+  const int gx = x0 + tx, gy = y0 + ty;
+  float z = w[OFF_B3];
+  for (int c = 0; c < kC; ++c)
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        z = fmaf(w[OFF_W3 + (c * 3 + u) * 3 + v], s2[(c * S2Y + ty + u) * S2X + tx + v], z);
+  if (gx < I.W && gy < I.H) {
+    if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
+    if (prob) prob[(long long)gy * I.W + gx] = 1.0f / (1.0f + expf(-z));
+  }
+}
+
+uint32_t crc32(const unsigned char* p, size_t n, uint32_t crc = 0) {
+  // CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bitwise
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= p[i];
+    for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+}  // namespace
+
+using namespace vf;
+
+struct vf_gate {
+  vf_ctx* ctx = nullptr;
+  float* theta = nullptr;  // FP32 masters
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  __nv_bfloat16* wb = nullptr;
+  unsigned long long step = 0, seed = 0;
+  // training scratch, grown on demand
+  float* z1 = nullptr;
+  float* z2 = nullptr;
+  float* z3 = nullptr;
+  float* dz1 = nullptr;
+  float* dz2 = nullptr;
+  float* part = nullptr;
+  float* loss_part = nullptr;
+  long long cap_pixels = 0;
+};
+
+namespace {
+
+void free_scratch(vf_gate* g) {
+  for (float** p : {&g->z1, &g->z2, &g->z3, &g->dz1, &g->dz2, &g->loss_part}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  g->cap_pixels = 0;
+}
+
+vf_status ensure_scratch(vf_gate* g, long long pixels) {
+  if (pixels <= g->cap_pixels) return VF_OK;
+  free_scratch(g);
+  const size_t P = (size_t)pixels;
+  const long long blocks = (pixels + kThreads - 1) / kThreads;
+  cudaError_t e = cudaMalloc(&g->z1, P * kC * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->z2, P * kC * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->z3, P * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->dz1, P * kC * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->dz2, P * kC * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->loss_part, (size_t)blocks * 4);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_scratch(g);
+    return set_error(g->ctx, VF_ERR_OOM, "gate training scratch allocation failed");
+  }
+  g->cap_pixels = pixels;
+  return VF_OK;
+}
+
+vf_status check_images(vf_gate* g, const uint8_t* d_imgs, int count, int H, int W, int channels,
+                       size_t pitch, Images* I) {
+  if (!d_imgs || count < 1 || H < 1 || W < 1 || (channels != 3 && channels != 4) ||
+      pitch < (size_t)W * channels)
+    return set_error(g->ctx, VF_ERR_ARG, "bad gate images");
+  I->img = d_imgs;
+  I->pitch = (long long)pitch;
+  I->stride = (long long)pitch * H;
+  I->count = count;
+  I->H = H;
+  I->W = W;
+  I->channels = channels;
+  return VF_OK;
+}
+
+// Forward (and, with targets, backward into g->grad) over a batch.
+vf_status run_train(vf_gate* g, const Images& I, const uint8_t* targets, cudaStream_t s,
+                    float* d_loss, float* d_prob) {
+  const long long P = (long long)I.count * I.H * I.W;
+  vf_status st = ensure_scratch(g, P);
+  if (st != VF_OK) return st;
+  const int blocks = (int)((P + kThreads - 1) / kThreads);
+  conv_fwd<3, kC, true><<<blocks, kThreads, 0, s>>>(I, g->wb, OFF_W1, OFF_B1, nullptr, g->z1);
+  conv_fwd<kC, kC, false><<<blocks, kThreads, 0, s>>>(I, g->wb, OFF_W2, OFF_B2, g->z1, g->z2);
+  conv_fwd<kC, 1, false><<<blocks, kThreads, 0, s>>>(I, g->wb, OFF_W3, OFF_B3, g->z2, g->z3);
+  float* dz3 = g->dz1;  // reused: dz3 has one channel
+  bce_head<<<blocks, kThreads, 0, s>>>(I, g->z3, targets, dz3, d_prob, g->loss_part);
+  if (targets) {
+    if (d_loss) sum_partials<<<1, kThreads, 0, s>>>(g->loss_part, blocks, 1.0f / (float)P, d_loss);
+    cudaMemsetAsync(g->part, 0, sizeof(float) * (size_t)kWgradBlocks * NPARAM, s);
+    conv_wgrad<kC, 1, false><<<dim3(kWgradBlocks, kC), kThreads, 0, s>>>(I, g->z2, dz3, OFF_W3,
+                                                                          OFF_B3, g->part);
+    conv_igrad<kC, 1><<<blocks, kThreads, 0, s>>>(I, g->wb, OFF_W3, dz3, g->z2, g->dz2);
+    conv_wgrad<kC, kC, false><<<dim3(kWgradBlocks, kC * kC), kThreads, 0, s>>>(
+        I, g->z1, g->dz2, OFF_W2, OFF_B2, g->part);
+    conv_igrad<kC, kC><<<blocks, kThreads, 0, s>>>(I, g->wb, OFF_W2, g->dz2, g->z1, g->dz1);
+    conv_wgrad<3, kC, true><<<dim3(kWgradBlocks, 3 * kC), kThreads, 0, s>>>(I, nullptr, g->dz1,
+                                                                            OFF_W1, OFF_B1, g->part);
+    reduce_grads<<<(NPARAM + 255) / 256, 256, 0, s>>>(g->part, kWgradBlocks, g->grad);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vf_status vf_gate_create(vf_ctx* ctx, unsigned long long seed, vf_gate** out) {
+  if (!ctx || !out) return VF_ERR_ARG;
+  *out = nullptr;
+  vf_gate* g = new (std::nothrow) vf_gate();
+  if (!g) return VF_ERR_OOM;
+  g->ctx = ctx;
+  g->seed = seed;
+  cudaError_t e = cudaMalloc(&g->theta, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->m, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->v, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->grad, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&g->wb, NPARAM * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&g->part, sizeof(float) * (size_t)kWgradBlocks * NPARAM);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    vf_gate_destroy(g);
+    return set_error(ctx, VF_ERR_OOM, "gate allocation failed");
+  }
+  // He-normal initial weights from a counter-based generator (splitmix64 +
+  // Box-Muller), zero biases
+  std::vector<float> h(NPARAM, 0.0f);
+  auto mix = [](unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto uni = [&](unsigned long long k) {
+    return ((mix(seed * 0x100000001B3ull + k) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](int off, int n, int fan_in) {
+    for (int k = 0; k < n; ++k) {
+      double u1 = uni(2ull * (off + k)), u2 = uni(2ull * (off + k) + 1);
+      double nrm = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+      h[off + k] = (float)(nrm * std::sqrt(2.0 / fan_in));
+    }
+  };
+  fill(OFF_W1, 432, 27);
+  fill(OFF_W2, 2304, 144);
+  fill(OFF_W3, 144, 144);
+  vf_status st = vf_gate_set_params(g, h.data(), NPARAM);
+  if (st != VF_OK) {
+    vf_gate_destroy(g);
+    return st;
+  }
+  *out = g;
+  return VF_OK;
+}
+
+vf_status vf_gate_set_params(vf_gate* g, const float* params, int n) {
+  if (!g || !params || n != NPARAM) return VF_ERR_ARG;
+  cudaError_t e = cudaMemcpy(g->theta, params, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(g->m, 0, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMemset(g->v, 0, NPARAM * 4);
+  if (e == cudaSuccess) {
+    to_bf16<<<(NPARAM + 255) / 256, 256>>>(g->theta, g->wb);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  g->step = 0;
+  return VF_OK;
+}
+
+vf_status vf_gate_get_params(vf_gate* g, float* params, int n) {
+  if (!g || !params || n != NPARAM) return VF_ERR_ARG;
+  cudaError_t e = cudaMemcpy(params, g->theta, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+vf_status vf_gate_gradient(vf_gate* g, const uint8_t* d_imgs, const uint8_t* d_targets, int count,
+                           int height, int width, int channels, size_t pitch, float* d_grad,
+                           float* d_loss, float* d_prob, void* stream) {
+  if (!g || !d_targets) return VF_ERR_ARG;
+  Images I;
+  vf_status st = check_images(g, d_imgs, count, height, width, channels, pitch, &I);
+  if (st != VF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = run_train(g, I, d_targets, s, d_loss, d_prob);
+  if (st != VF_OK) return st;
+  if (d_grad) {
+    cudaError_t e = cudaMemcpyAsync(d_grad, g->grad, NPARAM * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return VF_OK;
+}
+
+vf_status vf_gate_train_step(vf_gate* g, const uint8_t* d_imgs, const uint8_t* d_targets,
+                             int count, int height, int width, int channels, size_t pitch,
+                             float lr, float* d_loss, void* stream) {
+  if (!g || !d_targets || !(lr > 0.0f)) return VF_ERR_ARG;
+  Images I;
+  vf_status st = check_images(g, d_imgs, count, height, width, channels, pitch, &I);
+  if (st != VF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = run_train(g, I, d_targets, s, d_loss, nullptr);
+  if (st != VF_OK) return st;
+  g->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - (float)std::pow((double)b1, (double)g->step);
+  const float c2 = 1.0f - (float)std::pow((double)b2, (double)g->step);
+  adam<<<(NPARAM + 255) / 256, 256, 0, s>>>(g->theta, g->m, g->v, g->grad, g->wb, lr, b1, b2,
+                                            1e-8f, c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, int channels,
+                        size_t pitch, float threshold, uint8_t* d_flags, size_t flag_pitch,
+                        float* d_prob, void* stream) {
+  if (!g) return VF_ERR_ARG;
+  if (!d_flags && !d_prob) return set_error(g->ctx, VF_ERR_ARG, "no output");
+  if (!(threshold > 0.0f && threshold < 1.0f))
+    return set_error(g->ctx, VF_ERR_ARG, "threshold must be in (0, 1)");
+  if (d_flags && flag_pitch < (size_t)width) return set_error(g->ctx, VF_ERR_ARG, "flag pitch");
+  Images I;
+  vf_status st = check_images(g, d_in, 1, height, width, channels, pitch, &I);
+  if (st != VF_OK) return st;
+  const int tiles_x = (width + IX - 1) / IX, tiles_y = (height + IY - 1) / IY;
+  static_assert(kInferSmem <= 200 * 1024, "inference tile fits in shared memory");
+  cudaError_t e = cudaFuncSetAttribute(gate_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kInferSmem);
+  if (e == cudaSuccess) {
+    const float thr = std::log(threshold / (1.0f - threshold));
+    gate_infer<<<tiles_x * tiles_y, IX * IY, kInferSmem, (cudaStream_t)stream>>>(
+        I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
+                          int channels, size_t in_pitch, size_t out_pitch, const uint8_t* d_flags,
+                          size_t flag_pitch, const vf_params* p, void* stream,
+                          unsigned long long* d_stats) {
+  if (!ctx) return VF_ERR_ARG;
+  if (!d_flags || flag_pitch < (size_t)width) return set_error(ctx, VF_ERR_ARG, "bad flags");
+  Launch L;
+  LaunchClass cls;
+  vf_status st = prepare_launch(ctx, d_in, d_out, height, width, channels, in_pitch, out_pitch, p,
+                                d_stats, &L, &cls);
+  if (st != VF_OK) return st;
+  if (cls.crit == kEVMF || cls.precision != VF_FP32)
+    return set_error(ctx, VF_ERR_UNSUPPORTED, "the gated form runs VMF, BVDF and AMNF in FP32");
+  const int ty = 4;
+  L.tiles_x = (width + kTX - 1) / kTX;
+  const long long grid = (long long)L.tiles_x * ((height + ty - 1) / ty);
+  if (grid > 0x7fffffffLL) return set_error(ctx, VF_ERR_UNSUPPORTED, "image too large");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  switch (cls.w) {
+    case 3: e = launch_gated_w3(L, d_flags, (long long)flag_pitch, cls.crit, cls.apx, cls.deg, ty, (int)grid, s); break;
+    case 5: e = launch_gated_w5(L, d_flags, (long long)flag_pitch, cls.crit, cls.apx, cls.deg, ty, (int)grid, s); break;
+    default: e = launch_gated_w7(L, d_flags, (long long)flag_pitch, cls.crit, cls.apx, cls.deg, ty, (int)grid, s); break;
+  }
+  if (e != cudaSuccess) return set_error(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+vf_status vf_gate_save(vf_gate* g, const char* path) {
+  if (!g || !path) return VF_ERR_ARG;
+  std::vector<float> buf(3 * NPARAM);
+  cudaError_t e = cudaMemcpy(buf.data(), g->theta, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(buf.data() + NPARAM, g->m, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(buf.data() + 2 * NPARAM, g->v, NPARAM * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  std::vector<unsigned char> out;
+  auto put = [&](const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    out.insert(out.end(), c, c + n);
+  };
+  const char magic[8] = {'V', 'F', 'G', 'A', 'T', 'E', '0', '1'};
+  const uint32_t version = 1, n = NPARAM;
+  put(magic, 8);
+  put(&version, 4);
+  put(&n, 4);
+  put(&g->step, 8);
+  put(&g->seed, 8);
+  put(buf.data(), buf.size() * 4);
+  const uint32_t crc = crc32(out.data(), out.size());
+  put(&crc, 4);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error(g->ctx, VF_ERR_ARG, "cannot open checkpoint for writing");
+  const size_t w = std::fwrite(out.data(), 1, out.size(), f);
+  const int rc = std::fclose(f);
+  if (w != out.size() || rc != 0) return set_error(g->ctx, VF_ERR_ARG, "checkpoint write failed");
+  return VF_OK;
+}
+
+vf_status vf_gate_load(vf_gate* g, const char* path) {
+  if (!g || !path) return VF_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(g->ctx, VF_ERR_ARG, "cannot open checkpoint");
+  std::vector<unsigned char> in;
+  unsigned char chunk[65536];
+  size_t r;
+  while ((r = std::fread(chunk, 1, sizeof(chunk), f)) > 0) in.insert(in.end(), chunk, chunk + r);
+  std::fclose(f);
+  const size_t expect = 8 + 4 + 4 + 8 + 8 + (size_t)3 * NPARAM * 4 + 4;
+  if (in.size() != expect || std::memcmp(in.data(), "VFGATE01", 8) != 0)
+    return set_error(g->ctx, VF_ERR_ARG, "not a gate checkpoint");
+  uint32_t version, n, crc;
+  std::memcpy(&version, in.data() + 8, 4);
+  std::memcpy(&n, in.data() + 12, 4);
+  std::memcpy(&crc, in.data() + expect - 4, 4);
+  if (version != 1 || n != NPARAM) return set_error(g->ctx, VF_ERR_ARG, "checkpoint version");
+  if (crc32(in.data(), expect - 4) != crc) return set_error(g->ctx, VF_ERR_ARG, "checkpoint CRC");
+  unsigned long long step, seed;
+  std::memcpy(&step, in.data() + 16, 8);
+  std::memcpy(&seed, in.data() + 24, 8);
+  const float* buf = (const float*)(in.data() + 32);
+  cudaError_t e = cudaMemcpy(g->theta, buf, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->m, buf + NPARAM, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->v, buf + 2 * NPARAM, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    to_bf16<<<(NPARAM + 255) / 256, 256>>>(g->theta, g->wb);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  g->step = step;
+  g->seed = seed;
+  return VF_OK;
+}
+
+unsigned long long vf_gate_step_count(const vf_gate* g) { return g ? g->step : 0; }
+
+void vf_gate_destroy(vf_gate* g) {
+  if (!g) return;
+  free_scratch(g);
+  for (void* p : {(void*)g->theta, (void*)g->m, (void*)g->v, (void*)g->grad, (void*)g->wb,
+                  (void*)g->part})
+    if (p) cudaFree(p);
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Gated window filters, 3 x 3 window.
+#include "vf_gated.cuh"
+
+namespace vf {
+cudaError_t launch_gated_w3(const Launch& L, const uint8_t* flags, long long flag_pitch,
+                             int crit, int apx, int degree, int ty, int grid, cudaStream_t s) {
+  return launch_gated_w<3>(L, GateFlags{flags, flag_pitch}, crit, apx, degree, ty, grid, s);
+}
+}  // namespace vf

@@ -181,6 +181,13 @@ def noisy(h: int, w: int, p: float, seed: int, model: str = "uncorrelated"):
     raise ValueError(model)
 
 
+def impulse_mask(clean: np.ndarray, noisy: np.ndarray, threshold: int = 12) -> np.ndarray:
+    """uint8 H x W: 1 where some channel of the noisy pixel differs from the
+    clean one by more than `threshold` levels (a visible impulse)."""
+    d = np.abs(noisy[..., :3].astype(np.int16) - clean[..., :3].astype(np.int16))
+    return (d.max(axis=-1) > threshold).astype(np.uint8)
+
+
 def to_rgbx(img: np.ndarray) -> np.ndarray:
     """H x W x 3 -> H x W x 4 with the fourth byte 0 (the device layout)."""
     h, w, _ = img.shape

@@ -94,6 +94,29 @@ def lib():
             L.vf_batch_destroy.restype = None
             L.vf_batch_run_static.argtypes = [P, P, I, P]
             L.vf_batch_run_static.restype = I
+            L.vf_gate_create.argtypes = [P, ctypes.c_ulonglong, ctypes.POINTER(P)]
+            L.vf_gate_create.restype = I
+            L.vf_gate_set_params.argtypes = [P, P, I]
+            L.vf_gate_set_params.restype = I
+            L.vf_gate_get_params.argtypes = [P, P, I]
+            L.vf_gate_get_params.restype = I
+            L.vf_gate_gradient.argtypes = [P, P, P, I, I, I, I, S, P, P, P, P]
+            L.vf_gate_gradient.restype = I
+            L.vf_gate_train_step.argtypes = [P, P, P, I, I, I, I, S, ctypes.c_float, P, P]
+            L.vf_gate_train_step.restype = I
+            L.vf_gate_infer.argtypes = [P, P, I, I, I, S, ctypes.c_float, P, S, P, P]
+            L.vf_gate_infer.restype = I
+            L.vf_filter_gated.argtypes = [P, P, P, I, I, I, S, S, P, S, ctypes.POINTER(Params), P,
+                                          P]
+            L.vf_filter_gated.restype = I
+            L.vf_gate_save.argtypes = [P, ctypes.c_char_p]
+            L.vf_gate_save.restype = I
+            L.vf_gate_load.argtypes = [P, ctypes.c_char_p]
+            L.vf_gate_load.restype = I
+            L.vf_gate_step_count.argtypes = [P]
+            L.vf_gate_step_count.restype = ctypes.c_ulonglong
+            L.vf_gate_destroy.argtypes = [P]
+            L.vf_gate_destroy.restype = None
             _lib = L
         return _lib
 
@@ -241,6 +264,113 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+GATE_NPARAM = 2913
+
+
+class Gate:
+    """vf_gate: the learned impulse detector (training, inference, checkpoints)."""
+
+    def __init__(self, seed: int = 0):
+        self.ctx = context()
+        self.handle = ctypes.c_void_p()
+        _check(lib().vf_gate_create(self.ctx, int(seed), ctypes.byref(self.handle)), self.ctx)
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    @staticmethod
+    def _batch(imgs):
+        """imgs: B x H x W x C uint8 CUDA tensor (dense)."""
+        if imgs.dim() != 4 or not imgs.is_cuda or not imgs.is_contiguous():
+            raise ValueError("expected a dense B x H x W x C uint8 CUDA tensor")
+        B, H, W, C = imgs.shape
+        return imgs.data_ptr(), int(B), int(H), int(W), int(C), int(W * C)
+
+    def set_params(self, params):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().vf_gate_set_params(self.handle, a.ctypes.data, a.size), self.ctx)
+
+    def get_params(self):
+        import numpy as np
+        a = np.zeros(GATE_NPARAM, dtype=np.float32)
+        _check(lib().vf_gate_get_params(self.handle, a.ctypes.data, a.size), self.ctx)
+        return a
+
+    def gradient(self, imgs, targets, stream=None):
+        """(grad, loss, prob) tensors of the mean BCE on a batch (device)."""
+        import torch
+        p, B, H, W, C, pitch = self._batch(imgs)
+        grad = torch.zeros(GATE_NPARAM, dtype=torch.float32, device=imgs.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=imgs.device)
+        prob = torch.zeros((B, H, W), dtype=torch.float32, device=imgs.device)
+        _check(lib().vf_gate_gradient(self.handle, p, targets.data_ptr(), B, H, W, C, pitch,
+                                      grad.data_ptr(), loss.data_ptr(), prob.data_ptr(),
+                                      self._stream(stream)), self.ctx)
+        return grad, loss, prob
+
+    def train_step(self, imgs, targets, lr, loss=None, stream=None):
+        p, B, H, W, C, pitch = self._batch(imgs)
+        _check(lib().vf_gate_train_step(self.handle, p, targets.data_ptr(), B, H, W, C, pitch,
+                                        float(lr), loss.data_ptr() if loss is not None else None,
+                                        self._stream(stream)), self.ctx)
+
+    def infer(self, img, threshold=0.5, flags=None, prob=None, stream=None):
+        """Fused inference on one H x W x C image: flags (uint8) and/or prob."""
+        import torch
+        ip, h, w, c, pitch = _image_args(img)
+        if flags is None and prob is None:
+            flags = torch.empty((h, w), dtype=torch.uint8, device=img.device)
+        _check(lib().vf_gate_infer(self.handle, ip, h, w, c, pitch, float(threshold),
+                                   flags.data_ptr() if flags is not None else None,
+                                   flags.stride(0) if flags is not None else 0,
+                                   prob.data_ptr() if prob is not None else None,
+                                   self._stream(stream)), self.ctx)
+        return flags if prob is None else (flags, prob)
+
+    def save(self, path):
+        _check(lib().vf_gate_save(self.handle, str(path).encode()), self.ctx)
+
+    def load(self, path):
+        _check(lib().vf_gate_load(self.handle, str(path).encode()), self.ctx)
+
+    @property
+    def step(self):
+        return lib().vf_gate_step_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib().vf_gate_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def filter_gated(inp, flags, out=None, *, stream=None, stats=None, **params):
+    """vf_filter_gated: the window filter on flagged pixels, a copy elsewhere."""
+    import torch
+    if out is None:
+        out = torch.empty_like(inp)
+    ip, h, w, c, ipitch = _image_args(inp)
+    op, _, _, _, opitch = _image_args(out)
+    if flags.dtype != torch.uint8 or tuple(flags.shape) != (h, w) or flags.stride(1) != 1:
+        raise ValueError("flags must be an H x W uint8 tensor with unit column stride")
+    p = make_params(**params)
+    s = stream if stream is not None else torch.cuda.current_stream(inp.device)
+    ctx = context()
+    _check(lib().vf_filter_gated(ctx, ip, op, h, w, c, ipitch, opitch, flags.data_ptr(),
+                                 flags.stride(0), ctypes.byref(p), ctypes.c_void_p(s.cuda_stream),
+                                 stats.data_ptr() if stats is not None else None), ctx)
+    return out
 
 
 STATIC_MAX_IMAGES = 256

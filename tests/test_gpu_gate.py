@@ -1,0 +1,151 @@
+"""The learned impulse gate: gradients and forward against the FP64 oracle
+(oracle/gate.py), deterministic and resumable training, the gated filter, and
+what the trained gate gains over the plain filter."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import gate as G  # noqa: E402
+from oracle import metrics as M  # noqa: E402
+from paper_1009_0959_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_0959_gb300 import build, vfilt
+    build.build()
+    return vfilt
+
+
+def batch(n, h, w, seed, p_lo=0.05, p_hi=0.3):
+    imgs, tgts = [], []
+    for k in range(n):
+        p = p_lo + (p_hi - p_lo) * k / max(n - 1, 1)
+        clean, noisy = synth.noisy(h, w, p, seed * 100 + k)
+        imgs.append(synth.to_rgbx(noisy))
+        tgts.append(synth.impulse_mask(clean, noisy))
+    return np.stack(imgs), np.stack(tgts)
+
+
+def test_gradient_and_forward_match_oracle(vf):
+    """Same BF16-rounded weights on both sides; the GPU accumulates in FP32."""
+    imgs, tgts = batch(2, 19, 27, 1)
+    theta = G.init(3)
+    theta[G.NPARAM - 17:G.NPARAM] += 0.05  # non-zero biases
+    theta32 = theta.astype(np.float32)
+    gate = vf.Gate()
+    gate.set_params(theta32)
+    grad, loss, prob = gate.gradient(torch.from_numpy(imgs).cuda(), torch.from_numpy(tgts).cuda())
+    torch.cuda.synchronize()
+    wq = G.bf16_round(theta32.astype(np.float64))
+    caches = [G.forward(imgs[k], wq) for k in range(2)]
+    ts = [tgts[k].astype(np.float64) for k in range(2)]
+    ref_g = G.backward(caches, ts, wq)
+    np.testing.assert_allclose(loss.item(), G.loss(caches, ts), rtol=1e-5)
+    np.testing.assert_allclose(prob.cpu().numpy(), np.stack([c["p"] for c in caches]), atol=2e-6)
+    g = grad.cpu().numpy()
+    np.testing.assert_allclose(g, ref_g, rtol=2e-3, atol=2e-5 * np.abs(ref_g).max())
+    # fused inference = training forward
+    for k in range(2):
+        t = torch.from_numpy(imgs[k]).cuda()
+        _, pr = gate.infer(t, 0.5, prob=torch.empty((19, 27), device="cuda"))
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(pr.cpu().numpy(), caches[k]["p"], atol=2e-6)
+        fl = gate.infer(t, 0.5)
+        torch.cuda.synchronize()
+        sure = np.abs(caches[k]["p"] - 0.5) > 1e-4
+        np.testing.assert_array_equal(fl.cpu().numpy()[sure], (caches[k]["p"] > 0.5)[sure])
+    gate.close()
+
+
+def _train(vf, gate, imgs, tgts, steps, lr=3e-3, bs=8):
+    ti, tt = torch.from_numpy(imgs).cuda(), torch.from_numpy(tgts).cuda()
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for s in range(steps):
+        k = (s * bs) % len(imgs)
+        gate.train_step(ti[k:k + bs], tt[k:k + bs], lr, loss)
+        losses.append(loss.item())
+    return losses
+
+
+def test_training_deterministic_and_resumable(vf, tmp_path):
+    imgs, tgts = batch(16, 48, 48, 2)
+    a, b, c = vf.Gate(7), vf.Gate(7), vf.Gate(7)
+    la = _train(vf, a, imgs, tgts, 12)
+    lb = _train(vf, b, imgs, tgts, 12)
+    assert la == lb
+    np.testing.assert_array_equal(a.get_params(), b.get_params())
+    assert la[10] < la[0]  # the same batch (k = 0) before and after 10 steps
+    _train(vf, c, imgs, tgts, 6)
+    c.save(tmp_path / "gate.bin")
+    d = vf.Gate(99)
+    d.load(tmp_path / "gate.bin")
+    assert d.step == 6
+    # continue exactly where the 12-step run continued: steps 6..11 use the
+    # same batches as in a
+    ti, tt = torch.from_numpy(imgs).cuda(), torch.from_numpy(tgts).cuda()
+    loss = torch.zeros(1, device="cuda")
+    tail = []
+    for s in range(6, 12):
+        k = (s * 8) % 16
+        d.train_step(ti[k:k + 8], tt[k:k + 8], 3e-3, loss)
+        tail.append(loss.item())
+    assert tail == la[6:]
+    np.testing.assert_array_equal(d.get_params(), a.get_params())
+    # a corrupted checkpoint is rejected
+    raw = bytearray((tmp_path / "gate.bin").read_bytes())
+    raw[100] ^= 1
+    (tmp_path / "bad.bin").write_bytes(bytes(raw))
+    with pytest.raises(vf.VFError):
+        d.load(tmp_path / "bad.bin")
+    for gte in (a, b, c, d):
+        gte.close()
+
+
+def test_gated_filter_identities(vf):
+    clean, noisy = synth.noisy(45, 77, 0.2, 5)
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
+    plain = vf.filter(t, **kw)
+    ones = torch.ones((45, 77), dtype=torch.uint8, device="cuda")
+    zeros = torch.zeros_like(ones)
+    assert torch.equal(vf.filter_gated(t, ones, **kw), plain)
+    assert torch.equal(vf.filter_gated(t, zeros, **kw), t)
+    half = torch.from_numpy((np.arange(45 * 77).reshape(45, 77) % 3 == 0).astype(np.uint8)).cuda()
+    st = torch.zeros(3, dtype=torch.int64, device="cuda")
+    mixed = vf.filter_gated(t, half, stats=st, **kw)
+    torch.cuda.synchronize()
+    m = half.bool().unsqueeze(-1).expand_as(t)
+    assert torch.equal(mixed[m], plain[m]) and torch.equal(mixed[~m], t[~m])
+    assert st[2].item() == int(half.sum().item()) and st[0].item() == 45 * 77
+    for crit in ("vmf", "amnfe"):
+        assert torch.equal(vf.filter_gated(t, ones, criterion=crit, window=3),
+                           vf.filter(t, criterion=crit, window=3))
+
+
+def test_trained_gate_beats_plain_filter(vf):
+    """Trained on the GPU by the library's own kernels, the gate flags the
+    impulses; the gated 5 x 5 minimax BVDF keeps the clean pixels untouched
+    and scores a higher PSNR than the plain filter on held-out images."""
+    imgs, tgts = batch(32, 96, 96, 3)
+    gate = vf.Gate(11)
+    losses = _train(vf, gate, imgs, tgts, 600, lr=1e-2)
+    assert np.mean(losses[-20:]) < 0.4 * np.mean(losses[:5])
+    for p in (0.10, 0.25):
+        clean, noisy = synth.noisy(256, 256, p, 777)
+        t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+        flags = gate.infer(t, 0.5)
+        kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
+        gated = vf.filter_gated(t, flags, **kw).cpu().numpy()
+        plain = vf.filter(t, **kw).cpu().numpy()
+        frac = flags.float().mean().item()
+        truth = synth.impulse_mask(clean, noisy).mean()
+        assert 0.5 * truth < frac < 2.0 * truth + 0.02
+        assert M.psnr(clean, gated) > M.psnr(clean, plain)
+    gate.close()
