@@ -141,6 +141,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the packed-precision measurement")
+    ap.add_argument("--no-gate", action="store_true", help="skip the learned-gate measurement")
     ap.add_argument("--case", default=None,
                     help="profiling: run one kernel, e.g. bvdf/poly4/w5, on a --size image")
     ap.add_argument("--size", type=int, default=6144)
@@ -337,6 +338,8 @@ def main():
         line["batched"] = bench_batch()
     if not args.no_precision:
         line["precision"] = bench_precision()
+    if not args.no_gate:
+        line["gate"] = bench_gate()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs, V, budget_s=15.0)
     if rank == 0:
@@ -460,6 +463,110 @@ def bench_precision(reps=3):
             "ncd_diff": round(M.ncd(crow, g) - M.ncd(crow, r), 6)}
     return {"workload": "4096x4096 RGBX, 20 %% impulses (seed 8), w 5/7; quality on %d rows "
                         "against the FP64 oracle's exact filter" % len(rows), "variants": res}
+
+
+def bench_gate(frames=64, train_steps=800):
+    """Learned-gate form: the gate is trained on the GPU (own kernels) on 48
+    seeded 128 x 128 crops (impulse rate 5..30 %), then gates the 5 x 5
+    degree-4 minimax BVDF over `frames` frames of a panning 3840 x 2160 scene
+    with the impulse rate ramping 5 -> 30 %.  Timed (CUDA events, all frames
+    resident in HBM): the plain filter over every frame, and gate inference +
+    gated filter over every frame.  Quality: PSNR against the clean frames and
+    the fraction of pixels where the gated output differs from the plain one."""
+    import numpy as np
+    import torch
+
+    from paper_1009_0959_gb300 import synth, vfilt
+    t0 = time.perf_counter()
+    imgs, tgts = [], []
+    for k in range(48):
+        p = 0.05 + 0.25 * k / 47
+        clean, noisy = synth.noisy(128, 128, p, 5000 + k)
+        imgs.append(synth.to_rgbx(noisy))
+        tgts.append(synth.impulse_mask(clean, noisy))
+    ti = torch.from_numpy(np.stack(imgs)).cuda()
+    tt = torch.from_numpy(np.stack(tgts)).cuda()
+    gate = vfilt.Gate(265)
+    loss = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    first = None
+    for s in range(train_steps):
+        k = (s * 8) % 48
+        gate.train_step(ti[k:k + 8], tt[k:k + 8], 1e-2, loss)
+        if s == 0:
+            torch.cuda.synchronize()
+            first = loss.item()
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    final = loss.item()
+
+    H, W = 2160, 3840
+    noisy_d, clean_d = [], []
+    for clean, noisy, p in synth.video_frames(frames, H, W, 265):
+        noisy_d.append(torch.from_numpy(synth.to_rgbx(noisy)).cuda())
+        clean_d.append(torch.from_numpy(clean).cuda())
+    gen_s = time.perf_counter() - t0
+    out_plain = [torch.empty_like(noisy_d[0]) for _ in range(2)]
+    out_gated = [torch.empty_like(noisy_d[0]) for _ in range(2)]
+    flags = [torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for f, x in enumerate(noisy_d):
+            vfilt.filter(x, out_plain[f & 1], stream=stream, **kw)
+
+    def gate_only():
+        for f, x in enumerate(noisy_d):
+            gate.infer(x, 0.5, flags=flags[f & 1], stream=stream)
+
+    def gated():
+        for f, x in enumerate(noisy_d):
+            gate.infer(x, 0.5, flags=flags[f & 1], stream=stream)
+            vfilt.filter_gated(x, flags[f & 1], out_gated[f & 1], stream=stream, **kw)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    ms_plain, ms_gate, ms_gated = timed(plain), timed(gate_only), timed(gated)
+    # quality, untimed
+    ps_plain, ps_gated, differ, flagged = [], [], [], []
+    for f, x in enumerate(noisy_d):
+        op = vfilt.filter(x, **kw)
+        fl = gate.infer(x, 0.5)
+        og = vfilt.filter_gated(x, fl, **kw)
+        c = clean_d[f].float()
+        for o, acc in ((op, ps_plain), (og, ps_gated)):
+            mse = ((o[..., :3].float() - c) ** 2).mean().item()
+            acc.append(10 * math.log10(255 ** 2 / mse))
+        differ.append((og[..., :3] != op[..., :3]).any(-1).float().mean().item())
+        flagged.append(fl.float().mean().item())
+    gate.close()
+    mpix = frames * H * W / 1e6
+    return {"workload": "%d frames 3840x2160 panning scene (seed 265), impulses 5 -> 30 %%, "
+                        "gate + 5x5 minimax BVDF (degree 4)" % frames,
+            "train": {"steps": train_steps, "batch": "8 x 128x128", "ms": round(train_ms, 1),
+                      "loss_first": round(first, 4), "loss_last": round(final, 4)},
+            "plain_ms": round(ms_plain, 2), "plain_mpix_s": round(mpix / ms_plain * 1e3, 1),
+            "gate_infer_ms": round(ms_gate, 2),
+            "gate_infer_mpix_s": round(mpix / ms_gate * 1e3, 1),
+            "gated_ms": round(ms_gated, 2), "gated_mpix_s": round(mpix / ms_gated * 1e3, 1),
+            "speedup_gated_vs_plain": round(ms_plain / ms_gated, 3),
+            "flagged_fraction_mean": round(float(np.mean(flagged)), 4),
+            "psnr_plain_db_mean": round(float(np.mean(ps_plain)), 3),
+            "psnr_gated_db_mean": round(float(np.mean(ps_gated)), 3),
+            "gated_differs_from_plain_mean": round(float(np.mean(differ)), 4),
+            "frames_generated_s": round(gen_s, 1), "gpu_launches_gated": 2 * frames}
 
 
 def run_case(args):

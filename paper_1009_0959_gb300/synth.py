@@ -231,6 +231,31 @@ def batch_images(count: int, seed: int, lo=(240, 320), hi=(1080, 1920), p_lo: fl
         return list(ex.map(one, range(count)))
 
 
+def video_frames(count: int, h: int, w: int, seed: int, pan: int = 4, p_lo: float = 0.05,
+                 p_hi: float = 0.30):
+    """Iterator over `count` frames (clean, noisy, p) of one slowly panning
+    scene (pan pixels per frame, made once), uncorrelated impulses at a rate
+    ramping from p_lo to p_hi.  Frames are made ahead on a thread pool."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    scene = piecewise_smooth(h, w + pan * max(count - 1, 0), seed)
+
+    def one(f):
+        clean = np.ascontiguousarray(scene[:, pan * f:pan * f + w])
+        p = p_lo + (p_hi - p_lo) * (f / max(count - 1, 1))
+        return clean, impulse_uncorrelated(clean, p, seed * 1000 + f + 1), p
+
+    with ThreadPoolExecutor(min(8, os.cpu_count() or 1)) as ex:
+        pending = [ex.submit(one, f) for f in range(min(count, 8))]
+        for f in range(count):
+            item = pending[f].result()
+            pending[f] = None
+            if f + 8 < count:
+                pending.append(ex.submit(one, f + 8))
+            yield item
+
+
 def video_frame(h: int, w: int, frame: int, frames: int, seed: int, pan: int = 4,
                 p_lo: float = 0.05, p_hi: float = 0.30):
     """Frame `frame` of a slowly panning scene (pan pixels per frame) with
