@@ -102,6 +102,17 @@ void vf_destroy(vf_ctx* ctx);
 const char* vf_status_string(vf_status s);
 const char* vf_last_error(const vf_ctx* ctx);
 
+/* Context options (execution choices; results agree within the parity bar).
+ *   VF_OPT_PAIR_REUSE  pair-reuse kernels (each pairwise term computed once
+ *                      per 32 x 8 tile and shared by every window holding the
+ *                      pair), for FP32 VMF, BVDF, AMNFE, AMNFG with 3 x 3 and
+ *                      5 x 5 windows: 0 never (per-window kernels), 1 where
+ *                      they are faster (default: BVDF), 2 always.
+ *   VF_OPT_TILE_ROWS   rows of the per-window kernels' 32 x TY tiles: 2, 4
+ *                      (default) or 8. */
+typedef enum { VF_OPT_PAIR_REUSE = 0, VF_OPT_TILE_ROWS = 1 } vf_option;
+vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value);
+
 /* window 3, VF_VMF, VF_EXACT, degree 4, FP32, kappa 0.33, exp_cutoff 10,
  * ent_cutoff -1 (the window's default). */
 void vf_default_params(vf_params* p);

@@ -47,7 +47,8 @@ struct FitVal {
 struct vf_ctx {
   std::map<FitKey, FitVal> fits;
   std::string last_error;
-  int tile_rows = 4;  // TY of the single-image launches
+  int tile_rows = 4;  // TY of the per-window single-image launches
+  int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF), 2 always (w = 3 / 5)
   // device staging of vf_filter_host (grown on demand, freed by vf_destroy)
   uint8_t* d_stage = nullptr;
   size_t stage_bytes = 0;
@@ -106,6 +107,21 @@ const char* vf_status_string(vf_status s) {
 }
 
 const char* vf_last_error(const vf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value) {
+  if (!ctx) return VF_ERR_ARG;
+  switch (opt) {
+    case VF_OPT_PAIR_REUSE:
+      if (value < 0 || value > 2) return fail(ctx, VF_ERR_ARG, "pair reuse 0, 1 or 2");
+      ctx->pair_reuse = value;
+      return VF_OK;
+    case VF_OPT_TILE_ROWS:
+      if (value != 2 && value != 4 && value != 8) return fail(ctx, VF_ERR_ARG, "tile rows 2, 4 or 8");
+      ctx->tile_rows = value;
+      return VF_OK;
+  }
+  return fail(ctx, VF_ERR_ARG, "unknown option");
+}
 
 void vf_default_params(vf_params* p) {
   if (!p) return;
@@ -266,13 +282,23 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
   vf_status st = prepare_launch(ctx, d_in, d_out, height, width, channels, in_pitch, out_pitch, p,
                                 d_stats, &L, &cls);
   if (st != VF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool reuse = ctx->pair_reuse == 2 ? has_reuse_kernel(cls.w, cls.crit)
+                                           : (ctx->pair_reuse == 1 && reuse_pays(cls.w, cls.crit));
+  if (cls.precision == VF_FP32 && reuse) {
+    L.tiles_x = (width + kTX - 1) / kTX;
+    const long long rgrid = (long long)L.tiles_x * ((height + kReuseTileRows - 1) / kReuseTileRows);
+    if (rgrid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
+    cudaError_t e = launch_reuse(L, cls.crit, cls.w, cls.apx, cls.deg, (int)rgrid, s);
+    if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    return VF_OK;
+  }
   const int ty = ctx->tile_rows;
   const int cols = cls.precision == VF_FP32 ? kTX : kPackedTileCols;
   L.tiles_x = (width + cols - 1) / cols;
   const int tiles_y = (height + ty - 1) / ty;
   const long long grid = (long long)L.tiles_x * tiles_y;
   if (grid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cls.precision == VF_FP32
                       ? launch_filter(L, cls.crit, cls.w, cls.apx, cls.deg, ty, (int)grid, s)
                       : launch_packed(L, cls.precision, cls.crit, cls.w, cls.apx, cls.deg, ty,

@@ -25,6 +25,16 @@ cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int
 
 #undef VF_CASE
 
+cudaError_t launch_reuse(const Launch& L, int crit, int w, int apx, int degree, int grid,
+                         cudaStream_t s) {
+  const bool amnf = crit == kAMNFE || crit == kAMNFG;
+  if (w == 3) return amnf ? launch_reuse_amnf_w3(L, crit, apx, degree, grid, s)
+                          : launch_reuse_sel_w3(L, crit, apx, degree, grid, s);
+  if (w == 5) return amnf ? launch_reuse_amnf_w5(L, crit, apx, degree, grid, s)
+                          : launch_reuse_sel_w5(L, crit, apx, degree, grid, s);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_packed(const Launch& L, int precision, int criterion, int w, int approx,
                           int degree, int ty, int grid, cudaStream_t s) {
   if (precision == 1) {

@@ -1,0 +1,279 @@
+// vf_reuse.cuh -- window kernels that compute every pairwise term once per
+// tile instead of once per window (cross-window reuse).
+//
+// A pair of pixels (p, q) with |p - q| <= w - 1 (per axis) belongs to every
+// window that contains both, up to w^2 of them; the per-window kernel
+// computes it in each.  Here a CTA of 32 x 8 outputs stages its
+// (32 + w - 1) x (8 + w - 1) region once, then
+//   1. term table: for every region pixel p and each of the 2w(w-1) offsets
+//      delta of the forward half-plane (dy > 0, or dy = 0 and dx > 0) with
+//      p + delta in the region, T[delta][p] = term(x_p, x_{p+delta});
+//   2. aggregates: every region pixel p forms, for each window c containing p,
+//      agg(c, p) = sum_{q in W(c)} term(p, q) as separable box sums of its
+//      distance field D_p(delta) (T[delta][p] or T[-delta][p + delta], 0 at
+//      delta = 0) over the (2w-1)^2 offsets: row sums of width w, then column
+//      sums of height w.  Only additions (no differences of prefix sums, so no
+//      cancellation);
+//   3. every output thread reads the n aggregates of its window and selects
+//      (argmin, lowest index) or weights (AMNF), as the per-window kernel.
+// Work per output pixel: 2w(w-1) terms x (region / tile) instead of
+// n(n-1)/2, plus O(w^3) additions.  The aggregates are the same sums in
+// another order (FP32, relative differences of a few 1e-7).
+#pragma once
+
+#include "vf_kernels.cuh"
+
+namespace vf {
+
+constexpr int kRTX = 32, kRTY = 8;  // outputs per reuse tile
+
+template <int W>
+struct ReuseGeom {
+  static constexpr int R = W / 2;
+  static constexpr int RX = kRTX + W - 1;     // region columns
+  static constexpr int RY = kRTY + W - 1;     // region rows
+  static constexpr int NR = RX * RY;          // region pixels
+  static constexpr int N = W * W;             // window samples
+  static constexpr int M = W - 1;             // largest offset per axis
+  static constexpr int ND = M * (2 * M + 1) + M;  // forward half-plane offsets = 2w(w-1)
+  static constexpr int THREADS = kRTX * kRTY;
+};
+
+inline size_t reuse_smem_bytes(int w) {
+  size_t rx = kRTX + w - 1, ry = kRTY + w - 1, nr = rx * ry, m = w - 1;
+  size_t nd = m * (2 * m + 1) + m;
+  return nr * 20 + nd * nr * 4 + (size_t)w * w * kRTX * kRTY * 4;
+}
+
+// index of forward offset (dy, dx): dy = 0 -> dx - 1; dy > 0 -> M + (dy-1)(2M+1) + dx + M
+template <int W>
+__host__ __device__ constexpr int fwd_index(int dy, int dx) {
+  return dy == 0 ? dx - 1 : (W - 1) + (dy - 1) * (2 * (W - 1) + 1) + dx + (W - 1);
+}
+
+template <int W, int CRIT, int APX, int DEG>
+__global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_constant__ Launch L) {
+  using G = ReuseGeom<W>;
+  constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, N = G::N, M = G::M, ND = G::ND;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* px = reinterpret_cast<float4*>(smem);
+  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
+  float* T = reinterpret_cast<float*>(smem + NR * 20);   // [ND][NR]
+  float* A = T + ND * NR;                                  // [N][THREADS]
+  const int tile = blockIdx.x;
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  const int x0 = txi * kRTX, y0 = tyi * kRTY;
+
+  TileSmem t;
+  t.px = px;
+  t.raw = raw;
+  t.sw = RX;
+  t.sh = RY;
+  stage_tile<CRIT>(L, t, x0, y0, R);
+  __syncthreads();
+
+  // 1. term table, one region pixel per thread and pass
+  for (int p = threadIdx.x; p < NR; p += G::THREADS) {
+    const int r = p / RX, c = p - r * RX;
+    const float4 xp = px[p];
+    if constexpr (CRIT == kVMF) {
+      TermL2 term;
+#pragma unroll
+      for (int dy = 0; dy <= M; ++dy)
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          if (dy == 0 && dx <= 0) continue;
+          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
+            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
+        }
+    } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+      TermL1 term;
+#pragma unroll
+      for (int dy = 0; dy <= M; ++dy)
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          if (dy == 0 && dx <= 0) continue;
+          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
+            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
+        }
+    } else if constexpr (APX == kExact) {
+      TermAngleExact term;
+#pragma unroll 1
+      for (int dy = 0; dy <= M; ++dy)
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          if (dy == 0 && dx <= 0) continue;
+          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
+            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
+        }
+    } else {
+      TermAngleApprox<DEG> term(L.c.a, L.c.b);
+#pragma unroll 1
+      for (int dy = 0; dy <= M; ++dy)
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          if (dy == 0 && dx <= 0) continue;
+          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
+            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
+        }
+    }
+  }
+  __syncthreads();
+
+  // 2. box sums of each region pixel's distance field, scattered to the
+  //    windows of this tile that contain it
+  for (int p = threadIdx.x; p < NR; p += G::THREADS) {
+    const int r = p / RX, c = p - r * RX;
+    float agg[W][W];  // [ey + R][ex + R]: window centred at p + (ey, ex)
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+      for (int j = 0; j < W; ++j) agg[i][j] = 0.0f;
+#pragma unroll
+    for (int dy = -M; dy <= M; ++dy) {
+      float d[2 * M + 1];
+#pragma unroll
+      for (int dx = -M; dx <= M; ++dx) {
+        const int rq = r + dy, cq = c + dx;
+        const bool in = rq >= 0 && rq < RY && cq >= 0 && cq < RX;
+        float v = 0.0f;
+        if (dy == 0 && dx == 0) {
+          v = 0.0f;
+        } else if (dy > 0 || (dy == 0 && dx > 0)) {
+          if (in) v = T[fwd_index<W>(dy, dx) * NR + p];
+        } else {
+          if (in) v = T[fwd_index<W>(-dy, -dx) * NR + rq * RX + cq];
+        }
+        d[dx + M] = v;
+      }
+      // row sums of width w at the 2R+1 window columns ex
+      float h[W];
+#pragma unroll
+      for (int ex = -R; ex <= R; ++ex) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = ex - R; k <= ex + R; ++k) s += d[k + M];
+        h[ex + R] = s;
+      }
+      // column accumulation: window rows ey with |dy - ey| <= R
+#pragma unroll
+      for (int ey = -R; ey <= R; ++ey) {
+        if (dy < ey - R || dy > ey + R) continue;
+#pragma unroll
+        for (int ex = -R; ex <= R; ++ex) agg[ey + R][ex + R] += h[ex + R];
+      }
+    }
+    // window centred at region (r + ey, c + ex) = output (r + ey - R, c + ex - R)
+#pragma unroll
+    for (int ey = -R; ey <= R; ++ey)
+#pragma unroll
+      for (int ex = -R; ex <= R; ++ex) {
+        const int oy = r + ey - R, ox = c + ex - R;
+        if (oy >= 0 && oy < kRTY && ox >= 0 && ox < kRTX) {
+          const int j = (R - ey) * W + (R - ex);  // p's index in that window
+          A[j * G::THREADS + oy * kRTX + ox] = agg[ey + R][ex + R];
+        }
+      }
+  }
+  __syncthreads();
+
+  // 3. selection / weighting per output
+  const int ox = threadIdx.x % kRTX, oy = threadIdx.x / kRTX;
+  const int gx = x0 + ox, gy = y0 + oy;
+  const bool valid = gx < L.width && gy < L.height;
+  const float* sagg = A + threadIdx.x;
+  int ties = 0;
+  if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+    const float4 xc = px[(oy + R) * RX + ox + R];
+    const uint32_t rawc = raw[(oy + R) * RX + ox + R];
+    uint32_t v = rawc;
+    if (sagg[(N / 2) * G::THREADS] != 0.0f) {  // not a constant window
+      float wsum = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float4 xi = px[(oy + i / W) * RX + ox + i % W];
+        const float rh = rcp_approx(L.kappa_scale * sagg[i * G::THREADS]);
+        const float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
+        float u;
+        if constexpr (CRIT == kAMNFE) {
+          u = (fabsf(dx) + fabsf(dy) + fabsf(dz)) * rh;
+        } else {
+          u = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (rh * rh);
+        }
+        const float wi = (rh * rh * rh) * expneg<APX, DEG>(L, u);
+        wsum += wi;
+        ax = fmaf(wi, xi.x, ax);
+        ay = fmaf(wi, xi.y, ay);
+        az = fmaf(wi, xi.z, az);
+      }
+      const float rw = 1.0f / wsum;
+      const float yx = ax * rw, yy = ay * rw, yz = az * rw;
+      if (L.stats) {
+        auto g = [](float q) { return fabsf(q - floorf(q) - 0.5f); };
+        ties = fminf(g(yx), fminf(g(yy), g(yz))) < 1e-3f;
+      }
+      v = pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
+    }
+    if (valid) store_px(L, gx, gy, v);
+  } else {
+    const Selection s =
+        select_min<W, false>(nullptr, sagg, G::THREADS, px, RX, ox, oy, L.stats != nullptr);
+    if (valid) store_px(L, gx, gy, raw[(oy + s.best / W) * RX + ox + s.best % W]);
+    ties = s.near_tie;
+  }
+  block_stats(L, valid ? 1 : 0, valid ? ties : 0, 0);
+}
+
+template <int W, int CRIT, int APX, int DEG>
+cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
+  const size_t smem = reuse_smem_bytes(W);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  reuse_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
+  return cudaGetLastError();
+}
+
+// VMF and BVDF
+template <int W>
+cudaError_t launch_reuse_sel(const Launch& L, int crit, int apx, int degree, int grid,
+                             cudaStream_t s) {
+  if (crit == kVMF) return launch_reuse_one<W, kVMF, kExact, 0>(L, grid, s);
+  if (crit != kBVDF) return cudaErrorInvalidValue;
+  if (apx == kExact) return launch_reuse_one<W, kBVDF, kExact, 0>(L, grid, s);
+  switch (degree) {
+    case 2: return launch_reuse_one<W, kBVDF, kPoly, 2>(L, grid, s);
+    case 3: return launch_reuse_one<W, kBVDF, kPoly, 3>(L, grid, s);
+    case 4: return launch_reuse_one<W, kBVDF, kPoly, 4>(L, grid, s);
+    case 5: return launch_reuse_one<W, kBVDF, kPoly, 5>(L, grid, s);
+    case 6: return launch_reuse_one<W, kBVDF, kPoly, 6>(L, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int W, int CRIT>
+cudaError_t launch_reuse_amnf_c(const Launch& L, int apx, int degree, int grid, cudaStream_t s) {
+  if (apx == kExact) return launch_reuse_one<W, CRIT, kExact, 0>(L, grid, s);
+  if (apx == kRational) return launch_reuse_one<W, CRIT, kRational, 4>(L, grid, s);
+  switch (degree) {
+    case 2: return launch_reuse_one<W, CRIT, kPoly, 2>(L, grid, s);
+    case 3: return launch_reuse_one<W, CRIT, kPoly, 3>(L, grid, s);
+    case 4: return launch_reuse_one<W, CRIT, kPoly, 4>(L, grid, s);
+    case 5: return launch_reuse_one<W, CRIT, kPoly, 5>(L, grid, s);
+    case 6: return launch_reuse_one<W, CRIT, kPoly, 6>(L, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// AMNFE and AMNFG
+template <int W>
+cudaError_t launch_reuse_amnf(const Launch& L, int crit, int apx, int degree, int grid,
+                              cudaStream_t s) {
+  if (crit == kAMNFE) return launch_reuse_amnf_c<W, kAMNFE>(L, apx, degree, grid, s);
+  if (crit == kAMNFG) return launch_reuse_amnf_c<W, kAMNFG>(L, apx, degree, grid, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace vf

@@ -69,6 +69,8 @@ def lib():
             L.vf_status_string.restype = ctypes.c_char_p
             L.vf_last_error.argtypes = [P]
             L.vf_last_error.restype = ctypes.c_char_p
+            L.vf_set_option.argtypes = [P, I, I]
+            L.vf_set_option.restype = I
             L.vf_default_params.argtypes = [ctypes.POINTER(Params)]
             L.vf_default_params.restype = None
             L.vf_get_approximant.argtypes = [P, I, I, I, ctypes.c_double, ctypes.c_double, P,
@@ -131,6 +133,15 @@ def context():
             raise VFError(st, "vf_create failed")
         _tls.ctx = ctx
     return ctx
+
+
+OPTIONS = {"pair_reuse": 0, "tile_rows": 1}
+
+
+def set_option(name: str, value: int):
+    """vf_set_option on this thread's context."""
+    ctx = context()
+    _check(lib().vf_set_option(ctx, OPTIONS[name], int(value)), ctx)
 
 
 def _check(st: int, ctx):

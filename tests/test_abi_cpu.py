@@ -82,3 +82,15 @@ def test_library_rationals_are_the_papers(vf, golden):
         num, den, eps = vf.get_approximant(fn, "rational")
         assert num == golden[key]["num"] and den == golden[key]["den"]
         assert eps == golden[key]["eps"]
+
+
+def test_options(vf):
+    vf.set_option("pair_reuse", 0)
+    vf.set_option("pair_reuse", 2)
+    vf.set_option("pair_reuse", 1)
+    with pytest.raises(vf.VFError):
+        vf.set_option("pair_reuse", 3)
+    vf.set_option("tile_rows", 8)
+    vf.set_option("tile_rows", 4)
+    with pytest.raises(vf.VFError):
+        vf.set_option("tile_rows", 3)
