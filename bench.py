@@ -578,6 +578,23 @@ def run_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1009_0959_gb300 import synth, vfilt
+    if args.case == "gate/infer":
+        n = args.size
+        tile = synth.to_rgbx(synth.noisy(512, 512, 0.15, 3)[1])
+        img = torch.from_numpy(tile).cuda().repeat((n + 511) // 512, (n + 511) // 512, 1)[:n, :n]
+        img = img.contiguous()
+        gate = vfilt.Gate(1)
+        flags = torch.empty((n, n), dtype=torch.uint8, device="cuda")
+        for _ in range(args.launches):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gate.infer(img, 0.5, flags=flags)
+            e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"case": args.case, "size": n, "ms": round(ms, 4),
+                          "mpix_s": round(n * n / ms / 1e3, 1)}))
+        return 0
     c, a, w = args.case.split("/")
     d = int(a[4:]) if a.startswith("poly") else 4
     a = "poly" if a.startswith("poly") else a
