@@ -72,51 +72,31 @@ __global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_const
   stage_tile<CRIT>(L, t, x0, y0, R);
   __syncthreads();
 
-  // 1. term table, one region pixel per thread and pass
-  for (int p = threadIdx.x; p < NR; p += G::THREADS) {
-    const int r = p / RX, c = p - r * RX;
-    const float4 xp = px[p];
-    if constexpr (CRIT == kVMF) {
-      TermL2 term;
+  // 1. term table.  Work items are (offset row dy, region pixel p): w - 1 or
+  //    2w - 1 terms each, spread over all threads so that they reach the
+  //    barrier together; consecutive threads take consecutive pixels.
+  auto row_terms = [&](const auto& term) {
+    for (int item = threadIdx.x; item < (M + 1) * NR; item += G::THREADS) {
+      const int dy = item / NR, p = item - dy * NR;
+      const int r = p / RX, c = p - r * RX;
+      if (r + dy >= RY) continue;
+      const float4 xp = px[p];
 #pragma unroll
-      for (int dy = 0; dy <= M; ++dy)
-#pragma unroll
-        for (int dx = -M; dx <= M; ++dx) {
-          if (dy == 0 && dx <= 0) continue;
-          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
-            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
-        }
-    } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
-      TermL1 term;
-#pragma unroll
-      for (int dy = 0; dy <= M; ++dy)
-#pragma unroll
-        for (int dx = -M; dx <= M; ++dx) {
-          if (dy == 0 && dx <= 0) continue;
-          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
-            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
-        }
-    } else if constexpr (APX == kExact) {
-      TermAngleExact term;
-#pragma unroll 1
-      for (int dy = 0; dy <= M; ++dy)
-#pragma unroll
-        for (int dx = -M; dx <= M; ++dx) {
-          if (dy == 0 && dx <= 0) continue;
-          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
-            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
-        }
-    } else {
-      TermAngleApprox<DEG> term(L.c.a, L.c.b);
-#pragma unroll 1
-      for (int dy = 0; dy <= M; ++dy)
-#pragma unroll
-        for (int dx = -M; dx <= M; ++dx) {
-          if (dy == 0 && dx <= 0) continue;
-          if (r + dy < RY && c + dx >= 0 && c + dx < RX)
-            T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
-        }
+      for (int dx = -M; dx <= M; ++dx) {
+        if (dy == 0 && dx <= 0) continue;
+        if (c + dx >= 0 && c + dx < RX)
+          T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
+      }
     }
+  };
+  if constexpr (CRIT == kVMF) {
+    row_terms(TermL2{});
+  } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+    row_terms(TermL1{});
+  } else if constexpr (APX == kExact) {
+    row_terms(TermAngleExact{});
+  } else {
+    row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b));
   }
   __syncthreads();
 
