@@ -83,15 +83,19 @@ def conv3x3_grads(x, W, dz):
     return dW, db, dx
 
 
-def forward(img, theta):
-    """img: H x W x 3 (or 4) uint8.  Returns the cache of every layer."""
+def forward(img, theta, act_bf16: bool = False):
+    """img: H x W x 3 (or 4) uint8.  Returns the cache of every layer.
+    act_bf16 rounds every convolution's input (x0, a1, a2) to bfloat16 first,
+    the operand precision of a BF16 tensor-core inference (weights are passed
+    in already rounded; accumulation stays exact here)."""
     p = unflatten(theta)
+    q = bf16_round if act_bf16 else (lambda v: v)
     x0 = np.transpose(np.asarray(img)[..., :3].astype(np.float64) / 255.0 - 0.5, (2, 0, 1))
-    z1 = conv3x3(x0, p["W1"], p["b1"])
+    z1 = conv3x3(q(x0), p["W1"], p["b1"])
     a1 = np.maximum(z1, 0.0)
-    z2 = conv3x3(a1, p["W2"], p["b2"])
+    z2 = conv3x3(q(a1), p["W2"], p["b2"])
     a2 = np.maximum(z2, 0.0)
-    z3 = conv3x3(a2, p["W3"], p["b3"])[0]
+    z3 = conv3x3(q(a2), p["W3"], p["b3"])[0]
     prob = 1.0 / (1.0 + np.exp(-z3))
     return {"x0": x0, "z1": z1, "a1": a1, "z2": z2, "a2": a2, "z3": z3, "p": prob}
 

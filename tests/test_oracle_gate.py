@@ -84,3 +84,15 @@ def test_bf16_round():
     assert r[2] == 1.0 + 2 ** -7                              # rounds up
     assert abs(r[3] + 3.14159) <= 2 ** -7 * 4
     assert abs(r[4] - 1e-3) <= 1e-3 * 2 ** -8
+
+
+def test_bf16_activation_option():
+    """act_bf16 only rounds the convolution inputs: exact for inputs already
+    on the bfloat16 grid, within 2^-8 relative otherwise."""
+    clean, noisy = synth.noisy(6, 6, 0.3, 8)
+    theta = G.bf16_round(G.init(4))
+    a = G.forward(noisy, theta)
+    b = G.forward(noisy, theta, act_bf16=True)
+    assert np.max(np.abs(a["z3"] - b["z3"])) < 0.05 * (1 + np.max(np.abs(a["z3"])))
+    img = np.zeros((4, 5, 3), np.uint8)  # x0 = -0.5 exactly
+    np.testing.assert_array_equal(G.forward(img, theta)["z1"], G.forward(img, theta, True)["z1"])
