@@ -146,6 +146,8 @@ def main():
                     help="profiling: run one kernel, e.g. bvdf/poly4/w5, on a --size image")
     ap.add_argument("--size", type=int, default=6144)
     ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--pair-reuse", type=int, default=1,
+                    help="profiling: VF_OPT_PAIR_REUSE for --case (0 never, 1 auto, 2 always)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -595,6 +597,7 @@ def run_case(args):
         print(json.dumps({"case": args.case, "size": n, "ms": round(ms, 4),
                           "mpix_s": round(n * n / ms / 1e3, 1)}))
         return 0
+    vfilt.set_option("pair_reuse", args.pair_reuse)
     c, a, w = args.case.split("/")
     d = int(a[4:]) if a.startswith("poly") else 4
     a = "poly" if a.startswith("poly") else a

@@ -109,8 +109,12 @@ const char* vf_last_error(const vf_ctx* ctx);
  *                      5 x 5 windows: 0 never (per-window kernels), 1 where
  *                      they are faster (default: BVDF), 2 always.
  *   VF_OPT_TILE_ROWS   rows of the per-window kernels' 32 x TY tiles: 2, 4
- *                      (default) or 8. */
-typedef enum { VF_OPT_PAIR_REUSE = 0, VF_OPT_TILE_ROWS = 1 } vf_option;
+ *                      (default) or 8.
+ *   VF_OPT_GATE_TENSOR_CORES  1 (default): vf_gate_infer runs the three
+ *                      convolutions on the tensor cores (mma, BF16 operands:
+ *                      activations rounded to BF16 between layers, FP32
+ *                      accumulation); 0: CUDA cores with FP32 activations. */
+typedef enum { VF_OPT_PAIR_REUSE = 0, VF_OPT_TILE_ROWS = 1, VF_OPT_GATE_TENSOR_CORES = 2 } vf_option;
 vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value);
 
 /* window 3, VF_VMF, VF_EXACT, degree 4, FP32, kappa 0.33, exp_cutoff 10,

@@ -340,6 +340,202 @@ __global__ void __launch_bounds__(IX * IY) gate_infer(Images I, const __nv_bfloa
   }
 }
 
+// ---- fused inference on the tensor cores: each convolution is an implicit
+// GEMM (rows = output cells, K = input channel x 3 x 3 taps, N = 16 output
+// channels) run with warp-level mma.sync m16n8k16, BF16 operands (activations
+// rounded to BF16 between layers), FP32 accumulation.  Same 32 x 8 tile and
+// halos as gate_infer; activations live in shared memory as BF16
+// [cell][channel] so an A fragment is two 32-bit loads per row.
+constexpr int TC_S1 = S1Y * S1X;                 // 432 layer-1 cells = 27 m-tiles
+constexpr int TC_S2 = S2Y * S2X;                 // 340 layer-2 cells
+constexpr int TC_S2_TILES = (TC_S2 + 15) / 16;   // 22 m-tiles
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(const __nv_bfloat16* w, int i0, int i1) {
+  uint32_t lo = *reinterpret_cast<const unsigned short*>(w + i0);
+  uint32_t hi = *reinterpret_cast<const unsigned short*>(w + i1);
+  return lo | (hi << 16);
+}
+
+__global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bfloat16* wb,
+                                                         float logit_threshold, uint8_t* flags,
+                                                         long long flag_pitch, float* prob,
+                                                         int tiles_x) {
+  __shared__ __nv_bfloat16 s0[3 * S0Y * S0X];            // x0, [c][row][col]
+  __shared__ __align__(16) uint32_t s1[TC_S1 * kC / 2];  // a1, [cell][16 ch] as bf16 pairs
+  __shared__ __align__(16) uint32_t s2[TC_S2 * kC / 2];  // a2
+  __shared__ float bias[kC * 2 + 1];
+  const int x0 = (blockIdx.x % tiles_x) * IX, y0 = (blockIdx.x / tiles_x) * IY;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  for (int k = threadIdx.x; k < 3 * S0Y * S0X; k += blockDim.x) {
+    int c = k / (S0Y * S0X), r = k - c * S0Y * S0X, ry = r / S0X, rx = r - ry * S0X;
+    int gy = y0 - 3 + ry, gx = x0 - 3 + rx;
+    float v = (gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) ? pixel_channel(I, 0, gy, gx, c) : 0.0f;
+    s0[k] = __float2bfloat16_rn(v);
+  }
+  if (threadIdx.x < kC) bias[threadIdx.x] = __bfloat162float(wb[OFF_B1 + threadIdx.x]);
+  else if (threadIdx.x < 2 * kC) bias[threadIdx.x] = __bfloat162float(wb[OFF_B2 + threadIdx.x - kC]);
+  else if (threadIdx.x == 2 * kC) bias[threadIdx.x] = __bfloat162float(wb[OFF_B3]);
+  __syncthreads();
+
+  // layer 1: K = 27 taps (c, u, v) padded to 32 = two k-steps
+  {
+    uint32_t b[2][2][2];  // [k-step][n-tile][reg]
+    int off[2][4];        // per k-step: s0 offsets of this lane's K columns 2t, 2t+1, 2t+8, 2t+9
+    bool kin[2][4];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int k = ks * 16 + 2 * t + (e & 1) + (e >> 1) * 8;
+        kin[ks][e] = k < 27;
+        int c = k / 9, r = k - c * 9, u = r / 3, v = r - u * 3;
+        off[ks][e] = kin[ks][e] ? (c * S0Y + u) * S0X + v : 0;
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        int n = nt * 8 + g;
+        int k0 = ks * 16 + 2 * t, k8 = k0 + 8;
+        auto wv = [&](int k) { return k < 27 ? OFF_W1 + n * 27 + k : -1; };
+        auto pair = [&](int ka, int kb) {
+          uint32_t lo = wv(ka) >= 0 ? *reinterpret_cast<const unsigned short*>(wb + wv(ka)) : 0u;
+          uint32_t hi = wv(kb) >= 0 ? *reinterpret_cast<const unsigned short*>(wb + wv(kb)) : 0u;
+          return lo | (hi << 16);
+        };
+        b[ks][nt][0] = pair(k0, k0 + 1);
+        b[ks][nt][1] = pair(k8, k8 + 1);
+      }
+    }
+    const unsigned short* s0u = reinterpret_cast<const unsigned short*>(s0);
+    for (int mt = warp; mt < TC_S1 / 16; mt += IX * IY / 32) {
+      float d[2][4] = {};
+      const int m0 = mt * 16 + g, m1 = m0 + 8;
+      const int base0 = (m0 / S1X) * S0X + m0 % S1X, base1 = (m1 / S1X) * S0X + m1 % S1X;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t a[4];
+        auto ld = [&](int base, int e) -> uint32_t { return kin[ks][e] ? s0u[base + off[ks][e]] : 0u; };
+        a[0] = ld(base0, 0) | (ld(base0, 1) << 16);
+        a[1] = ld(base1, 0) | (ld(base1, 1) << 16);
+        a[2] = ld(base0, 2) | (ld(base0, 3) << 16);
+        a[3] = ld(base1, 2) | (ld(base1, 3) << 16);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_bf16(d[nt], a, b[ks][nt][0], b[ks][nt][1]);
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int m = half ? m1 : m0;
+        const int ry = m / S1X, rx = m - ry * S1X;
+        const int gy = y0 - 2 + ry, gx = x0 - 2 + rx;
+        const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int n = nt * 8 + 2 * t;
+          float v0 = in ? fmaxf(d[nt][half * 2] + bias[n], 0.0f) : 0.0f;
+          float v1 = in ? fmaxf(d[nt][half * 2 + 1] + bias[n + 1], 0.0f) : 0.0f;
+          s1[(m * kC + n) >> 1] = pack_bf16(v0, v1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // layer 2: K = 9 taps x 16 channels = 9 k-steps
+  {
+    uint32_t b[9][2][2];
+#pragma unroll
+    for (int ks = 0; ks < 9; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int n = nt * 8 + g;  // W2[n][c][u][v], k-step ks = u * 3 + v, c = K column
+        const int base = OFF_W2 + n * 144 + ks;
+        b[ks][nt][0] = bf16_pair(wb, base + (2 * t) * 9, base + (2 * t + 1) * 9);
+        b[ks][nt][1] = bf16_pair(wb, base + (2 * t + 8) * 9, base + (2 * t + 9) * 9);
+      }
+    for (int mt = warp; mt < TC_S2_TILES; mt += IX * IY / 32) {
+      float d[2][4] = {};
+      const int m0 = mt * 16 + g, m1 = m0 + 8;
+      const int c0 = min(m0, TC_S2 - 1), c1 = min(m1, TC_S2 - 1);
+      const int base0 = (c0 / S2X) * S1X + c0 % S2X, base1 = (c1 / S2X) * S1X + c1 % S2X;
+#pragma unroll
+      for (int ks = 0; ks < 9; ++ks) {
+        const int o = (ks / 3) * S1X + ks % 3;
+        const uint32_t* r0 = s1 + (((base0 + o) * kC) >> 1);
+        const uint32_t* r1 = s1 + (((base1 + o) * kC) >> 1);
+        uint32_t a[4] = {r0[t], r1[t], r0[t + 4], r1[t + 4]};
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma_bf16(d[nt], a, b[ks][nt][0], b[ks][nt][1]);
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int m = half ? m1 : m0;
+        if (m >= TC_S2) continue;
+        const int ry = m / S2X, rx = m - ry * S2X;
+        const int gy = y0 - 1 + ry, gx = x0 - 1 + rx;
+        const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int n = nt * 8 + 2 * t;
+          float v0 = in ? fmaxf(d[nt][half * 2] + bias[kC + n], 0.0f) : 0.0f;
+          float v1 = in ? fmaxf(d[nt][half * 2 + 1] + bias[kC + n + 1], 0.0f) : 0.0f;
+          s2[(m * kC + n) >> 1] = pack_bf16(v0, v1);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // layer 3: one output channel (N padded to 8 with zero weights)
+  {
+    uint32_t b[9][2];
+#pragma unroll
+    for (int ks = 0; ks < 9; ++ks) {
+      const int base = OFF_W3 + ks;  // W3[0][c][u][v]
+      b[ks][0] = g == 0 ? bf16_pair(wb, base + (2 * t) * 9, base + (2 * t + 1) * 9) : 0u;
+      b[ks][1] = g == 0 ? bf16_pair(wb, base + (2 * t + 8) * 9, base + (2 * t + 9) * 9) : 0u;
+    }
+    for (int mt = warp; mt < IX * IY / 16; mt += IX * IY / 32) {
+      float d[4] = {};
+      const int m0 = mt * 16 + g, m1 = m0 + 8;  // output pixel (m / IX, m % IX)
+      const int base0 = (m0 / IX) * S2X + m0 % IX, base1 = (m1 / IX) * S2X + m1 % IX;
+#pragma unroll
+      for (int ks = 0; ks < 9; ++ks) {
+        const int o = (ks / 3) * S2X + ks % 3;
+        const uint32_t* r0 = s2 + (((base0 + o) * kC) >> 1);
+        const uint32_t* r1 = s2 + (((base1 + o) * kC) >> 1);
+        uint32_t a[4] = {r0[t], r1[t], r0[t + 4], r1[t + 4]};
+        mma_bf16(d, a, b[ks][0], b[ks][1]);
+      }
+      if (t == 0) {  // column n = 0 of D: d[0] (row g) and d[2] (row g + 8)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int m = half ? m1 : m0;
+          const int gx = x0 + m % IX, gy = y0 + m / IX;
+          const float z = d[half * 2] + bias[2 * kC];
+          if (gx < I.W && gy < I.H) {
+            if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
+            if (prob) prob[(long long)gy * I.W + gx] = 1.0f / (1.0f + expf(-z));
+          }
+        }
+      }
+    }
+  }
+}
+
 uint32_t crc32(const unsigned char* p, size_t n, uint32_t crc = 0) {
   // CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bitwise
   crc = ~crc;
@@ -573,14 +769,21 @@ vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, 
   vf_status st = check_images(g, d_in, 1, height, width, channels, pitch, &I);
   if (st != VF_OK) return st;
   const int tiles_x = (width + IX - 1) / IX, tiles_y = (height + IY - 1) / IY;
-  static_assert(kInferSmem <= 200 * 1024, "inference tile fits in shared memory");
-  cudaError_t e = cudaFuncSetAttribute(gate_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kInferSmem);
-  if (e == cudaSuccess) {
-    const float thr = std::log(threshold / (1.0f - threshold));
-    gate_infer<<<tiles_x * tiles_y, IX * IY, kInferSmem, (cudaStream_t)stream>>>(
+  const float thr = std::log(threshold / (1.0f - threshold));
+  cudaError_t e = cudaSuccess;
+  if (gate_tensor_cores(g->ctx)) {
+    gate_infer_tc<<<tiles_x * tiles_y, IX * IY, 0, (cudaStream_t)stream>>>(
         I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x);
     e = cudaGetLastError();
+  } else {
+    static_assert(kInferSmem <= 200 * 1024, "inference tile fits in shared memory");
+    e = cudaFuncSetAttribute(gate_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kInferSmem);
+    if (e == cudaSuccess) {
+      gate_infer<<<tiles_x * tiles_y, IX * IY, kInferSmem, (cudaStream_t)stream>>>(
+          I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x);
+      e = cudaGetLastError();
+    }
   }
   if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
   return VF_OK;

@@ -111,6 +111,9 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
                          unsigned long long* d_stats, Launch* out, LaunchClass* cls);
 
+// Whether the gate inference runs on the tensor cores (context option).
+bool gate_tensor_cores(const vf_ctx* ctx);
+
 // Record an error text in the context and return s.
 vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg);
 
