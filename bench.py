@@ -101,9 +101,12 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline model
 
-MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 5): 18290}
-# DRAM bytes (read + write) per output pixel from the same ncu capture
-MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 5): 7.29}
+# Thread instructions (predicated on) per output pixel of the pair-reuse BVDF
+# exact kernel, measured with ncu on a 6144 x 6144 capture (the arctangent is
+# CUDA's atan2f, whose instruction count the source does not fix)
+MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 5): 4668}
+# DRAM bytes (read + write) per output pixel from the same capture
+MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 5): 7.09}
 
 
 # FP32-pipe instructions per pair / per sample of each kernel, counted from the
@@ -116,9 +119,6 @@ def ops_per_pixel(crit, approx, deg, w):
         return P * 8 + n, P          # 3 sub, mul + 2 fma, 2 agg adds; argmin
     if crit == "bvdf":
         if approx == "exact":
-            # atan2f is a library sequence with data-dependent branches: its
-            # count is measured, thread instructions (predicated on) per pixel
-            # from an ncu capture of the 6144 x 6144 case
             return MEASURED_INST_PER_PIXEL.get((crit, approx, w)), None
         # dot 3, rr 1, z 2, cross 9, t2 3, 1+z 1, two Horner chains 2 deg,
         # select 2, 2 agg adds; rcp + sqrt on MUFU
