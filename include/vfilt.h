@@ -105,9 +105,10 @@ const char* vf_last_error(const vf_ctx* ctx);
 /* Context options (execution choices; results agree within the parity bar).
  *   VF_OPT_PAIR_REUSE  pair-reuse kernels (each pairwise term computed once
  *                      per 32 x 8 tile and shared by every window holding the
- *                      pair), for FP32 VMF, BVDF, AMNFE, AMNFG with 3 x 3 and
- *                      5 x 5 windows: 0 never (per-window kernels), 1 where
- *                      they are faster (default: BVDF), 2 always.
+ *                      pair), for FP32 VMF, BVDF, AMNFE, AMNFG with 3 x 3,
+ *                      5 x 5 and 7 x 7 windows: 0 never (per-window
+ *                      kernels), 1 where they are faster (default: BVDF),
+ *                      2 always.
  *   VF_OPT_TILE_ROWS   rows of the per-window kernels' 32 x TY tiles: 2, 4
  *                      (default) or 8.
  *   VF_OPT_GATE_TENSOR_CORES  1 (default): vf_gate_infer runs the three

@@ -32,6 +32,8 @@ cudaError_t launch_reuse(const Launch& L, int crit, int w, int apx, int degree, 
                           : launch_reuse_sel_w3(L, crit, apx, degree, grid, s);
   if (w == 5) return amnf ? launch_reuse_amnf_w5(L, crit, apx, degree, grid, s)
                           : launch_reuse_sel_w5(L, crit, apx, degree, grid, s);
+  if (w == 7) return amnf ? launch_reuse_amnf_w7(L, crit, apx, degree, grid, s)
+                          : launch_reuse_sel_w7(L, crit, apx, degree, grid, s);
   return cudaErrorInvalidValue;
 }
 

@@ -79,13 +79,18 @@ VF_DECLARE_PACKED(bf16)
 constexpr int kPackedTileCols = 64;
 
 // Pair-reuse launchers (vf_r_w<w>_<sel|amnf>.cu): one CTA covers 32 x 8
-// outputs; windows 3 and 5, VMF / BVDF / AMNFE / AMNFG in FP32.
+// outputs; windows 3, 5 (whole term table) and 7 (table built one offset row
+// at a time), VMF / BVDF / AMNFE / AMNFG in FP32.
 constexpr int kReuseTileRows = 8;
 cudaError_t launch_reuse_sel_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w5(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w5(const Launch&, int, int, int, int, cudaStream_t);
-inline bool has_reuse_kernel(int w, int crit) { return (w == 3 || w == 5) && crit != kEVMF; }
+cudaError_t launch_reuse_sel_w7(const Launch&, int, int, int, int, cudaStream_t);
+cudaError_t launch_reuse_amnf_w7(const Launch&, int, int, int, int, cudaStream_t);
+inline bool has_reuse_kernel(int w, int crit) {
+  return (w == 3 || w == 5 || w == 7) && crit != kEVMF;
+}
 // Where the reuse kernels are the faster choice (measured on GB300 at
 // 1024 x 1024): the angle terms (BVDF), 2.0 - 3.4x; for the cheap L2 / L1
 // terms the table and box-sum traffic costs more than the terms it saves.

@@ -51,10 +51,65 @@ __host__ __device__ constexpr int fwd_index(int dy, int dx) {
   return dy == 0 ? dx - 1 : (W - 1) + (dy - 1) * (2 * (W - 1) + 1) + dx + (W - 1);
 }
 
+// Phase 3 of the reuse kernels: each output thread reads the n aggregates
+// of its window from the slots A[i * THREADS + thread] and selects (argmin,
+// lowest index) or weights (AMNF) exactly as the per-window kernel does.
+template <int W, int CRIT, int APX, int DEG>
+__device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
+                                             const uint32_t* raw, const float* A, int x0,
+                                             int y0) {
+  using G = ReuseGeom<W>;
+  constexpr int R = G::R, RX = G::RX, N = G::N;
+  const int ox = threadIdx.x % kRTX, oy = threadIdx.x / kRTX;
+  const int gx = x0 + ox, gy = y0 + oy;
+  const bool valid = gx < L.width && gy < L.height;
+  const float* sagg = A + threadIdx.x;
+  int ties = 0;
+  if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+    const float4 xc = px[(oy + R) * RX + ox + R];
+    const uint32_t rawc = raw[(oy + R) * RX + ox + R];
+    uint32_t v = rawc;
+    if (sagg[(N / 2) * G::THREADS] != 0.0f) {  // not a constant window
+      float wsum = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const float4 xi = px[(oy + i / W) * RX + ox + i % W];
+        const float rh = rcp_approx(L.kappa_scale * sagg[i * G::THREADS]);
+        const float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
+        float u;
+        if constexpr (CRIT == kAMNFE) {
+          u = (fabsf(dx) + fabsf(dy) + fabsf(dz)) * rh;
+        } else {
+          u = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (rh * rh);
+        }
+        const float wi = (rh * rh * rh) * expneg<APX, DEG>(L, u);
+        wsum += wi;
+        ax = fmaf(wi, xi.x, ax);
+        ay = fmaf(wi, xi.y, ay);
+        az = fmaf(wi, xi.z, az);
+      }
+      const float rw = 1.0f / wsum;
+      const float yx = ax * rw, yy = ay * rw, yz = az * rw;
+      if (L.stats) {
+        auto g = [](float q) { return fabsf(q - floorf(q) - 0.5f); };
+        ties = fminf(g(yx), fminf(g(yy), g(yz))) < 1e-3f;
+      }
+      v = pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
+    }
+    if (valid) store_px(L, gx, gy, v);
+  } else {
+    const Selection s =
+        select_min<W, false>(nullptr, sagg, G::THREADS, px, RX, ox, oy, L.stats != nullptr);
+    if (valid) store_px(L, gx, gy, raw[(oy + s.best / W) * RX + ox + s.best % W]);
+    ties = s.near_tie;
+  }
+  block_stats(L, valid ? 1 : 0, valid ? ties : 0, 0);
+}
+
 template <int W, int CRIT, int APX, int DEG>
 __global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_constant__ Launch L) {
   using G = ReuseGeom<W>;
-  constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, N = G::N, M = G::M, ND = G::ND;
+  constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M, ND = G::ND;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* px = reinterpret_cast<float4*>(smem);
   uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
@@ -158,63 +213,153 @@ __global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_const
   __syncthreads();
 
   // 3. selection / weighting per output
-  const int ox = threadIdx.x % kRTX, oy = threadIdx.x / kRTX;
-  const int gx = x0 + ox, gy = y0 + oy;
-  const bool valid = gx < L.width && gy < L.height;
-  const float* sagg = A + threadIdx.x;
-  int ties = 0;
-  if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
-    const float4 xc = px[(oy + R) * RX + ox + R];
-    const uint32_t rawc = raw[(oy + R) * RX + ox + R];
-    uint32_t v = rawc;
-    if (sagg[(N / 2) * G::THREADS] != 0.0f) {  // not a constant window
-      float wsum = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+  reuse_finish<W, CRIT, APX, DEG>(L, px, raw, A, x0, y0);
+}
+
+// Chunked form for large windows, where the whole term table would not fit in
+// shared memory next to a useful occupancy (w = 7: 84 x 532 floats).  The
+// table is built one forward offset row dy = k at a time (2w - 1 entries per
+// pixel); after each row every region pixel adds the box-sum contributions of
+// its distance field's rows +k and -k (the latter from the mirrored entries
+// T_k[-dx][p + (-k, dx)]) directly to the per-window slots A, which therefore
+// accumulate in shared memory instead of registers.  Same sums, another
+// order.
+inline size_t reuse_chunked_smem_bytes(int w) {
+  size_t rx = kRTX + w - 1, ry = kRTY + w - 1, nr = rx * ry;
+  return nr * 20 + (size_t)(2 * w - 1) * nr * 4 + (size_t)w * w * kRTX * kRTY * 4;
+}
+
+template <int W, int CRIT, int APX, int DEG>
+__global__ void __launch_bounds__(kRTX* kRTY, 2)
+    reuse_chunked_kernel(const __grid_constant__ Launch L) {
+  using G = ReuseGeom<W>;
+  constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, N = G::N, M = G::M;
+  constexpr int ROW = 2 * M + 1;  // entries of one offset row
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* px = reinterpret_cast<float4*>(smem);
+  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
+  float* T = reinterpret_cast<float*>(smem + NR * 20);  // [ROW][NR]: T[dx + M][p]
+  float* A = T + ROW * NR;                                // [N][THREADS]
+  const int tile = blockIdx.x;
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  const int x0 = txi * kRTX, y0 = tyi * kRTY;
+
+  TileSmem t;
+  t.px = px;
+  t.raw = raw;
+  t.sw = RX;
+  t.sh = RY;
+  stage_tile<CRIT>(L, t, x0, y0, R);
+  for (int k = threadIdx.x; k < N * G::THREADS; k += G::THREADS) A[k] = 0.0f;
+  __syncthreads();
+
+  // adds the box sums of one field row dy (values d[dx + M]) of region pixel
+  // (r, c) to the slots of the tile's windows that contain the pixel
+  auto add_row = [&](int r, int c, int dy, const float (&d)[ROW]) {
+    float h[W];
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const float4 xi = px[(oy + i / W) * RX + ox + i % W];
-        const float rh = rcp_approx(L.kappa_scale * sagg[i * G::THREADS]);
-        const float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
-        float u;
-        if constexpr (CRIT == kAMNFE) {
-          u = (fabsf(dx) + fabsf(dy) + fabsf(dz)) * rh;
-        } else {
-          u = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (rh * rh);
-        }
-        const float wi = (rh * rh * rh) * expneg<APX, DEG>(L, u);
-        wsum += wi;
-        ax = fmaf(wi, xi.x, ax);
-        ay = fmaf(wi, xi.y, ay);
-        az = fmaf(wi, xi.z, az);
-      }
-      const float rw = 1.0f / wsum;
-      const float yx = ax * rw, yy = ay * rw, yz = az * rw;
-      if (L.stats) {
-        auto g = [](float q) { return fabsf(q - floorf(q) - 0.5f); };
-        ties = fminf(g(yx), fminf(g(yy), g(yz))) < 1e-3f;
-      }
-      v = pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
+    for (int ex = -R; ex <= R; ++ex) {
+      float s = 0.0f;
+#pragma unroll
+      for (int q = ex - R; q <= ex + R; ++q) s += d[q + M];
+      h[ex + R] = s;
     }
-    if (valid) store_px(L, gx, gy, v);
-  } else {
-    const Selection s =
-        select_min<W, false>(nullptr, sagg, G::THREADS, px, RX, ox, oy, L.stats != nullptr);
-    if (valid) store_px(L, gx, gy, raw[(oy + s.best / W) * RX + ox + s.best % W]);
-    ties = s.near_tie;
+#pragma unroll
+    for (int ey = -R; ey <= R; ++ey) {
+      if (dy < ey - R || dy > ey + R) continue;
+      const int oy = r + ey - R;
+      if (oy < 0 || oy >= kRTY) continue;
+#pragma unroll
+      for (int ex = -R; ex <= R; ++ex) {
+        const int ox = c + ex - R;
+        if (ox >= 0 && ox < kRTX) {
+          const int j = (R - ey) * W + (R - ex);
+          A[j * G::THREADS + oy * kRTX + ox] += h[ex + R];
+        }
+      }
+    }
+  };
+
+  for (int k = 0; k <= M; ++k) {
+    // term row k: T[dx + M][p] = term(x_p, x_{p + (k, dx)})
+    auto row_terms = [&](const auto& term) {
+      for (int p = threadIdx.x; p < NR; p += G::THREADS) {
+        const int r = p / RX, c = p - r * RX;
+        if (r + k >= RY) continue;
+        const float4 xp = px[p];
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          if (k == 0 && dx <= 0) continue;
+          if (c + dx >= 0 && c + dx < RX) T[(dx + M) * NR + p] = term(xp, px[p + k * RX + dx]);
+        }
+      }
+    };
+    if constexpr (CRIT == kVMF) {
+      row_terms(TermL2{});
+    } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+      row_terms(TermL1{});
+    } else if constexpr (APX == kExact) {
+      row_terms(TermAngleExact{});
+    } else {
+      row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b));
+    }
+    __syncthreads();
+    // field rows +k and -k of every region pixel
+    for (int p = threadIdx.x; p < NR; p += G::THREADS) {
+      const int r = p / RX, c = p - r * RX;
+      float d[ROW];
+      if (k == 0) {
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          const int cq = c + dx;
+          float v = 0.0f;
+          if (cq >= 0 && cq < RX) {
+            if (dx > 0) v = T[(dx + M) * NR + p];
+            else if (dx < 0) v = T[(-dx + M) * NR + p + dx];
+          }
+          d[dx + M] = v;
+        }
+        add_row(r, c, 0, d);
+      } else {
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          const int cq = c + dx;
+          d[dx + M] = (r + k < RY && cq >= 0 && cq < RX) ? T[(dx + M) * NR + p] : 0.0f;
+        }
+        add_row(r, c, k, d);
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          const int rq = r - k, cq = c + dx;
+          d[dx + M] = (rq >= 0 && cq >= 0 && cq < RX) ? T[(-dx + M) * NR + rq * RX + cq] : 0.0f;
+        }
+        add_row(r, c, -k, d);
+      }
+    }
+    __syncthreads();
   }
-  block_stats(L, valid ? 1 : 0, valid ? ties : 0, 0);
+  reuse_finish<W, CRIT, APX, DEG>(L, px, raw, A, x0, y0);
 }
 
 template <int W, int CRIT, int APX, int DEG>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
-  const size_t smem = reuse_smem_bytes(W);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG>,
+  if constexpr (W >= 7) {
+    const size_t smem = reuse_chunked_smem_bytes(W);
+    cudaError_t e = cudaFuncSetAttribute(reuse_chunked_kernel<W, CRIT, APX, DEG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    reuse_chunked_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
+  } else {
+    const size_t smem = reuse_smem_bytes(W);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    reuse_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
   }
-  reuse_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
   return cudaGetLastError();
 }
+
 
 // VMF and BVDF
 template <int W>

@@ -193,7 +193,7 @@ def test_alias_rejected(vf):
     assert e.value.name == "VF_ERR_ALIAS"
 
 
-@pytest.mark.parametrize("w", [3, 5])
+@pytest.mark.parametrize("w", [3, 5, 7])
 @pytest.mark.parametrize("crit,approx,deg", [("vmf", "exact", 4), ("bvdf", "exact", 4),
                                              ("bvdf", "poly", 3), ("amnfe", "poly", 5),
                                              ("amnfg", "rational", 4), ("amnfe", "exact", 4)])
