@@ -9,7 +9,8 @@
 // atomicAdd per tile; no CTA ever waits on another.  A tile is mapped to its
 // image by binary search over the images' first tile indices, then run by the
 // same per-tile body as the single-image kernel (vf_kernels.cuh), selected by
-// the image's class (window x criterion x approximation).  Polynomials run
+// the image's class (window x criterion x approximation); BVDF tiles run the
+// pair-reuse body (vf_reuse.cuh) when the tiles are 32 x 8.  Polynomials run
 // as degree 6 with zero-padded coefficients (fma(0, z, c) = c exactly, so the
 // result is bit-identical to the degree-specific kernel).
 #include <algorithm>
@@ -18,6 +19,7 @@
 #include <vector>
 
 #include "vf_kernels.cuh"
+#include "vf_reuse.cuh"
 
 namespace vf {
 
@@ -40,24 +42,37 @@ struct BatchImage {
   int cls;
 };
 
-// Inside the batch kernel only 3 x 3 keeps its aggregates in registers: the
-// kernel's register budget is that of its largest body, and the 5 x 5
-// register bodies would force spills into every other class.
-constexpr bool batch_reg(int w) { return w == 3; }
+// Inside the batch kernel 3 x 3 keeps its aggregates in registers, and so
+// does the 5 x 5 AMNF (its integer city-block path needs about 64
+// registers); the other 5 x 5 register bodies (about 127 registers) would
+// force spills into every class, since the kernel's register budget is that
+// of its largest body.
+constexpr bool batch_reg(int w, int crit) {
+  return w == 3 || (w == 5 && (crit == kAMNFE || crit == kAMNFG));
+}
 
 template <int W>
 __device__ __forceinline__ void run_class(int k, const Launch& L, int tile) {
-  constexpr bool RG = batch_reg(W);
+  constexpr bool RG = batch_reg(W, kVMF);
+  constexpr bool RA = batch_reg(W, kAMNFE);
   switch (k) {
     case 0: process_tile<W, kVMF, kExact, 0, RG>(L, tile); break;
-    case 1: process_tile<W, kBVDF, kExact, 0, RG>(L, tile); break;
-    case 2: process_tile<W, kBVDF, kPoly, 6, RG>(L, tile); break;
-    case 3: process_tile<W, kAMNFE, kExact, 0, RG>(L, tile); break;
-    case 4: process_tile<W, kAMNFE, kPoly, 6, RG>(L, tile); break;
-    case 5: process_tile<W, kAMNFE, kRational, 4, RG>(L, tile); break;
-    case 6: process_tile<W, kAMNFG, kExact, 0, RG>(L, tile); break;
-    case 7: process_tile<W, kAMNFG, kPoly, 6, RG>(L, tile); break;
-    case 8: process_tile<W, kAMNFG, kRational, 4, RG>(L, tile); break;
+    // BVDF: with 32 x 8 tiles (256 threads) the pair-reuse body, whose tile
+    // grid is the same; otherwise the per-window body
+    case 1:
+      if (blockDim.x == kRTX * kRTY) reuse_any_tile<W, kBVDF, kExact, 0>(L, tile);
+      else process_tile<W, kBVDF, kExact, 0, RG>(L, tile);
+      break;
+    case 2:
+      if (blockDim.x == kRTX * kRTY) reuse_any_tile<W, kBVDF, kPoly, 6>(L, tile);
+      else process_tile<W, kBVDF, kPoly, 6, RG>(L, tile);
+      break;
+    case 3: process_tile<W, kAMNFE, kExact, 0, RA>(L, tile); break;
+    case 4: process_tile<W, kAMNFE, kPoly, 6, RA>(L, tile); break;
+    case 5: process_tile<W, kAMNFE, kRational, 4, RA>(L, tile); break;
+    case 6: process_tile<W, kAMNFG, kExact, 0, RA>(L, tile); break;
+    case 7: process_tile<W, kAMNFG, kPoly, 6, RA>(L, tile); break;
+    case 8: process_tile<W, kAMNFG, kRational, 4, RA>(L, tile); break;
     case 9: process_tile<W, kEVMF, kExact, 0, RG>(L, tile); break;
     case 10: process_tile<W, kEVMF, kPoly, 6, RG>(L, tile); break;
     default: process_tile<W, kEVMF, kRational, 4, RG>(L, tile); break;
@@ -143,7 +158,8 @@ size_t batch_smem(const vf_batch* b, int ty) {
     int wi = im.cls / kClassesPerWindow, k = im.cls % kClassesPerWindow;
     int w = 3 + 2 * wi;
     int crit = k == 0 ? kVMF : (k <= 2 ? kBVDF : (k <= 5 ? kAMNFE : (k <= 8 ? kAMNFG : kEVMF)));
-    m = std::max(m, smem_bytes(w, crit, ty, batch_reg(w)));
+    m = std::max(m, smem_bytes(w, crit, ty, batch_reg(w, crit)));
+    if (crit == kBVDF && kTX * ty == kRTX * kRTY) m = std::max(m, reuse_any_smem_bytes(w));
   }
   return m;
 }
@@ -179,8 +195,15 @@ vf_status drop_graph(vf_batch* b) {
 
 int resident_ctas(const vf_batch* b, int ty) {
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel, kTX * ty,
-                                                    batch_smem(b, ty)) != cudaSuccess)
+  const size_t smem = batch_smem(b, ty);
+  // the occupancy query counts a dynamic size above 48 KB only once the
+  // kernel has been allowed that much
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel, kTX * ty, smem) !=
+      cudaSuccess)
     return 1;
   return std::max(blocks, 1);
 }
@@ -512,7 +535,7 @@ vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count
     H.begin[q] = (int)total;
     total += (long long)L.tiles_x * ((L.height + ty - 1) / ty);
     if (total > 0x7fffffffLL) return VF_ERR_UNSUPPORTED;
-    smem = std::max(smem, smem_bytes(cls[i].w, cls[i].crit, ty, batch_reg(cls[i].w)));
+    smem = std::max(smem, smem_bytes(cls[i].w, cls[i].crit, ty, batch_reg(cls[i].w, cls[i].crit)));
   }
   H.begin[count] = (int)total;
   cudaStream_t s = (cudaStream_t)stream;

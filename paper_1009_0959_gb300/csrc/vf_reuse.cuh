@@ -107,7 +107,7 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
 }
 
 template <int W, int CRIT, int APX, int DEG>
-__global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_constant__ Launch L) {
+__device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   using G = ReuseGeom<W>;
   constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M, ND = G::ND;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -115,7 +115,6 @@ __global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_const
   uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
   float* T = reinterpret_cast<float*>(smem + NR * 20);   // [ND][NR]
   float* A = T + ND * NR;                                  // [N][THREADS]
-  const int tile = blockIdx.x;
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kRTX, y0 = tyi * kRTY;
 
@@ -230,8 +229,7 @@ inline size_t reuse_chunked_smem_bytes(int w) {
 }
 
 template <int W, int CRIT, int APX, int DEG>
-__global__ void __launch_bounds__(kRTX* kRTY, 2)
-    reuse_chunked_kernel(const __grid_constant__ Launch L) {
+__device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
   using G = ReuseGeom<W>;
   constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, N = G::N, M = G::M;
   constexpr int ROW = 2 * M + 1;  // entries of one offset row
@@ -240,7 +238,6 @@ __global__ void __launch_bounds__(kRTX* kRTY, 2)
   uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
   float* T = reinterpret_cast<float*>(smem + NR * 20);  // [ROW][NR]: T[dx + M][p]
   float* A = T + ROW * NR;                                // [N][THREADS]
-  const int tile = blockIdx.x;
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kRTX, y0 = tyi * kRTY;
 
@@ -340,25 +337,38 @@ __global__ void __launch_bounds__(kRTX* kRTY, 2)
   reuse_finish<W, CRIT, APX, DEG>(L, px, raw, A, x0, y0);
 }
 
+// One 32 x 8 tile per CTA (a 256-thread CTA whose shared memory is reused:
+// callers looping over tiles must __syncthreads() between calls).
+template <int W, int CRIT, int APX, int DEG>
+__device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
+  if constexpr (W >= 7) {
+    reuse_chunked_tile<W, CRIT, APX, DEG>(L, tile);
+  } else {
+    reuse_tile<W, CRIT, APX, DEG>(L, tile);
+  }
+}
+
+inline size_t reuse_any_smem_bytes(int w) {
+  return w >= 7 ? reuse_chunked_smem_bytes(w) : reuse_smem_bytes(w);
+}
+
+template <int W, int CRIT, int APX, int DEG>
+__global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_constant__ Launch L) {
+  reuse_any_tile<W, CRIT, APX, DEG>(L, blockIdx.x);
+}
+
 template <int W, int CRIT, int APX, int DEG>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
-  if constexpr (W >= 7) {
-    const size_t smem = reuse_chunked_smem_bytes(W);
-    cudaError_t e = cudaFuncSetAttribute(reuse_chunked_kernel<W, CRIT, APX, DEG>,
+  const size_t smem = reuse_any_smem_bytes(W);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    reuse_chunked_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
-  } else {
-    const size_t smem = reuse_smem_bytes(W);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    reuse_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
   }
+  reuse_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
   return cudaGetLastError();
 }
+
 
 
 // VMF and BVDF

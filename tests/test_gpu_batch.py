@@ -62,33 +62,36 @@ def test_batch_matches_oracle(vf):
 
 
 def test_batch_graph_autotune_identical(vf):
+    """Within one configuration, plain and graph launches give identical
+    bytes; every tile shape the autotuner or the caller picks meets the
+    oracle parity bar (with 32 x 8 tiles BVDF runs the pair-reuse body, whose
+    sums are in another order, so near ties may resolve differently)."""
     items = make_batch(20, 2, lo=(20, 30), hi=(120, 200))
     dev = to_dev(items)
+    refs = [F.filter_image(noisy, F.Config(p["criterion"], p["window"], p["approx"], p["degree"]))
+            for noisy, p in items]
     b = vf.Batch(dev)
-    b.launch()
-    torch.cuda.synchronize()
-    first = [o.clone() for _, o, _ in dev]
-    for _, o, _ in dev:
-        o.zero_()
-    b.graph_launch()
-    b.graph_launch()
-    torch.cuda.synchronize()
-    for f, (_, o, _) in zip(first, dev):
-        assert torch.equal(f, o)
-    cfg = b.autotune()
-    assert cfg["tile_rows"] in (2, 4, 8) and cfg["ctas_per_sm"] >= 1 and cfg["ms"] > 0
-    for _, o, _ in dev:
-        o.zero_()
-    b.graph_launch()
-    torch.cuda.synchronize()
-    for f, (_, o, _) in zip(first, dev):
-        assert torch.equal(f, o)
-    for ty in (2, 8):
-        b.configure(ty, 1)
+
+    def run_and_check():
         b.launch()
         torch.cuda.synchronize()
-        for f, (_, o, _) in zip(first, dev):
+        first = [o.clone() for _, o, _ in dev]
+        for _, o, _ in dev:
+            o.zero_()
+        b.graph_launch()
+        b.graph_launch()
+        torch.cuda.synchronize()
+        for f, (_, o, p), (ro, rd) in zip(first, dev, refs):
             assert torch.equal(f, o)
+            check(p["criterion"], ro, rd, o.cpu().numpy())
+
+    run_and_check()
+    cfg = b.autotune()
+    assert cfg["tile_rows"] in (2, 4, 8) and cfg["ctas_per_sm"] >= 1 and cfg["ms"] > 0
+    run_and_check()
+    for ty in (2, 8):
+        b.configure(ty, 1)
+        run_and_check()
     b.close()
 
 
