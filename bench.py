@@ -212,43 +212,75 @@ def main():
         for i, (c, a, d, w, k) in enumerate(launches):
             slot = (step.counter + i) % POOL
             src = pool_in[(slot // 3) * 3 + k]  # a copy of image k, rotating
+            # the current stream: the bench stream, or the capture stream below
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            vfilt.filter(src, pool_out[slot], criterion=c, window=w, approx=a, degree=max(d, 2),
-                         stream=stream)
+                e0.record()
+            vfilt.filter(src, pool_out[slot], criterion=c, window=w, approx=a, degree=max(d, 2))
             if record:
-                e1.record(stream)
+                e1.record()
                 per[vkey(c, a, d, w)].append((e0, e1))
         step.counter += len(launches)
     step.counter = 0
 
+    def timed(run):
+        """K runs between a barrier + synchronize on both sides; device time
+        from CUDA events on the launching stream, max over ranks; also the host
+        time the enqueueing took."""
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        h0 = time.perf_counter()
+        for _ in range(args.steps):
+            run()
+        host_ms = (time.perf_counter() - h0) * 1e3
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        if dist:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+            dist.barrier()
+        return ms, host_ms
+
     for _ in range(args.warmup):
         step(False)
+    # the same step captured once as a CUDA graph (168 kernel nodes), replayed
+    graph, graph_error = torch.cuda.CUDAGraph(), None
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    try:
+        with torch.cuda.stream(cap):
+            step(False)  # warm the library's per-kernel attribute caches on this stream
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=cap):
+                step(False)
+    except RuntimeError as e:  # reported in the line; the eager timing stands
+        graph, graph_error = None, str(e).splitlines()[0][:200]
+    stream.wait_stream(cap)
+    for _ in range(args.warmup if graph is not None else 0):
+        graph.replay()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+
     clocks = Clocks(local)
     clocks.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    for _ in range(args.steps):
-        step(True)
-    t1.record(stream)
-    torch.cuda.synchronize()
+    ms_eager, host_eager = timed(lambda: step(False))
+    ms_graph, host_graph = timed(graph.replay) if graph is not None else (ms_eager, host_eager)
     ck = clocks.stop()
-    ms_total = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
-        dist.barrier()
+    # per-launch device times: a separate pass with events around each launch
+    for _ in range(2):
+        step(True)
+    torch.cuda.synchronize()
 
     pix_per_step = len(launches) * H * W
+    ms_total = ms_graph
     value = pix_per_step * args.steps * world / (ms_total / 1e3) / 1e6
+    value_eager = pix_per_step * args.steps * world / (ms_eager / 1e3) / 1e6
     kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v) for k, v in per.items()}
 
     # per filter / window: exact vs fastest minimax meeting the 0.05 dB bar
@@ -316,7 +348,13 @@ def main():
                        "launches_per_step": len(launches), "mpix_per_step": pix_per_step / 1e6,
                        "l2": "inputs rotate through a %d MB pool (> 129 MB L2)" %
                              (POOL * 8),
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "launch": ("one step captured as a CUDA graph of its vf_filter calls, "
+                                  "replayed K times") if graph is not None else
+                                 "vf_filter calls (graph capture failed: %s)" % graph_error},
+            "eager": {"value": round(value_eager, 1), "ms_per_step": round(ms_eager / args.steps, 3),
+                      "host_enqueue_ms_per_step": round(host_eager / args.steps, 3),
+                      "call": "vf_filter from Python, one call per launch"},
             "gpu_launches": len(launches) * args.steps,
             "clocks": ck, "roofline": roof, "per_filter_window": pfw}
 

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) gated_kernel(const __grid_constant__ Laun
   const int x0 = txi * kTX, y0 = tyi * TY;
   __shared__ int s_count;
   if (threadIdx.x == 0) s_count = 0;
-  stage_tile<CRIT>(L, t, x0, y0, R);
+  stage_tile<CRIT, CRIT != kVMF>(L, t, x0, y0, R);
   __syncthreads();
   const int px = threadIdx.x % kTX, py = threadIdx.x / kTX;
   const int gx = x0 + px, gy = y0 + py;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) gated_kernel(const __grid_constant__ Laun
       v = amnf_pixel<W, REG, CRIT, APX, DEG>(L, t, qx, qy, stride, tie);
       ties += tie;
     } else if constexpr (CRIT == kVMF) {
-      Selection s = window_select<W, REG>(t.px, t.sw, qx, qy, TermL2{}, sagg, stride, want_tie);
+      Selection s = window_select<W, REG>(t.raw, t.sw, qx, qy, TermL2U8{}, sagg, stride, want_tie);
       v = t.raw[(qy + s.best / W) * t.sw + qx + s.best % W];
       ties += s.near_tie;
     } else if constexpr (APX == kExact) {

@@ -80,6 +80,20 @@ struct TermL2 {
   }
 };
 
+// The same distance on packed 8-bit colours (fourth byte zero): __vabsdiffu4
+// forms the byte-wise |a_k - b_k| and one __dp4a squares and sums them, the
+// exact integer d2 < 2^18.  Accumulated onto the bits of 2^23 it reads as the
+// FP32 number 2^23 + d2, and one subtraction leaves d2 exactly: the value the
+// FP32 form computes, so the same square root, from two integer-pipe and one
+// FP32 instruction instead of six FP32 ones.
+struct TermL2U8 {
+  __device__ __forceinline__ float operator()(uint32_t a, uint32_t b) const {
+    const uint32_t d = __vabsdiffu4(a, b);
+    const float d2 = __uint_as_float(__dp4a(d, d, 0x4B000000u)) - 8388608.0f;
+    return sqrt_approx(d2);
+  }
+};
+
 // Sec. 3.2: city-block distance (exact integer in FP32).
 struct TermL1 {
   __device__ __forceinline__ float operator()(float4 a, float4 b) const {
@@ -138,20 +152,29 @@ struct TermAngleApprox {
 
 // ---------------------------------------------------------------- window aggregates
 
+// A window sample: an FP32 colour (staged .w kept) or a packed 8-bit colour
+// with the fourth byte cleared.
+__device__ __forceinline__ float4 load_sample(const float4* p) { return *p; }
+__device__ __forceinline__ uint32_t load_sample(const uint32_t* p) { return *p & 0x00ffffffu; }
+__device__ __forceinline__ bool same_colour(float4 a, float4 b) {
+  return a.x == b.x && a.y == b.y && a.z == b.z;
+}
+__device__ __forceinline__ bool same_colour(uint32_t a, uint32_t b) { return a == b; }
+
 // Per-thread window view: the window of output pixel (px, py) of the tile is
 // rows py..py+W-1, columns px..px+W-1 of the staged tile (pitch sw).
 
 // w <= 5: all n aggregates in registers, fully unrolled.
-template <int W, class Term>
-__device__ __forceinline__ void aggregates_reg(const float4* tile, int sw, int px, int py,
+template <int W, class Term, class S>
+__device__ __forceinline__ void aggregates_reg(const S* tile, int sw, int px, int py,
                                                const Term& term, float (&agg)[W * W]) {
 #pragma unroll
   for (int i = 0; i < W * W; ++i) agg[i] = 0.0f;
 #pragma unroll
   for (int a = 0; a < W; ++a) {
-    float4 A[W];
+    S A[W];
 #pragma unroll
-    for (int i = 0; i < W; ++i) A[i] = tile[(py + a) * sw + px + i];
+    for (int i = 0; i < W; ++i) A[i] = load_sample(tile + (py + a) * sw + px + i);
 #pragma unroll
     for (int i = 0; i < W; ++i)
 #pragma unroll
@@ -162,9 +185,9 @@ __device__ __forceinline__ void aggregates_reg(const float4* tile, int sw, int p
       }
 #pragma unroll
     for (int b = a + 1; b < W; ++b) {
-      float4 B[W];
+      S B[W];
 #pragma unroll
-      for (int j = 0; j < W; ++j) B[j] = tile[(py + b) * sw + px + j];
+      for (int j = 0; j < W; ++j) B[j] = load_sample(tile + (py + b) * sw + px + j);
 #pragma unroll
       for (int i = 0; i < W; ++i)
 #pragma unroll
@@ -180,18 +203,18 @@ __device__ __forceinline__ void aggregates_reg(const float4* tile, int sw, int p
 // Rolled row-pair loop (w = 7, and w = 5 for the costly angle term); aggregates in shared memory slots
 // sagg[i * stride] (stride = threads per CTA, so a warp's slots are
 // consecutive words).
-template <int W, class Term>
-__device__ __forceinline__ void aggregates_smem(const float4* tile, int sw, int px, int py,
+template <int W, class Term, class S>
+__device__ __forceinline__ void aggregates_smem(const S* tile, int sw, int px, int py,
                                                 const Term& term, float* sagg, int stride) {
 #pragma unroll
   for (int i = 0; i < W * W; ++i) sagg[i * stride] = 0.0f;
 #pragma unroll 1
   for (int a = 0; a < W; ++a) {
-    float4 A[W];
+    S A[W];
     float ra[W];
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      A[i] = tile[(py + a) * sw + px + i];
+      A[i] = load_sample(tile + (py + a) * sw + px + i);
       ra[i] = 0.0f;
     }
 #pragma unroll
@@ -204,11 +227,11 @@ __device__ __forceinline__ void aggregates_smem(const float4* tile, int sw, int 
       }
 #pragma unroll 1
     for (int b = a + 1; b < W; ++b) {
-      float4 B[W];
+      S B[W];
       float rb[W];
 #pragma unroll
       for (int j = 0; j < W; ++j) {
-        B[j] = tile[(py + b) * sw + px + j];
+        B[j] = load_sample(tile + (py + b) * sw + px + j);
         rb[j] = 0.0f;
       }
 #pragma unroll
@@ -234,9 +257,9 @@ struct Selection {
   bool near_tie;
 };
 
-template <int W, bool REG>
+template <int W, bool REG, class S>
 __device__ __forceinline__ Selection select_min(const float* agg_reg, const float* sagg, int stride,
-                                                const float4* tile, int sw, int px, int py,
+                                                const S* tile, int sw, int px, int py,
                                                 bool want_tie) {
   constexpr int N = W * W;
   int best = 0;
@@ -251,13 +274,13 @@ __device__ __forceinline__ Selection select_min(const float* agg_reg, const floa
   }
   Selection s{best, false};
   if (want_tie) {
-    float4 xb = tile[(py + best / W) * sw + px + best % W];
+    const S xb = load_sample(tile + (py + best / W) * sw + px + best % W);
     float second = __int_as_float(0x7f800000);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      float4 xi = tile[(py + i / W) * sw + px + i % W];
+      const S xi = load_sample(tile + (py + i / W) * sw + px + i % W);
       float v = REG ? agg_reg[i] : sagg[i * stride];
-      bool diff = xi.x != xb.x || xi.y != xb.y || xi.z != xb.z;
+      bool diff = !same_colour(xi, xb);
       if (diff && v < second) second = v;
     }
     s.near_tie = second <= bv * (1.0f + 1e-5f);
@@ -267,8 +290,8 @@ __device__ __forceinline__ Selection select_min(const float* agg_reg, const floa
 
 // Selection over the window of (px, py) with pairwise term `term`; REG picks
 // register aggregates (fully unrolled) or shared-memory slots (rolled).
-template <int W, bool REG, class Term>
-__device__ __forceinline__ Selection window_select(const float4* tile, int sw, int px, int py,
+template <int W, bool REG, class Term, class S>
+__device__ __forceinline__ Selection window_select(const S* tile, int sw, int px, int py,
                                                    const Term& term, float* sagg, int stride,
                                                    bool want_tie) {
   if constexpr (REG) {
@@ -336,7 +359,9 @@ __device__ __forceinline__ TileSmem carve(int W, bool reg, int TY, int threads) 
   return t;
 }
 
-template <int CRIT>
+// FLOATS = false stages only the packed pixels (the VMF selection works on
+// them directly).
+template <int CRIT, bool FLOATS = true>
 __device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, int x0, int y0, int R) {
   const int cells = t.sw * t.sh;
   for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
@@ -344,6 +369,8 @@ __device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, i
     int gy = min(max(y0 + ry - R, 0), L.height - 1);
     int gx = min(max(x0 + rx - R, 0), L.width - 1);
     uint32_t v = load_px(L, gx, gy);
+    t.raw[idx] = v;
+    if constexpr (!FLOATS) continue;
     float r = (float)(v & 255u), g = (float)((v >> 8) & 255u), b = (float)((v >> 16) & 255u);
     float w = 0.0f;
     if (CRIT == kBVDF) {
@@ -354,7 +381,6 @@ __device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, i
       }
     }
     t.px[idx] = make_float4(r, g, b, w);
-    t.raw[idx] = v;
   }
 }
 
@@ -517,53 +543,62 @@ __device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& 
 }
 
 // EVMF switch (Sec. 3.3, Eq. equ_evf) of the window of (px, py).  The sample
-// loops run row by row; for w = 7 the row loop stays rolled so that the 49
-// staged samples are not all held in registers across the passes.
+// loops run row by row; for w <= 5 the n distances r_i stay in registers
+// between the sum and the entropy pass, for w = 7 the row loop stays rolled
+// and the entropy pass recomputes r_i (one sqrt per sample) instead.
 template <int W, int APX, int DEG>
 __device__ __forceinline__ bool evmf_switch(const Launch& L, const TileSmem& t, int px, int py,
                                             bool& tie) {
   constexpr int N = W * W, C = N / 2;
-  constexpr int ROW_UNROLL = W <= 5 ? W : 1;
-  float mx = 0.0f, my = 0.0f, mz = 0.0f;
+  constexpr bool KEEP_R = W <= 5;
+  constexpr int ROW_UNROLL = KEEP_R ? W : 1;
+  // pass 1: the channel sums, exact integers, from the packed pixels: bytes 0
+  // and 2 accumulate in the two 16-bit halves of one word, byte 1 in another
+  // (n * 255 < 2^16)
+  uint32_t s02 = 0, s1 = 0;
 #pragma unroll ROW_UNROLL
   for (int a = 0; a < W; ++a) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      float4 xi = t.px[(py + a) * t.sw + px + i];
-      mx += xi.x;
-      my += xi.y;
-      mz += xi.z;
+      const uint32_t v = t.raw[(py + a) * t.sw + px + i];
+      s02 += v & 0x00ff00ffu;
+      s1 += (v >> 8) & 0xffu;
     }
   }
   // correctly rounded division: exact whenever the mean is an integer, so a
   // centre equal to the mean gives P_C = 0 exactly (no switch), as in exact
   // arithmetic; a reciprocal multiply would leave a spurious P_C > 0 = beta_C
-  mx = mx / (float)N;
-  my = my / (float)N;
-  mz = mz / (float)N;
-  // pass 2: r_i = ||x_i - xbar||_2 and their sum; pass 3 recomputes r_i (one
-  // sqrt per sample) rather than holding n of them in registers
+  const float mx = (float)(s02 & 0xffffu) / (float)N;
+  const float my = (float)s1 / (float)N;
+  const float mz = (float)(s02 >> 16) / (float)N;
+  // pass 2: r_i = ||x_i - xbar||_2 and their sum
+  auto dist = [&](int a, int i) {
+    float4 xi = t.px[(py + a) * t.sw + px + i];
+    float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
+    return sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  };
+  float r[KEEP_R ? N : 1];
   float rsum = 0.0f;
 #pragma unroll ROW_UNROLL
   for (int a = 0; a < W; ++a) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      float4 xi = t.px[(py + a) * t.sw + px + i];
-      float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
-      rsum += sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      const float ri = dist(a, i);
+      if constexpr (KEEP_R) r[a * W + i] = ri;
+      rsum += ri;
     }
   }
   tie = false;
   if (rsum == 0.0f) return false;  // constant window: identity
   const float rs = 1.0f / rsum;
+  // pass 3: the entropy sum over P_i = r_i / sum_j r_j
   float esum = 0.0f;
 #pragma unroll ROW_UNROLL
   for (int a = 0; a < W; ++a) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      float4 xi = t.px[(py + a) * t.sw + px + i];
-      float dx = xi.x - mx, dy = xi.y - my, dz = xi.z - mz;
-      esum += ent<APX, DEG>(L, sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * rs);
+      const float ri = KEEP_R ? r[KEEP_R ? a * W + i : 0] : dist(a, i);
+      esum += ent<APX, DEG>(L, ri * rs);
     }
   }
   if (esum == 0.0f) return false;  // nothing left after the cut-off: identity
@@ -583,7 +618,7 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kTX, y0 = tyi * TY;
 
-  stage_tile<CRIT>(L, t, x0, y0, R);
+  stage_tile<CRIT, CRIT != kVMF>(L, t, x0, y0, R);
   __syncthreads();
 
   const int px = threadIdx.x % kTX, py = threadIdx.x / kTX;
@@ -597,7 +632,7 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
   if constexpr (CRIT == kVMF || CRIT == kBVDF) {
     Selection s;
     if constexpr (CRIT == kVMF) {
-      s = window_select<W, REG>(t.px, t.sw, px, py, TermL2{}, sagg, stride, want_tie);
+      s = window_select<W, REG>(t.raw, t.sw, px, py, TermL2U8{}, sagg, stride, want_tie);
     } else if constexpr (APX == kExact) {
       s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleExact{}, sagg, stride, want_tie);
     } else {
@@ -630,7 +665,7 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
     for (int k = threadIdx.x; k < count; k += blockDim.x) {
       const int id = t.list[k];
       const int qx = id % kTX, qy = id / kTX;
-      Selection s = window_select<W, REG>(t.px, t.sw, qx, qy, TermL2{}, sagg, stride, want_tie);
+      Selection s = window_select<W, REG>(t.raw, t.sw, qx, qy, TermL2U8{}, sagg, stride, want_tie);
       store_px(L, x0 + qx, y0 + qy, t.raw[(qy + s.best / W) * t.sw + qx + s.best % W]);
       ties += s.near_tie;
     }

@@ -1,20 +1,27 @@
 // vf_launch.cuh -- launch helper shared by the per-criterion translation units.
 #pragma once
 
+#include "vf_evmf.cuh"
 #include "vf_kernels.cuh"
 
 namespace vf {
 
 template <int W, int CRIT, int APX, int DEG>
 cudaError_t launch_one(const Launch& L, int ty, int grid, cudaStream_t s) {
-  const size_t smem = smem_bytes(W, CRIT, ty);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel<W, CRIT, APX, DEG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  // EVMF with w >= 5: persistent kernel with a work queue (for w = 3 the
+  // 36-pair median is too cheap for the queue copies to pay, measured)
+  if constexpr (CRIT == kEVMF && W >= 5) {
+    return launch_evmf_queue<W, APX, DEG>(L, ty, grid, s);
+  } else {
+    const size_t smem = smem_bytes(W, CRIT, ty);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(filter_kernel<W, CRIT, APX, DEG>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    filter_kernel<W, CRIT, APX, DEG><<<grid, kTX * ty, smem, s>>>(L);
+    return cudaGetLastError();
   }
-  filter_kernel<W, CRIT, APX, DEG><<<grid, kTX * ty, smem, s>>>(L);
-  return cudaGetLastError();
 }
 
 // Polynomial degree 2..6 as a template argument.

@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(256) packed_kernel(const __grid_constant__ Lau
     // switch of both windows in FP32 (vf_kernels.cuh), pairs only if needed
     TileSmem ts;
     ts.px = t.px;
+    ts.raw = t.raw;
     ts.sw = t.sw;
     bool tie0 = false, tie1 = false;
     sw[0] = x0 + c0 < L.width && gy < L.height && evmf_switch<W, APX, DEG>(L, ts, c0, py, tie0);

@@ -212,3 +212,34 @@ def test_pair_reuse_and_per_window_agree(vf, crit, approx, deg, w):
         vf.set_option("pair_reuse", 1)
     check(crit, o, d, a)
     check(crit, o, d, b)
+
+
+def test_graph_capture_matches_eager(vf):
+    """vf_filter calls captured in a CUDA graph (every kernel family: per
+    window, pair reuse, the EVMF work queue, packed) replay to the same bytes
+    as the eager calls."""
+    clean, noisy = synth.noisy(70, 150, 0.2, 77)
+    src = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    calls = [dict(criterion="vmf", window=5), dict(criterion="bvdf", window=5),
+             dict(criterion="bvdf", window=3, approx="poly", degree=4),
+             dict(criterion="amnfe", window=5, approx="rational"),
+             dict(criterion="evmf", window=3), dict(criterion="evmf", window=5, approx="poly",
+                                                     degree=4),
+             dict(criterion="evmf", window=7), dict(criterion="vmf", window=5, precision="fp16x2")]
+    eager = [vf.filter(src, **kw) for kw in calls]
+    outs = [torch.zeros_like(src) for _ in calls]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for kw, o in zip(calls, outs):
+                vf.filter(src, o, **kw)
+    torch.cuda.current_stream().wait_stream(s)
+    for o in outs:
+        o.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for kw, e, o in zip(calls, eager, outs):
+        assert torch.equal(e, o), kw
