@@ -106,6 +106,36 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
   block_stats(L, valid ? 1 : 0, valid ? ties : 0, 0);
 }
 
+// The w sums of w consecutive values of v[0 .. 2w-2]: out[e] = v[e] + ... +
+// v[e + w - 1].  Neighbouring sums share their overlap (w = 5: 12 additions
+// instead of 20); additions only.
+template <int W>
+__device__ __forceinline__ void box_sums(const float (&v)[2 * W - 1], float (&out)[W]) {
+  if constexpr (W == 5) {
+    const float m1 = (v[1] + v[2]) + (v[3] + v[4]);
+    out[0] = v[0] + m1;
+    out[1] = m1 + v[5];
+    const float q = (v[4] + v[5]) + v[6];
+    const float m3 = v[3] + q;
+    out[2] = v[2] + m3;
+    out[3] = m3 + v[7];
+    out[4] = q + (v[7] + v[8]);
+  } else if constexpr (W == 3) {
+    const float m = v[1] + v[2];
+    out[0] = v[0] + m;
+    out[1] = m + v[3];
+    out[2] = (v[2] + v[3]) + v[4];
+  } else {
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      float t = 0.0f;
+#pragma unroll
+      for (int k = 0; k < W; ++k) t += v[e + k];
+      out[e] = t;
+    }
+  }
+}
+
 template <int W, int CRIT, int APX, int DEG>
 __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   using G = ReuseGeom<W>;
@@ -128,18 +158,21 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
 
   // 1. term table.  Work items are (offset row dy, region pixel p): w - 1 or
   //    2w - 1 terms each, spread over all threads so that they reach the
-  //    barrier together; consecutive threads take consecutive pixels.
+  //    barrier together; consecutive threads take consecutive pixels.  An
+  //    entry whose partner p + delta lies outside the region is 0, so the
+  //    forward reads of phase 2 need no bounds test.
   auto row_terms = [&](const auto& term) {
     for (int item = threadIdx.x; item < (M + 1) * NR; item += G::THREADS) {
       const int dy = item / NR, p = item - dy * NR;
       const int r = p / RX, c = p - r * RX;
-      if (r + dy >= RY) continue;
+      const bool row_in = r + dy < RY;
       const float4 xp = px[p];
 #pragma unroll
       for (int dx = -M; dx <= M; ++dx) {
         if (dy == 0 && dx <= 0) continue;
-        if (c + dx >= 0 && c + dx < RX)
-          T[fwd_index<W>(dy, dx) * NR + p] = term(xp, px[p + dy * RX + dx]);
+        float v = 0.0f;
+        if (row_in && c + dx >= 0 && c + dx < RX) v = term(xp, px[p + dy * RX + dx]);
+        T[fwd_index<W>(dy, dx) * NR + p] = v;
       }
     }
   };
@@ -155,59 +188,48 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   __syncthreads();
 
   // 2. box sums of each region pixel's distance field, scattered to the
-  //    windows of this tile that contain it
+  //    windows of this tile that contain it: width-w sums along each of the
+  //    2w - 1 field rows, then height-w sums down the columns, both sharing
+  //    their common partial sums (additions only)
   for (int p = threadIdx.x; p < NR; p += G::THREADS) {
     const int r = p / RX, c = p - r * RX;
-    float agg[W][W];  // [ey + R][ex + R]: window centred at p + (ey, ex)
-#pragma unroll
-    for (int i = 0; i < W; ++i)
-#pragma unroll
-      for (int j = 0; j < W; ++j) agg[i][j] = 0.0f;
+    float h[2 * M + 1][W];  // h[dy + M][ex + R]: field row dy summed over dx in ex +- R
 #pragma unroll
     for (int dy = -M; dy <= M; ++dy) {
       float d[2 * M + 1];
+      const bool row_in = r + dy >= 0 && r + dy < RY;
 #pragma unroll
       for (int dx = -M; dx <= M; ++dx) {
-        const int rq = r + dy, cq = c + dx;
-        const bool in = rq >= 0 && rq < RY && cq >= 0 && cq < RX;
-        float v = 0.0f;
-        if (dy == 0 && dx == 0) {
-          v = 0.0f;
-        } else if (dy > 0 || (dy == 0 && dx > 0)) {
-          if (in) v = T[fwd_index<W>(dy, dx) * NR + p];
+        if (dy > 0 || (dy == 0 && dx > 0)) {
+          d[dx + M] = T[fwd_index<W>(dy, dx) * NR + p];  // 0 when p + delta is outside
+        } else if (dy == 0 && dx == 0) {
+          d[dx + M] = 0.0f;
         } else {
-          if (in) v = T[fwd_index<W>(-dy, -dx) * NR + rq * RX + cq];
+          const int cq = c + dx;
+          d[dx + M] = (row_in && cq >= 0 && cq < RX)
+                          ? T[fwd_index<W>(-dy, -dx) * NR + p + dy * RX + dx]
+                          : 0.0f;
         }
-        d[dx + M] = v;
       }
-      // row sums of width w at the 2R+1 window columns ex
-      float h[W];
-#pragma unroll
-      for (int ex = -R; ex <= R; ++ex) {
-        float s = 0.0f;
-#pragma unroll
-        for (int k = ex - R; k <= ex + R; ++k) s += d[k + M];
-        h[ex + R] = s;
-      }
-      // column accumulation: window rows ey with |dy - ey| <= R
-#pragma unroll
-      for (int ey = -R; ey <= R; ++ey) {
-        if (dy < ey - R || dy > ey + R) continue;
-#pragma unroll
-        for (int ex = -R; ex <= R; ++ex) agg[ey + R][ex + R] += h[ex + R];
-      }
+      box_sums<W>(d, h[dy + M]);
     }
     // window centred at region (r + ey, c + ex) = output (r + ey - R, c + ex - R)
 #pragma unroll
-    for (int ey = -R; ey <= R; ++ey)
+    for (int ex = -R; ex <= R; ++ex) {
+      float col[2 * M + 1], v[W];
 #pragma unroll
-      for (int ex = -R; ex <= R; ++ex) {
-        const int oy = r + ey - R, ox = c + ex - R;
+      for (int k = 0; k <= 2 * M; ++k) col[k] = h[k][ex + R];
+      box_sums<W>(col, v);
+      const int ox = c + ex - R;
+#pragma unroll
+      for (int ey = -R; ey <= R; ++ey) {
+        const int oy = r + ey - R;
         if (oy >= 0 && oy < kRTY && ox >= 0 && ox < kRTX) {
           const int j = (R - ey) * W + (R - ex);  // p's index in that window
-          A[j * G::THREADS + oy * kRTX + ox] = agg[ey + R][ex + R];
+          A[j * G::THREADS + oy * kRTX + ox] = v[ey + R];
         }
       }
+    }
   }
   __syncthreads();
 
