@@ -101,34 +101,18 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline model
 
-# Thread instructions (predicated on) per output pixel of the pair-reuse BVDF
-# exact kernel, measured with ncu on a 6144 x 6144 capture (the arctangent is
-# CUDA's atan2f, whose instruction count the source does not fix)
-MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 5): 4668}
-# DRAM bytes (read + write) per output pixel from the same capture
-MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 5): 7.09}
-
-
-# FP32-pipe instructions per pair / per sample of each kernel, counted from the
-# kernel source (vf_kernels.cuh); MUFU (SFU) operations separately.  FFMA,
-# FADD, FMUL, FMNMX, FSETP/FSEL each count as one.
-def ops_per_pixel(crit, approx, deg, w):
-    n = w * w
-    P = n * (n - 1) // 2
-    if crit == "vmf":
-        return P * 8 + n, P          # 3 sub, mul + 2 fma, 2 agg adds; argmin
-    if crit == "bvdf":
-        if approx == "exact":
-            return MEASURED_INST_PER_PIXEL.get((crit, approx, w)), None
-        # dot 3, rr 1, z 2, cross 9, t2 3, 1+z 1, two Horner chains 2 deg,
-        # select 2, 2 agg adds; rcp + sqrt on MUFU
-        return P * (23 + 2 * deg) + n, 2 * P
-    if crit in ("amnfe", "amnfg"):
-        per_e = {"exact": None, "poly": deg, "rational": 10}[approx]
-        if per_e is None:
-            return None, None
-        return P * 7 + n * (14 + per_e), n * (1 + (approx == "rational"))
-    return None, None                # EVMF: data-dependent switch fraction
+# Thread instructions (predicated on) per output pixel of the kernels that
+# can dominate the step, from ncu captures on 6144 x 6144 (thread_inst_executed
+# with the predicate on; the kernels' instruction counts are not fixed by the
+# source: atan2f, the EVMF switch fraction, the pair-reuse tile borders).
+# Keyed (criterion, approx, degree, window); degree 0 for exact / rational.
+MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 0, 5): 4896, ("bvdf", "poly", 4, 5): 3606,
+                           ("evmf", "poly", 4, 5): 1932, ("amnfe", "rational", 0, 5): 1637,
+                           ("vmf", "exact", 0, 5): 2139}
+# DRAM bytes (read + write) per output pixel from the same captures
+MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 0, 5): 7.10, ("bvdf", "poly", 4, 5): 7.09,
+                                 ("evmf", "poly", 4, 5): 6.90, ("amnfe", "rational", 0, 5): 7.11,
+                                 ("vmf", "exact", 0, 5): 7.09}
 
 
 def main():
@@ -209,16 +193,19 @@ def main():
     per = {vkey(c, a, d, w): [] for (c, a, d, w, k) in launches}
 
     def step(record):
+        """One step; record: events around every launch (True), around the
+        launches of one kernel class (its key), or none (False)."""
         for i, (c, a, d, w, k) in enumerate(launches):
             slot = (step.counter + i) % POOL
             src = pool_in[(slot // 3) * 3 + k]  # a copy of image k, rotating
+            rec = record is True or record == vkey(c, a, d, w)
             # the current stream: the bench stream, or the capture stream below
-            if record:
+            if rec:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record()
             vfilt.filter(src, pool_out[slot], criterion=c, window=w, approx=a, degree=max(d, 2))
-            if record:
+            if rec:
                 e1.record()
                 per[vkey(c, a, d, w)].append((e0, e1))
         step.counter += len(launches)
@@ -267,21 +254,28 @@ def main():
         graph.replay()
     torch.cuda.synchronize()
 
-    clocks = Clocks(local)
-    clocks.start()
-    ms_eager, host_eager = timed(lambda: step(False))
-    ms_graph, host_graph = timed(graph.replay) if graph is not None else (ms_eager, host_eager)
-    ck = clocks.stop()
-    # per-launch device times: a separate pass with events around each launch
+    # per-launch device times (untimed pass, events around every launch): the
+    # per-variant table and the kernel with the largest share of the step
     for _ in range(2):
         step(True)
     torch.cuda.synchronize()
+    kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v) for k, v in per.items()}
+    dom = max(kern_ms, key=kern_ms.get)  # every class runs 3 launches per step
+    per[dom] = []
+
+    clocks = Clocks(local)
+    clocks.start()
+    # eager steps: events only around the dominant kernel's launches, whose
+    # mean duration inside this timed region is the roofline's denominator
+    ms_eager, host_eager = timed(lambda: step(dom))
+    ms_graph, host_graph = timed(graph.replay) if graph is not None else (ms_eager, host_eager)
+    ck = clocks.stop()
+    dom_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in per[dom])
 
     pix_per_step = len(launches) * H * W
     ms_total = ms_graph
     value = pix_per_step * args.steps * world / (ms_total / 1e3) / 1e6
     value_eager = pix_per_step * args.steps * world / (ms_eager / 1e3) / 1e6
-    kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v) for k, v in per.items()}
 
     # per filter / window: exact vs fastest minimax meeting the 0.05 dB bar
     pfw = {}
@@ -307,12 +301,11 @@ def main():
             pfw["%s/w%d" % (crit, w)] = ent
 
     # roofline: the kernel with the largest share of the step
-    share = {k: v * args.steps * 3 for k, v in kern_ms.items()}
-    dom = max(share, key=share.get)
     c, a, wtag = dom.split("/")
-    d = int(a[4:]) if a.startswith("poly") else 4
+    d = int(a[4:]) if a.startswith("poly") else 0
     a = "poly" if a.startswith("poly") else a
-    fp32, mufu = ops_per_pixel(c, a, d, int(wtag[1:]))
+    mkey = (c, a, d, int(wtag[1:]))
+    inst = MEASURED_INST_PER_PIXEL.get(mkey)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -320,23 +313,27 @@ def main():
     except OSError:
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tinst = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lane-instructions/s
+    # issue rate: 4 schedulers x 32 lanes x 1 instruction per clock per SM
+    peak_tinst = 152 * 128 * sm_max * 1e6 / 1e12  # thread instructions/s
     roof = {"bound": "alu", "kernel": dom, "unit": "Tinst/s", "peak": round(peak_tinst, 2),
-            "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (recipe unit counts and max "
-                           "clock)" % sm_max,
+            "peak_source": "152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x %.0f MHz "
+                           "(recipe unit counts and max clock)" % sm_max,
             "traffic": None}
-    dram = MEASURED_DRAM_BYTES_PER_PIXEL.get((c, a, int(wtag[1:])))
+    dram = MEASURED_DRAM_BYTES_PER_PIXEL.get(mkey)
     if dram is not None:
         roof["traffic"] = round(dram * H * W)
         roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled "
                                 "from a 6144 x 6144 capture by pixels; algorithmic 8 B/px")
-    if fp32 is not None:
-        ach = fp32 * H * W / (kern_ms[dom] / 1e3) / 1e12
+    roof["launch_ms"] = round(dom_ms, 4)
+    if inst is not None:
+        ach = inst * H * W / (dom_ms / 1e3) / 1e12
         roof.update({"achieved": round(ach, 3), "frac": round(ach / peak_tinst, 4),
-                     "ops_per_pixel": fp32, "mufu_per_pixel": mufu})
+                     "inst_per_pixel": inst,
+                     "inst_source": "thread instructions (predicated on) per pixel, ncu on "
+                                    "6144 x 6144 (profiles/kernels_w5_6144.md)"})
     else:
         roof.update({"achieved": None, "frac": None,
-                     "note": "per-pixel FP32 count of this kernel is not fixed by the source"})
+                     "note": "no instruction count measured for this kernel"})
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpixels/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
