@@ -255,11 +255,13 @@ def main():
     torch.cuda.synchronize()
 
     # per-launch device times (untimed pass, events around every launch): the
-    # per-variant table and the kernel with the largest share of the step
-    for _ in range(2):
+    # per-variant table and the kernel with the largest share of the step.
+    # Medians of 15 launches: an event pair also spans any wait of the GPU
+    # for the host's next launch, and the host pauses now and then.
+    for _ in range(5):
         step(True)
     torch.cuda.synchronize()
-    kern_ms = {k: statistics.mean(e0.elapsed_time(e1) for e0, e1 in v) for k, v in per.items()}
+    kern_ms = {k: statistics.median(e0.elapsed_time(e1) for e0, e1 in v) for k, v in per.items()}
     dom = max(kern_ms, key=kern_ms.get)  # every class runs 3 launches per step
     per[dom] = []
 
