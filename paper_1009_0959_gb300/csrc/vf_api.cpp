@@ -291,7 +291,8 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
                                            : (ctx->pair_reuse == 1 && reuse_pays(cls.w, cls.crit));
   if (cls.precision == VF_FP32 && reuse) {
     L.tiles_x = (width + kTX - 1) / kTX;
-    const long long rgrid = (long long)L.tiles_x * ((height + kReuseTileRows - 1) / kReuseTileRows);
+    const int rows = reuse_tile_rows(cls.w, cls.crit);
+    const long long rgrid = (long long)L.tiles_x * ((height + rows - 1) / rows);
     if (rgrid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
     cudaError_t e = launch_reuse(L, cls.crit, cls.w, cls.apx, cls.deg, (int)rgrid, s);
     if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));

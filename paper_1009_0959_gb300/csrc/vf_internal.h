@@ -78,10 +78,16 @@ VF_DECLARE_PACKED(bf16)
 #undef VF_DECLARE_PACKED
 constexpr int kPackedTileCols = 64;
 
-// Pair-reuse launchers (vf_r_w<w>_<sel|amnf>.cu): one CTA covers 32 x 8
-// outputs; windows 3, 5 (whole term table) and 7 (table built one offset row
-// at a time), VMF / BVDF / AMNFE / AMNFG in FP32.
+// Pair-reuse launchers (vf_r_w<w>_<sel|amnf>.cu): one CTA covers 32 x 8 or
+// 32 x 16 outputs; windows 3, 5 (whole term table) and 7 (table built one
+// offset row at a time), VMF / BVDF / AMNFE / AMNFG in FP32.
 constexpr int kReuseTileRows = 8;
+// Output rows of a single-image pair-reuse tile: 16 for BVDF 3 x 3 and 5 x 5
+// (a 512-thread CTA; fewer terms and box sums per output on the taller
+// region: 36 x 20 / 512 = 1.41 region pixels per output at w = 5 instead of
+// 36 x 12 / 256 = 1.69; measured 5-8 % faster), 8 otherwise.  The batched
+// kernel always uses 8.
+constexpr int reuse_tile_rows(int w, int crit) { return (w <= 5 && crit == kBVDF) ? 16 : 8; }
 cudaError_t launch_reuse_sel_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w5(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w3(const Launch&, int, int, int, int, cudaStream_t);

@@ -27,22 +27,22 @@ namespace vf {
 
 constexpr int kRTX = 32, kRTY = 8;  // outputs per reuse tile
 
-template <int W>
+template <int W, int RTY = kRTY>
 struct ReuseGeom {
   static constexpr int R = W / 2;
   static constexpr int RX = kRTX + W - 1;     // region columns
-  static constexpr int RY = kRTY + W - 1;     // region rows
+  static constexpr int RY = RTY + W - 1;      // region rows
   static constexpr int NR = RX * RY;          // region pixels
   static constexpr int N = W * W;             // window samples
   static constexpr int M = W - 1;             // largest offset per axis
   static constexpr int ND = M * (2 * M + 1) + M;  // forward half-plane offsets = 2w(w-1)
-  static constexpr int THREADS = kRTX * kRTY;
+  static constexpr int THREADS = kRTX * RTY;
 };
 
-inline size_t reuse_smem_bytes(int w) {
-  size_t rx = kRTX + w - 1, ry = kRTY + w - 1, nr = rx * ry, m = w - 1;
+inline size_t reuse_smem_bytes(int w, int rty = kRTY) {
+  size_t rx = kRTX + w - 1, ry = rty + w - 1, nr = rx * ry, m = w - 1;
   size_t nd = m * (2 * m + 1) + m;
-  return nr * 20 + nd * nr * 4 + (size_t)w * w * kRTX * kRTY * 4;
+  return nr * 20 + nd * nr * 4 + (size_t)w * w * kRTX * rty * 4;
 }
 
 // index of forward offset (dy, dx): dy = 0 -> dx - 1; dy > 0 -> M + (dy-1)(2M+1) + dx + M
@@ -54,11 +54,11 @@ __host__ __device__ constexpr int fwd_index(int dy, int dx) {
 // Phase 3 of the reuse kernels: each output thread reads the n aggregates
 // of its window from the slots A[i * THREADS + thread] and selects (argmin,
 // lowest index) or weights (AMNF) exactly as the per-window kernel does.
-template <int W, int CRIT, int APX, int DEG>
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY>
 __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
                                              const uint32_t* raw, const float* A, int x0,
                                              int y0) {
-  using G = ReuseGeom<W>;
+  using G = ReuseGeom<W, RTY>;
   constexpr int R = G::R, RX = G::RX, N = G::N;
   const int ox = threadIdx.x % kRTX, oy = threadIdx.x / kRTX;
   const int gx = x0 + ox, gy = y0 + oy;
@@ -136,9 +136,9 @@ __device__ __forceinline__ void box_sums(const float (&v)[2 * W - 1], float (&ou
   }
 }
 
-template <int W, int CRIT, int APX, int DEG>
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY>
 __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
-  using G = ReuseGeom<W>;
+  using G = ReuseGeom<W, RTY>;
   constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M, ND = G::ND;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* px = reinterpret_cast<float4*>(smem);
@@ -146,7 +146,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   float* T = reinterpret_cast<float*>(smem + NR * 20);   // [ND][NR]
   float* A = T + ND * NR;                                  // [N][THREADS]
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
-  const int x0 = txi * kRTX, y0 = tyi * kRTY;
+  const int x0 = txi * kRTX, y0 = tyi * RTY;
 
   TileSmem t;
   t.px = px;
@@ -224,7 +224,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
 #pragma unroll
       for (int ey = -R; ey <= R; ++ey) {
         const int oy = r + ey - R;
-        if (oy >= 0 && oy < kRTY && ox >= 0 && ox < kRTX) {
+        if (oy >= 0 && oy < RTY && ox >= 0 && ox < kRTX) {
           const int j = (R - ey) * W + (R - ex);  // p's index in that window
           A[j * G::THREADS + oy * kRTX + ox] = v[ey + R];
         }
@@ -234,7 +234,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   __syncthreads();
 
   // 3. selection / weighting per output
-  reuse_finish<W, CRIT, APX, DEG>(L, px, raw, A, x0, y0);
+  reuse_finish<W, CRIT, APX, DEG, RTY>(L, px, raw, A, x0, y0);
 }
 
 // Chunked form for large windows, where the whole term table would not fit in
@@ -361,33 +361,38 @@ __device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
 
 // One 32 x 8 tile per CTA (a 256-thread CTA whose shared memory is reused:
 // callers looping over tiles must __syncthreads() between calls).
-template <int W, int CRIT, int APX, int DEG>
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY>
 __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
   if constexpr (W >= 7) {
+    static_assert(RTY == kRTY, "the chunked form has 32 x 8 tiles");
     reuse_chunked_tile<W, CRIT, APX, DEG>(L, tile);
   } else {
-    reuse_tile<W, CRIT, APX, DEG>(L, tile);
+    reuse_tile<W, CRIT, APX, DEG, RTY>(L, tile);
   }
 }
 
-inline size_t reuse_any_smem_bytes(int w) {
-  return w >= 7 ? reuse_chunked_smem_bytes(w) : reuse_smem_bytes(w);
+inline size_t reuse_any_smem_bytes(int w, int rty = kRTY) {
+  return w >= 7 ? reuse_chunked_smem_bytes(w) : reuse_smem_bytes(w, rty);
 }
 
-template <int W, int CRIT, int APX, int DEG>
-__global__ void __launch_bounds__(kRTX* kRTY, 2) reuse_kernel(const __grid_constant__ Launch L) {
-  reuse_any_tile<W, CRIT, APX, DEG>(L, blockIdx.x);
+// 32 x RTY outputs per CTA: two 256-thread CTAs per SM at RTY = 8, one
+// 512-thread CTA at RTY = 16 (its term table is 1.6x larger, its region /
+// tile ratio 1.41 instead of 1.69)
+template <int W, int CRIT, int APX, int DEG, int RTY>
+__global__ void __launch_bounds__(kRTX* RTY, RTY == kRTY ? 2 : 1)
+    reuse_kernel(const __grid_constant__ Launch L) {
+  reuse_any_tile<W, CRIT, APX, DEG, RTY>(L, blockIdx.x);
 }
 
-template <int W, int CRIT, int APX, int DEG>
+template <int W, int CRIT, int APX, int DEG, int RTY = reuse_tile_rows(W, CRIT)>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
-  const size_t smem = reuse_any_smem_bytes(W);
+  const size_t smem = reuse_any_smem_bytes(W, RTY);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG>,
+    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG, RTY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  reuse_kernel<W, CRIT, APX, DEG><<<grid, kRTX * kRTY, smem, s>>>(L);
+  reuse_kernel<W, CRIT, APX, DEG, RTY><<<grid, kRTX * RTY, smem, s>>>(L);
   return cudaGetLastError();
 }
 
