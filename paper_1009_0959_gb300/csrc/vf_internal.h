@@ -82,12 +82,16 @@ constexpr int kPackedTileCols = 64;
 // 32 x 16 outputs; windows 3, 5 (whole term table) and 7 (table built one
 // offset row at a time), VMF / BVDF / AMNFE / AMNFG in FP32.
 constexpr int kReuseTileRows = 8;
-// Output rows of a single-image pair-reuse tile: 16 for BVDF 3 x 3 and 5 x 5
-// (a 512-thread CTA; fewer terms and box sums per output on the taller
-// region: 36 x 20 / 512 = 1.41 region pixels per output at w = 5 instead of
-// 36 x 12 / 256 = 1.69; measured 5-8 % faster), 8 otherwise.  The batched
-// kernel always uses 8.
-constexpr int reuse_tile_rows(int w, int crit) { return (w <= 5 && crit == kBVDF) ? 16 : 8; }
+// Output rows of a single-image pair-reuse tile: taller tiles for BVDF 3 x 3
+// (14 rows) and 5 x 5 (20 rows), whose CTA has one thread per region pixel
+// (34 x 16 = 544, 36 x 24 = 864): fewer region pixels per output (1.35 at
+// w = 5 instead of 36 x 12 / 256 = 1.69), both phases in whole rounds and,
+// at w = 5, 27 warps per SM instead of 16 (measured 5,350 / 9,278 Mpix/s
+// for the exact / degree-4 5 x 5 filter against 3,681 / 6,801 with 32 x 8
+// tiles); 8 otherwise.  The batched kernel always uses 8.
+constexpr int reuse_tile_rows(int w, int crit) {
+  return crit != kBVDF ? 8 : (w == 5 ? 20 : (w == 3 ? 14 : 8));
+}
 cudaError_t launch_reuse_sel_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w5(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w3(const Launch&, int, int, int, int, cudaStream_t);

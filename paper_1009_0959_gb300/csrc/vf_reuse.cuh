@@ -27,7 +27,7 @@ namespace vf {
 
 constexpr int kRTX = 32, kRTY = 8;  // outputs per reuse tile
 
-template <int W, int RTY = kRTY>
+template <int W, int RTY = kRTY, int NT = kRTX * RTY>
 struct ReuseGeom {
   static constexpr int R = W / 2;
   static constexpr int RX = kRTX + W - 1;     // region columns
@@ -36,13 +36,21 @@ struct ReuseGeom {
   static constexpr int N = W * W;             // window samples
   static constexpr int M = W - 1;             // largest offset per axis
   static constexpr int ND = M * (2 * M + 1) + M;  // forward half-plane offsets = 2w(w-1)
-  static constexpr int THREADS = kRTX * RTY;
+  static constexpr int THREADS = NT;         // threads of the CTA
+  static constexpr int OUT = kRTX * RTY;      // outputs of the tile
 };
 
 inline size_t reuse_smem_bytes(int w, int rty = kRTY) {
   size_t rx = kRTX + w - 1, ry = rty + w - 1, nr = rx * ry, m = w - 1;
   size_t nd = m * (2 * m + 1) + m;
   return nr * 20 + nd * nr * 4 + (size_t)w * w * kRTX * rty * 4;
+}
+
+// Threads of a reuse CTA: one per output at 8 rows; for taller tiles one per
+// region pixel (rounded up to whole warps), so that the term items and the
+// box sums of phase 2 split into whole rounds
+constexpr int reuse_threads(int w, int rty) {
+  return rty == kRTY ? kRTX * rty : ((kRTX + w - 1) * (rty + w - 1) + 31) / 32 * 32;
 }
 
 // index of forward offset (dy, dx): dy = 0 -> dx - 1; dy > 0 -> M + (dy-1)(2M+1) + dx + M
@@ -52,29 +60,32 @@ __host__ __device__ constexpr int fwd_index(int dy, int dx) {
 }
 
 // Phase 3 of the reuse kernels: each output thread reads the n aggregates
-// of its window from the slots A[i * THREADS + thread] and selects (argmin,
+// of its window from the slots A[i * OUT + output] and selects (argmin,
 // lowest index) or weights (AMNF) exactly as the per-window kernel does.
-template <int W, int CRIT, int APX, int DEG, int RTY = kRTY>
+// Threads beyond the tile's outputs only join the counters' reduction.
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
 __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
                                              const uint32_t* raw, const float* A, int x0,
                                              int y0) {
-  using G = ReuseGeom<W, RTY>;
+  using G = ReuseGeom<W, RTY, NT>;
   constexpr int R = G::R, RX = G::RX, N = G::N;
   const int ox = threadIdx.x % kRTX, oy = threadIdx.x / kRTX;
   const int gx = x0 + ox, gy = y0 + oy;
-  const bool valid = gx < L.width && gy < L.height;
+  const bool mine = (int)threadIdx.x < G::OUT;
+  const bool valid = mine && gx < L.width && gy < L.height;
   const float* sagg = A + threadIdx.x;
   int ties = 0;
-  if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+  if (!mine) {
+  } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
     const float4 xc = px[(oy + R) * RX + ox + R];
     const uint32_t rawc = raw[(oy + R) * RX + ox + R];
     uint32_t v = rawc;
-    if (sagg[(N / 2) * G::THREADS] != 0.0f) {  // not a constant window
+    if (sagg[(N / 2) * G::OUT] != 0.0f) {  // not a constant window
       float wsum = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         const float4 xi = px[(oy + i / W) * RX + ox + i % W];
-        const float rh = rcp_approx(L.kappa_scale * sagg[i * G::THREADS]);
+        const float rh = rcp_approx(L.kappa_scale * sagg[i * G::OUT]);
         const float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
         float u;
         if constexpr (CRIT == kAMNFE) {
@@ -99,7 +110,7 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
     if (valid) store_px(L, gx, gy, v);
   } else {
     const Selection s =
-        select_min<W, false>(nullptr, sagg, G::THREADS, px, RX, ox, oy, L.stats != nullptr);
+        select_min<W, false>(nullptr, sagg, G::OUT, px, RX, ox, oy, L.stats != nullptr);
     if (valid) store_px(L, gx, gy, raw[(oy + s.best / W) * RX + ox + s.best % W]);
     ties = s.near_tie;
   }
@@ -136,15 +147,15 @@ __device__ __forceinline__ void box_sums(const float (&v)[2 * W - 1], float (&ou
   }
 }
 
-template <int W, int CRIT, int APX, int DEG, int RTY = kRTY>
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
 __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
-  using G = ReuseGeom<W, RTY>;
+  using G = ReuseGeom<W, RTY, NT>;
   constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M, ND = G::ND;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* px = reinterpret_cast<float4*>(smem);
   uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
   float* T = reinterpret_cast<float*>(smem + NR * 20);   // [ND][NR]
-  float* A = T + ND * NR;                                  // [N][THREADS]
+  float* A = T + ND * NR;                                  // [N][OUT]
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kRTX, y0 = tyi * RTY;
 
@@ -160,30 +171,34 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   //    2w - 1 terms each, spread over all threads so that they reach the
   //    barrier together; consecutive threads take consecutive pixels.  An
   //    entry whose partner p + delta lies outside the region is 0, so the
-  //    forward reads of phase 2 need no bounds test.
-  auto row_terms = [&](const auto& term) {
-    for (int item = threadIdx.x; item < (M + 1) * NR; item += G::THREADS) {
-      const int dy = item / NR, p = item - dy * NR;
+  //    forward reads of phase 2 need no bounds test.  Work items are (offset
+  //    column dx, region pixel p), w - 1 or w terms each (dy = 0 only for
+  //    dx > 0): (2w - 1) x region items of nearly equal cost, so the last
+  //    round leaves few threads idle.
+  auto row_terms = [&](const auto& term, const auto* src) {
+    for (int item = threadIdx.x; item < (2 * M + 1) * NR; item += G::THREADS) {
+      const int dxi = item / NR, p = item - dxi * NR;
+      const int dx = dxi - M;
       const int r = p / RX, c = p - r * RX;
-      const bool row_in = r + dy < RY;
-      const float4 xp = px[p];
+      const bool col_in = c + dx >= 0 && c + dx < RX;
+      const auto xp = load_sample(src + p);
 #pragma unroll
-      for (int dx = -M; dx <= M; ++dx) {
+      for (int dy = 0; dy <= M; ++dy) {
         if (dy == 0 && dx <= 0) continue;
         float v = 0.0f;
-        if (row_in && c + dx >= 0 && c + dx < RX) v = term(xp, px[p + dy * RX + dx]);
+        if (col_in && r + dy < RY) v = term(xp, load_sample(src + p + dy * RX + dx));
         T[fwd_index<W>(dy, dx) * NR + p] = v;
       }
     }
   };
   if constexpr (CRIT == kVMF) {
-    row_terms(TermL2{});
+    row_terms(TermL2U8{}, raw);  // packed bytes: exact squared distances
   } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
-    row_terms(TermL1{});
+    row_terms(TermL1{}, px);
   } else if constexpr (APX == kExact) {
-    row_terms(TermAngleExact{});
+    row_terms(TermAngleExact{}, px);
   } else {
-    row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b));
+    row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b), px);
   }
   __syncthreads();
 
@@ -226,7 +241,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
         const int oy = r + ey - R;
         if (oy >= 0 && oy < RTY && ox >= 0 && ox < kRTX) {
           const int j = (R - ey) * W + (R - ex);  // p's index in that window
-          A[j * G::THREADS + oy * kRTX + ox] = v[ey + R];
+          A[j * G::OUT + oy * kRTX + ox] = v[ey + R];
         }
       }
     }
@@ -234,7 +249,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   __syncthreads();
 
   // 3. selection / weighting per output
-  reuse_finish<W, CRIT, APX, DEG, RTY>(L, px, raw, A, x0, y0);
+  reuse_finish<W, CRIT, APX, DEG, RTY, NT>(L, px, raw, A, x0, y0);
 }
 
 // Chunked form for large windows, where the whole term table would not fit in
@@ -361,13 +376,13 @@ __device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
 
 // One 32 x 8 tile per CTA (a 256-thread CTA whose shared memory is reused:
 // callers looping over tiles must __syncthreads() between calls).
-template <int W, int CRIT, int APX, int DEG, int RTY = kRTY>
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
 __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
   if constexpr (W >= 7) {
-    static_assert(RTY == kRTY, "the chunked form has 32 x 8 tiles");
+    static_assert(RTY == kRTY && NT == kRTX * kRTY, "the chunked form has 32 x 8 tiles");
     reuse_chunked_tile<W, CRIT, APX, DEG>(L, tile);
   } else {
-    reuse_tile<W, CRIT, APX, DEG, RTY>(L, tile);
+    reuse_tile<W, CRIT, APX, DEG, RTY, NT>(L, tile);
   }
 }
 
@@ -375,24 +390,25 @@ inline size_t reuse_any_smem_bytes(int w, int rty = kRTY) {
   return w >= 7 ? reuse_chunked_smem_bytes(w) : reuse_smem_bytes(w, rty);
 }
 
-// 32 x RTY outputs per CTA: two 256-thread CTAs per SM at RTY = 8, one
-// 512-thread CTA at RTY = 16 (its term table is 1.6x larger, its region /
-// tile ratio 1.41 instead of 1.69)
-template <int W, int CRIT, int APX, int DEG, int RTY>
-__global__ void __launch_bounds__(kRTX* RTY, RTY == kRTY ? 2 : 1)
+// 32 x RTY outputs per CTA of NT threads: two 256-thread CTAs per SM at
+// RTY = 8; one CTA of a thread per region pixel for taller tiles (a larger
+// term table, fewer region pixels per output, phases in whole rounds)
+template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     reuse_kernel(const __grid_constant__ Launch L) {
-  reuse_any_tile<W, CRIT, APX, DEG, RTY>(L, blockIdx.x);
+  reuse_any_tile<W, CRIT, APX, DEG, RTY, NT>(L, blockIdx.x);
 }
 
-template <int W, int CRIT, int APX, int DEG, int RTY = reuse_tile_rows(W, CRIT)>
+template <int W, int CRIT, int APX, int DEG, int RTY = reuse_tile_rows(W, CRIT),
+          int NT = reuse_threads(W, RTY)>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
   const size_t smem = reuse_any_smem_bytes(W, RTY);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG, RTY>,
+    cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG, RTY, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  reuse_kernel<W, CRIT, APX, DEG, RTY><<<grid, kRTX * RTY, smem, s>>>(L);
+  reuse_kernel<W, CRIT, APX, DEG, RTY, NT><<<grid, NT, smem, s>>>(L);
   return cudaGetLastError();
 }
 
