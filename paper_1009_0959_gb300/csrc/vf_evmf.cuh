@@ -32,7 +32,7 @@ inline size_t evmf_queue_smem_bytes(int w, int ty) {
 }
 
 template <int W, int APX, int DEG, bool REG = uses_reg_path(W, kEVMF)>
-__global__ void __launch_bounds__(256) evmf_queue_kernel(const __grid_constant__ Launch L,
+__global__ void __launch_bounds__(256, 3) evmf_queue_kernel(const __grid_constant__ Launch L,
                                                          int ntiles) {
   constexpr int N = W * W, R = W / 2;
   const int T = blockDim.x, TY = T / kTX, CAP = 2 * T;
