@@ -132,6 +132,8 @@ def main():
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--pair-reuse", type=int, default=1,
                     help="profiling: VF_OPT_PAIR_REUSE for --case (0 never, 1 auto, 2 always)")
+    ap.add_argument("--overlap-launch", type=int, default=1, choices=[0, 1],
+                    help="VF_OPT_OVERLAP_LAUNCH: programmatic dependent launches (default 1)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -164,6 +166,7 @@ def main():
     pool_in = [dev_imgs[k % 3].clone() for k in range(POOL)]
     pool_out = [torch.empty_like(pool_in[0]) for _ in range(POOL)]
     V = variants()
+    vfilt.set_option("overlap_launch", args.overlap_launch)
     launches = [(c, a, d, w, k) for w in WINDOWS for (c, a, d) in V for k in range(3)]
 
     # quality (outside the timed region): PSNR vs clean, drop vs the exact path
@@ -348,6 +351,7 @@ def main():
                        "l2": "inputs rotate through a %d MB pool (> 129 MB L2)" %
                              (POOL * 8),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "overlap_launch": args.overlap_launch,
                        "launch": ("one step captured as a CUDA graph of its vf_filter calls, "
                                   "replayed K times") if graph is not None else
                                  "vf_filter calls (graph capture failed: %s)" % graph_error},

@@ -114,8 +114,20 @@ const char* vf_last_error(const vf_ctx* ctx);
  *   VF_OPT_GATE_TENSOR_CORES  1 (default): vf_gate_infer runs the three
  *                      convolutions on the tensor cores (mma, BF16 operands:
  *                      activations rounded to BF16 between layers, FP32
- *                      accumulation); 0: CUDA cores with FP32 activations. */
-typedef enum { VF_OPT_PAIR_REUSE = 0, VF_OPT_TILE_ROWS = 1, VF_OPT_GATE_TENSOR_CORES = 2 } vf_option;
+ *                      accumulation); 0: CUDA cores with FP32 activations.
+ *   VF_OPT_OVERLAP_LAUNCH  1 (default): vf_filter's kernels are launched as
+ *                      programmatic dependents of the previous kernel in the
+ *                      stream: their CTAs may be scheduled while that kernel
+ *                      drains, and wait for its completion (and the
+ *                      visibility of its memory) before their first access
+ *                      to device memory, so stream order is kept; 0: plain
+ *                      launches. */
+typedef enum {
+  VF_OPT_PAIR_REUSE = 0,
+  VF_OPT_TILE_ROWS = 1,
+  VF_OPT_GATE_TENSOR_CORES = 2,
+  VF_OPT_OVERLAP_LAUNCH = 3
+} vf_option;
 vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value);
 
 /* window 3, VF_VMF, VF_EXACT, degree 4, FP32, kappa 0.33, exp_cutoff 10,

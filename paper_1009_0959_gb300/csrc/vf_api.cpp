@@ -50,6 +50,7 @@ struct vf_ctx {
   int tile_rows = 4;  // TY of the per-window single-image launches
   int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF), 2 always (w = 3 / 5)
   int gate_tc = 1;     // gate inference on the tensor cores (BF16 activations)
+  int overlap = 1;     // programmatic dependent launches for vf_filter
   // device staging of vf_filter_host (grown on demand, freed by vf_destroy)
   uint8_t* d_stage = nullptr;
   size_t stage_bytes = 0;
@@ -117,6 +118,7 @@ vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value) {
       ctx->pair_reuse = value;
       return VF_OK;
     case VF_OPT_GATE_TENSOR_CORES: ctx->gate_tc = value != 0; return VF_OK;
+    case VF_OPT_OVERLAP_LAUNCH: ctx->overlap = value != 0; return VF_OK;
     case VF_OPT_TILE_ROWS:
       if (value != 2 && value != 4 && value != 8) return fail(ctx, VF_ERR_ARG, "tile rows 2, 4 or 8");
       ctx->tile_rows = value;
@@ -215,6 +217,7 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   L.exp_cutoff = p->exp_cutoff;
   L.ent_cutoff = p->ent_cutoff < 0.0f ? default_ent_cutoff(n) : p->ent_cutoff;
   L.stats = d_stats;
+  L.pdl = ctx->overlap;
 
   // coefficients of the approximant, rounded to FP32, zero above the degree
   if (apx != kExact) {

@@ -35,6 +35,7 @@ template <int W, int APX, int DEG, bool REG = uses_reg_path(W, kEVMF)>
 __global__ void __launch_bounds__(256, 3) evmf_queue_kernel(const __grid_constant__ Launch L,
                                                          int ntiles) {
   constexpr int N = W * W, R = W / 2;
+  pdl_begin();
   const int T = blockDim.x, TY = T / kTX, CAP = 2 * T;
   const TileSmem t = carve(W, REG, TY, T);
   // the queue starts where the one-tile kernel keeps its compaction list (an
@@ -143,8 +144,7 @@ cudaError_t launch_evmf_queue(const Launch& L, int ty, int ntiles, cudaStream_t 
   if (grid < 1) grid = 1;
   const int per = (ntiles + grid - 1) / grid;  // tiles per CTA
   grid = (ntiles + per - 1) / per;
-  kern<<<grid, threads, smem, s>>>(L, ntiles);
-  return cudaGetLastError();
+  return launch_maybe_pdl(L.pdl != 0, kern, dim3(grid), dim3(threads), smem, s, L, ntiles);
 }
 
 }  // namespace vf

@@ -36,6 +36,7 @@ struct Launch {
   float ent_cutoff;
   Coeffs c;
   unsigned long long* stats;  // optional device counters
+  int pdl;                    // launch as a programmatic dependent (host side)
 };
 
 // Register aggregates (fully unrolled pair loop) or shared-memory aggregate

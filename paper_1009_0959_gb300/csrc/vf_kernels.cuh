@@ -24,6 +24,35 @@ namespace vf {
 
 // ---------------------------------------------------------------- helpers
 
+// Programmatic dependent launch (sm_90 and later).  A filter kernel launched
+// with programmatic stream serialisation may have its CTAs scheduled while
+// the previous kernel of the stream drains; griddepcontrol.wait then holds
+// them until that kernel has completed and its memory is visible, before
+// any device-memory access, so stream order is kept.  Right after, the
+// kernel allows its own successor to be scheduled (that one waits the same
+// way).  Without the launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `kern` with the programmatic-serialisation attribute when `pdl`.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t s, const Args&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -676,6 +705,7 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
 // One CTA per tile of one image.
 template <int W, int CRIT, int APX, int DEG>
 __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Launch L) {
+  pdl_begin();
   process_tile<W, CRIT, APX, DEG>(L, blockIdx.x);
 }
 

@@ -19,8 +19,8 @@ cudaError_t launch_one(const Launch& L, int ty, int grid, cudaStream_t s) {
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    filter_kernel<W, CRIT, APX, DEG><<<grid, kTX * ty, smem, s>>>(L);
-    return cudaGetLastError();
+    return launch_maybe_pdl(L.pdl != 0, filter_kernel<W, CRIT, APX, DEG>, dim3(grid),
+                            dim3(kTX * ty), smem, s, L);
   }
 }
 

@@ -285,6 +285,7 @@ __device__ __forceinline__ uint32_t packed_amnf_finish(const Launch& L, const fl
 
 template <int W, int CRIT, int APX, int DEG, class T>
 __global__ void __launch_bounds__(256) packed_kernel(const __grid_constant__ Launch L) {
+  pdl_begin();
   constexpr int R = W / 2;
   const int TY = blockDim.x / kTX;
   const PackedSmem<T> t = carve_packed<T>(W, TY);

@@ -13,8 +13,8 @@ cudaError_t launch_packed_one(const Launch& L, int ty, int grid, cudaStream_t s)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  packed_kernel<W, CRIT, APX, DEG, T><<<grid, kTX * ty, smem, s>>>(L);
-  return cudaGetLastError();
+  return launch_maybe_pdl(L.pdl != 0, packed_kernel<W, CRIT, APX, DEG, T>, dim3(grid),
+                          dim3(kTX * ty), smem, s, L);
 }
 
 // One window size and format.  The per-sample approximants of AMNF and EVMF run

@@ -396,6 +396,7 @@ inline size_t reuse_any_smem_bytes(int w, int rty = kRTY) {
 template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     reuse_kernel(const __grid_constant__ Launch L) {
+  pdl_begin();
   reuse_any_tile<W, CRIT, APX, DEG, RTY, NT>(L, blockIdx.x);
 }
 
@@ -408,8 +409,8 @@ cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  reuse_kernel<W, CRIT, APX, DEG, RTY, NT><<<grid, NT, smem, s>>>(L);
-  return cudaGetLastError();
+  return launch_maybe_pdl(L.pdl != 0, reuse_kernel<W, CRIT, APX, DEG, RTY, NT>, dim3(grid),
+                          dim3(NT), smem, s, L);
 }
 
 

@@ -135,7 +135,7 @@ def context():
     return ctx
 
 
-OPTIONS = {"pair_reuse": 0, "tile_rows": 1, "gate_tensor_cores": 2}
+OPTIONS = {"pair_reuse": 0, "tile_rows": 1, "gate_tensor_cores": 2, "overlap_launch": 3}
 
 
 def set_option(name: str, value: int):

@@ -243,3 +243,31 @@ def test_graph_capture_matches_eager(vf):
     torch.cuda.synchronize()
     for kw, e, o in zip(calls, eager, outs):
         assert torch.equal(e, o), kw
+
+
+def test_overlapped_launches_keep_stream_order(vf):
+    """A chain of filters, each reading the previous one's output, gives the
+    same bytes with programmatic dependent launches (default) as with plain
+    launches: every kernel waits for its predecessor before reading."""
+    clean, noisy = synth.noisy(300, 260, 0.25, 91)
+    src = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    chain = [dict(criterion="bvdf", window=5, approx="poly", degree=4),
+             dict(criterion="evmf", window=5), dict(criterion="vmf", window=3),
+             dict(criterion="amnfe", window=5, approx="rational"),
+             dict(criterion="bvdf", window=3), dict(criterion="evmf", window=7),
+             dict(criterion="vmf", window=5, precision="fp16x2")]
+
+    def run():
+        x = src
+        for kw in chain:
+            x = vf.filter(x, **kw)
+        torch.cuda.synchronize()
+        return x
+
+    try:
+        vf.set_option("overlap_launch", 0)
+        plain = run()
+    finally:
+        vf.set_option("overlap_launch", 1)
+    for _ in range(3):
+        assert torch.equal(run(), plain)
