@@ -301,10 +301,11 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
     if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
     return VF_OK;
   }
-  const int ty = ctx->tile_rows;
+  const int ty = ctx->tile_rows;  // thread rows of the CTA
   const int cols = cls.precision == VF_FP32 ? kTX : kPackedTileCols;
+  const int rows = cls.precision == VF_FP32 ? ty * outputs_per_thread(cls.w, cls.crit) : ty;
   L.tiles_x = (width + cols - 1) / cols;
-  const int tiles_y = (height + ty - 1) / ty;
+  const int tiles_y = (height + rows - 1) / rows;
   const long long grid = (long long)L.tiles_x * tiles_y;
   if (grid > 0x7fffffffLL) return fail(ctx, VF_ERR_UNSUPPORTED, "image too large");
   cudaError_t e = cls.precision == VF_FP32

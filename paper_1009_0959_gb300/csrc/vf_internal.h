@@ -43,6 +43,13 @@ struct Launch {
 // slots (rolled row-pair loop) for a window / criterion.
 constexpr bool uses_reg_path(int w, int crit) { return w == 3 || (w == 5 && crit != kBVDF); }
 
+// Output rows per thread of the single-image per-window kernels: two for
+// VMF and AMNF with w <= 5 (two vertically adjacent windows share w(w - 1)
+// samples and their pairs), one otherwise.
+constexpr int outputs_per_thread(int w, int crit) {
+  return (w <= 5 && (crit == kVMF || crit == kAMNFE || crit == kAMNFG)) ? 2 : 1;
+}
+
 // Shared memory bytes of one CTA of 32 x ty threads for window w (reg: the
 // aggregates live in registers, no shared-memory slots).
 inline size_t smem_bytes(int w, int crit, int ty, bool reg) {

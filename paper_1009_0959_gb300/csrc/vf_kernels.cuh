@@ -522,24 +522,15 @@ __device__ __forceinline__ void l1_aggregates_int_smem(const uint32_t* raw, int 
     reinterpret_cast<float*>(sagg)[i * stride] = (float)sagg[i * stride];
 }
 
-template <int W, bool REG, int CRIT, int APX, int DEG>
-__device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& t, int px, int py,
-                                               int stride, bool& tie) {
+// AMNF output of the window of (px, py) from its aggregates h_i (agg(i)):
+// weights w_i = h_i^-3 K((x_C - x_i) / h_i), weighted mean, rounded.
+template <int W, int CRIT, int APX, int DEG, class Agg>
+__device__ __forceinline__ uint32_t amnf_finish(const Launch& L, const TileSmem& t, int px, int py,
+                                                const Agg& agg, bool& tie) {
   constexpr int N = W * W, C = N / 2;
-  float aggr[N] = {};
-  float* sagg = t.agg + threadIdx.x;
-  if constexpr (REG) {
-    uint32_t iagg[N];
-    l1_aggregates_int<W>(t.raw, t.sw, px, py, iagg);
-#pragma unroll
-    for (int i = 0; i < N; ++i) aggr[i] = (float)iagg[i];
-  } else {
-    l1_aggregates_int_smem<W>(t.raw, t.sw, px, py, reinterpret_cast<uint32_t*>(sagg), stride);
-  }
   const float4 xc = t.px[(py + W / 2) * t.sw + px + W / 2];
   const uint32_t rawc = t.raw[(py + W / 2) * t.sw + px + W / 2];
-  float aggC = REG ? aggr[C] : sagg[C * stride];
-  if (aggC == 0.0f) {  // constant window: every h_i is 0, output the centre
+  if (agg(C) == 0.0f) {  // constant window: every h_i is 0, output the centre
     tie = false;
     return rawc;
   }
@@ -547,8 +538,7 @@ __device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& 
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
-    float ai = REG ? aggr[i] : sagg[i * stride];
-    float rh = rcp_approx(L.kappa_scale * ai);  // 1 / h_i
+    float rh = rcp_approx(L.kappa_scale * agg(i));  // 1 / h_i
     float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
     float u;
     if constexpr (CRIT == kAMNFE) {
@@ -564,11 +554,119 @@ __device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& 
   }
   float rw = 1.0f / wsum;
   float yx = ax * rw, yy = ay * rw, yz = az * rw;
+  tie = false;
   if (L.stats) {
     auto g = [](float v) { return fabsf(v - floorf(v) - 0.5f); };
     tie = fminf(g(yx), fminf(g(yy), g(yz))) < 1e-3f;
   }
   return pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
+}
+
+template <int W, bool REG, int CRIT, int APX, int DEG>
+__device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& t, int px, int py,
+                                               int stride, bool& tie) {
+  constexpr int N = W * W;
+  if constexpr (REG) {
+    uint32_t iagg[N];
+    l1_aggregates_int<W>(t.raw, t.sw, px, py, iagg);
+    float aggr[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) aggr[i] = (float)iagg[i];
+    return amnf_finish<W, CRIT, APX, DEG>(L, t, px, py, [&](int i) { return aggr[i]; }, tie);
+  } else {
+    uint32_t* sagg = reinterpret_cast<uint32_t*>(t.agg + threadIdx.x);
+    l1_aggregates_int_smem<W>(t.raw, t.sw, px, py, sagg, stride);
+    const float* fagg = t.agg + threadIdx.x;
+    return amnf_finish<W, CRIT, APX, DEG>(L, t, px, py,
+                                          [&](int i) { return fagg[i * stride]; }, tie);
+  }
+}
+
+// ---------------------------------------------------------------- two windows per thread
+
+// The windows of (px, py) and (px, py + 1) share the w(w - 1) samples of rows
+// py + 1 .. py + w - 1.  One thread forms both: the pairs among the shared
+// samples once (partial aggregates Cm), then each window's pairs with its own
+// extra row (row py for the upper, py + w for the lower window), starting
+// from Cm.  Pair terms for the two outputs: m(m - 1)/2 among the m = w(w - 1)
+// shared samples plus, per window, w(w - 1)/2 + w m with its extra row: 410
+// at w = 5 (205 per output instead of 300), 57 at w = 3 (28.5 instead of 36).
+// P::pair(a, b, x, y) adds the term of samples a, b to accumulators x and y.
+struct PairL1Int {  // AMNF: city-block distance, exact integer sums
+  using Acc = uint32_t;
+  static __device__ __forceinline__ Acc zero() { return 0u; }
+  static __device__ __forceinline__ void pair(uint32_t a, uint32_t b, Acc& x, Acc& y) {
+    x = __vsadu4(a, b) + x;
+    y = __vsadu4(a, b) + y;
+  }
+};
+struct PairL2 {  // VMF: Euclidean distance, one square root per pair
+  using Acc = float;
+  static __device__ __forceinline__ Acc zero() { return 0.0f; }
+  static __device__ __forceinline__ void pair(uint32_t a, uint32_t b, Acc& x, Acc& y) {
+    const float d = TermL2U8{}(a, b);
+    x += d;
+    y += d;
+  }
+};
+
+template <int W, class P>
+__device__ __forceinline__ void two_window_aggregates(const uint32_t* raw, int sw, int px, int py,
+                                                      typename P::Acc (&A)[W * W],
+                                                      typename P::Acc (&B)[W * W]) {
+  using Acc = typename P::Acc;
+  uint32_t X[W + 1][W];  // rows py .. py + w, fourth byte cleared
+#pragma unroll
+  for (int r = 0; r <= W; ++r)
+#pragma unroll
+    for (int c = 0; c < W; ++c) X[r][c] = load_sample(raw + (py + r) * sw + px + c);
+  Acc Cm[W - 1][W];  // shared rows 1 .. w - 1
+#pragma unroll
+  for (int r = 0; r < W - 1; ++r)
+#pragma unroll
+    for (int c = 0; c < W; ++c) Cm[r][c] = P::zero();
+#pragma unroll
+  for (int r1 = 1; r1 < W; ++r1)
+#pragma unroll
+    for (int c1 = 0; c1 < W; ++c1) {
+#pragma unroll
+      for (int c2 = c1 + 1; c2 < W; ++c2)
+        P::pair(X[r1][c1], X[r1][c2], Cm[r1 - 1][c1], Cm[r1 - 1][c2]);
+#pragma unroll
+      for (int r2 = r1 + 1; r2 < W; ++r2)
+#pragma unroll
+        for (int c2 = 0; c2 < W; ++c2) P::pair(X[r1][c1], X[r2][c2], Cm[r1 - 1][c1], Cm[r2 - 1][c2]);
+    }
+  // upper window: rows 0 .. w - 1 (A index r * w + c)
+#pragma unroll
+  for (int r = 1; r < W; ++r)
+#pragma unroll
+    for (int c = 0; c < W; ++c) A[r * W + c] = Cm[r - 1][c];
+  // lower window: rows 1 .. w (B index (r - 1) * w + c)
+#pragma unroll
+  for (int r = 1; r < W; ++r)
+#pragma unroll
+    for (int c = 0; c < W; ++c) B[(r - 1) * W + c] = Cm[r - 1][c];
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    A[c] = P::zero();
+    B[(W - 1) * W + c] = P::zero();
+  }
+#pragma unroll
+  for (int c1 = 0; c1 < W; ++c1) {
+#pragma unroll
+    for (int c2 = c1 + 1; c2 < W; ++c2) {
+      P::pair(X[0][c1], X[0][c2], A[c1], A[c2]);
+      P::pair(X[W][c1], X[W][c2], B[(W - 1) * W + c1], B[(W - 1) * W + c2]);
+    }
+#pragma unroll
+    for (int r = 1; r < W; ++r)
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        P::pair(X[0][c1], X[r][c], A[c1], A[r * W + c]);
+        P::pair(X[W][c1], X[r][c], B[(W - 1) * W + c1], B[(r - 1) * W + c]);
+      }
+  }
 }
 
 // EVMF switch (Sec. 3.3, Eq. equ_evf) of the window of (px, py).  The sample
@@ -700,6 +798,63 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
     }
   }
   block_stats(L, valid ? 1 : 0, ties, switched);
+}
+
+// Per-window VMF / AMNF with two outputs per thread (w <= 5): a CTA of
+// 32 x T threads covers a 32 x 2T tile, thread (px, r) the windows of rows 2r
+// and 2r + 1, formed together by two_window_aggregates.
+template <int W, int CRIT, int APX, int DEG>
+__device__ __forceinline__ void process_tile2(const Launch& L, int tile) {
+  constexpr int R = W / 2, N = W * W;
+  const int TY = 2 * (blockDim.x / kTX);
+  const TileSmem t = carve(W, true, TY, blockDim.x);
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  const int x0 = txi * kTX, y0 = tyi * TY;
+  stage_tile<CRIT, CRIT != kVMF>(L, t, x0, y0, R);
+  __syncthreads();
+  const int px = threadIdx.x % kTX, py = 2 * (threadIdx.x / kTX);
+  const int gx = x0 + px, gy = y0 + py;
+  const bool va = gx < L.width && gy < L.height;
+  const bool vb = gx < L.width && gy + 1 < L.height;
+  int ties = 0;
+  if constexpr (CRIT == kVMF) {
+    const bool want_tie = L.stats != nullptr;
+    float A[N], B[N];
+    two_window_aggregates<W, PairL2>(t.raw, t.sw, px, py, A, B);
+    const Selection sa = select_min<W, true>(A, nullptr, 0, t.raw, t.sw, px, py, want_tie);
+    const Selection sb = select_min<W, true>(B, nullptr, 0, t.raw, t.sw, px, py + 1, want_tie);
+    if (va) {
+      store_px(L, gx, gy, t.raw[(py + sa.best / W) * t.sw + px + sa.best % W]);
+      ties += sa.near_tie;
+    }
+    if (vb) {
+      store_px(L, gx, gy + 1, t.raw[(py + 1 + sb.best / W) * t.sw + px + sb.best % W]);
+      ties += sb.near_tie;
+    }
+  } else {
+    uint32_t A[N], B[N];
+    two_window_aggregates<W, PairL1Int>(t.raw, t.sw, px, py, A, B);
+    bool ta = false, tb = false;
+    const uint32_t oa =
+        amnf_finish<W, CRIT, APX, DEG>(L, t, px, py, [&](int i) { return (float)A[i]; }, ta);
+    const uint32_t ob =
+        amnf_finish<W, CRIT, APX, DEG>(L, t, px, py + 1, [&](int i) { return (float)B[i]; }, tb);
+    if (va) {
+      store_px(L, gx, gy, oa);
+      ties += ta;
+    }
+    if (vb) {
+      store_px(L, gx, gy + 1, ob);
+      ties += tb;
+    }
+  }
+  block_stats(L, (int)va + (int)vb, ties, 0);
+}
+
+template <int W, int CRIT, int APX, int DEG>
+__global__ void __launch_bounds__(256) filter2_kernel(const __grid_constant__ Launch L) {
+  pdl_begin();
+  process_tile2<W, CRIT, APX, DEG>(L, blockIdx.x);
 }
 
 // One CTA per tile of one image.

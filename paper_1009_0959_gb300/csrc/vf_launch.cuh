@@ -12,6 +12,16 @@ cudaError_t launch_one(const Launch& L, int ty, int grid, cudaStream_t s) {
   // 36-pair median is too cheap for the queue copies to pay, measured)
   if constexpr (CRIT == kEVMF && W >= 5) {
     return launch_evmf_queue<W, APX, DEG>(L, ty, grid, s);
+  } else if constexpr (outputs_per_thread(W, CRIT) == 2) {
+    // 32 x ty threads, 32 x 2ty outputs
+    const size_t smem = smem_bytes(W, CRIT, 2 * ty);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(filter2_kernel<W, CRIT, APX, DEG>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_maybe_pdl(L.pdl != 0, filter2_kernel<W, CRIT, APX, DEG>, dim3(grid),
+                            dim3(kTX * ty), smem, s, L);
   } else {
     const size_t smem = smem_bytes(W, CRIT, ty);
     if (smem > 48 * 1024) {
