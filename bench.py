@@ -106,13 +106,9 @@ class Clocks:
 # with the predicate on; the kernels' instruction counts are not fixed by the
 # source: atan2f, the EVMF switch fraction, the pair-reuse tile borders).
 # Keyed (criterion, approx, degree, window); degree 0 for exact / rational.
-MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 0, 5): 3970, ("bvdf", "poly", 4, 5): 2851,
-                           ("evmf", "poly", 4, 5): 1932, ("amnfe", "rational", 0, 5): 1637,
-                           ("vmf", "exact", 0, 5): 2139}
+MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 0, 5): 3970, ("bvdf", "poly", 4, 5): 2851}
 # DRAM bytes (read + write) per output pixel from the same captures
-MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 0, 5): 7.07, ("bvdf", "poly", 4, 5): 7.06,
-                                 ("evmf", "poly", 4, 5): 6.90, ("amnfe", "rational", 0, 5): 7.11,
-                                 ("vmf", "exact", 0, 5): 7.09}
+MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 0, 5): 7.07, ("bvdf", "poly", 4, 5): 7.06}
 
 
 def main():
