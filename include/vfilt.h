@@ -55,7 +55,17 @@ typedef enum {
 
 typedef enum { VF_VMF = 0, VF_BVDF = 1, VF_AMNFE = 2, VF_AMNFG = 3, VF_EVMF = 4 } vf_criterion;
 
-typedef enum { VF_EXACT = 0, VF_MINIMAX_POLY = 1, VF_MINIMAX_RATIONAL = 2 } vf_approx;
+/* VF_MINIMAX_RATIONAL: the paper's printed (4,4) rationals (EXP and ENT);
+ * VF_MINIMAX_RATIONAL_FIT: the library's own best (d,d) rational, d = degree
+ * in 2..4, fitted on the filter's interval ([0, exp_cutoff] for EXP,
+ * [ent_cutoff, 1] for ENT) by a rational Remez exchange (Sec. 2, the class
+ * R^n_m). */
+typedef enum {
+  VF_EXACT = 0,
+  VF_MINIMAX_POLY = 1,
+  VF_MINIMAX_RATIONAL = 2,
+  VF_MINIMAX_RATIONAL_FIT = 3
+} vf_approx;
 
 /* Arithmetic of the pairwise terms and of the approximant evaluation.  The
  * aggregates are always accumulated in FP32. */
@@ -138,10 +148,16 @@ void vf_default_params(vf_params* p);
  * VF_MINIMAX_POLY the library's own Remez exchange fit (host, FP64) of degree
  * `degree` on [lo, hi]; for VF_MINIMAX_RATIONAL the paper's printed (4,4)
  * rational (VF_FN_EXP: tab_exp_rat on [0, 10]; VF_FN_ENT: tab_ent_rat on
- * [0.05, 1]; lo and hi are ignored).  num[0..*num_len), den[0..*den_len)
+ * [0.05, 1]; lo and hi are ignored); for VF_MINIMAX_RATIONAL_FIT the
+ * library's own best (degree, degree) rational on [lo, hi] (degree 2..4,
+ * denominator normalised to den[0] = 1).  num[0..*num_len), den[0..*den_len)
  * receive coefficients in increasing powers (den_len = 0 for a polynomial;
- * arrays of 8 suffice), *eps the maximum error on [lo, hi] (polynomial) or
- * on the rational's interval.  Host memory; synchronous. */
+ * arrays of 8 suffice), *eps the maximum error on [lo, hi] (fits) or on the
+ * printed rational's interval (its printed value).  Fits are cached in the
+ * context.  Host memory; synchronous.
+ * Errors: VF_ERR_ARG (null pointers, bad enum, degree or interval; a fit
+ * whose denominator vanishes on the interval), VF_ERR_UNSUPPORTED (a printed
+ * rational for a function the paper gives none for). */
 vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int degree,
                              double lo, double hi, double* num, int* num_len, double* den,
                              int* den_len, double* eps);

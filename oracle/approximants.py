@@ -8,7 +8,9 @@ TEST INFRASTRUCTURE ONLY (oracle side).
   ent     : z ln z on [T, 1], T = 0.05                  (tab_ent_rat)
 
 Polynomials of degree 2..6 come from the oracle's own Remez fit (oracle.remez);
-the rationals are the paper's printed ones (oracle.paper_tables).
+'rational' is the paper's printed (4,4) rational (oracle.paper_tables),
+'rational_fit' the oracle's own best (d,d) rational (oracle.remez.rational_remez)
+on the filter's interval.
 """
 from __future__ import annotations
 
@@ -18,7 +20,7 @@ import math
 import numpy as np
 
 from . import paper_tables as T
-from .remez import remez
+from .remez import rational_remez, remez
 
 
 def f_acos(z):
@@ -55,6 +57,12 @@ TARGETS = {
 def fit(name: str, degree: int, lo: float, hi: float):
     """Degree-`degree` minimax polynomial of TARGETS[name] on [lo, hi]."""
     return remez(TARGETS[name], lo, hi, degree)
+
+
+@functools.lru_cache(maxsize=None)
+def rational_fit(name: str, degree: int, lo: float, hi: float):
+    """Best (degree, degree) rational of TARGETS[name] on [lo, hi]."""
+    return rational_remez(TARGETS[name], lo, hi, degree, degree)
 
 
 def default_ent_cutoff(n: int) -> float:
@@ -95,6 +103,9 @@ def acos_pieces(degree: int, source: str = "fit"):
 def exp_approximant(kind: str, degree: int, cutoff: float = T.EXP_CUTOFF,
                     source: str = "fit"):
     """EXP approximant on [0, cutoff] (Sec. 3.2)."""
+    if kind == "rational_fit":
+        r = rational_fit("exp", degree, 0.0, float(cutoff))
+        return Approximant(r.num, r.den)
     if kind == "rational":
         if cutoff != T.EXP_CUTOFF:
             raise ValueError("the paper's EXP rational is fitted on [0, 10]")
@@ -106,7 +117,11 @@ def exp_approximant(kind: str, degree: int, cutoff: float = T.EXP_CUTOFF,
 
 def ent_approximant(kind: str, degree: int, cutoff: float = T.ENT_CUTOFF):
     """ENT approximant on [cutoff, 1] (Sec. 3.3).  The rational is the paper's,
-    fitted on [0.05, 1]; below 0.05 (larger windows) it is used as printed."""
+    fitted on [0.05, 1]; below 0.05 (larger windows) it is used as printed.
+    The own rational fit is made on [cutoff, 1]."""
+    if kind == "rational_fit":
+        r = rational_fit("ent", degree, float(cutoff), 1.0)
+        return Approximant(r.num, r.den)
     if kind == "rational":
         return Approximant(T.ENT_RATIONAL_NUM, T.ENT_RATIONAL_DEN)
     return Approximant(fit("ent", degree, float(cutoff), 1.0).coef)

@@ -24,7 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4}
-APPROX = {"exact": 0, "poly": 1, "rational": 2}
+APPROX = {"exact": 0, "poly": 1, "rational": 2, "rational_fit": 2}  # C side: any rational
 MAXC = 16
 
 

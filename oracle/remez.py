@@ -181,3 +181,142 @@ def max_error(f, approx, a: float, b: float, samples: int = 2_000_001) -> float:
 def equioscillation(f, fit: MinimaxFit):
     """Signed error at the final reference points (p+2 of them)."""
     return f(fit.reference) - fit(fit.reference)
+
+
+# ---------------------------------------------------------------- rationals
+
+class RationalFit:
+    """Minimax rational p/q: numerator a_0..a_m, denominator b_0..b_n (b_0 = 1),
+    error eps, final reference of m+n+2 points."""
+
+    def __init__(self, num, den, eps, levelled, reference, a, b, iterations):
+        self.num = np.asarray(num, dtype=np.float64)
+        self.den = np.asarray(den, dtype=np.float64)
+        self.eps = float(eps)
+        self.levelled = float(levelled)
+        self.reference = np.asarray(reference, dtype=np.float64)
+        self.a, self.b = float(a), float(b)
+        self.iterations = iterations
+
+    def __call__(self, z):
+        z = np.asarray(z, dtype=np.float64)
+        return npoly.polyval(z, self.num) / npoly.polyval(z, self.den)
+
+
+def rational_remez(f, a: float, b: float, m: int, n: int, grid: int = 20001,
+                   tol: float = 1e-7, max_iter: int = 80) -> RationalFit:
+    """Best rational approximation p/q, deg p <= m, deg q <= n, of f on [a, b]
+    in the maximum norm (Sec. 2, the class R^n_m and its existence theorem).
+
+    A non-degenerate best approximation is characterised by an error that
+    equioscillates on m+n+2 points, so the same exchange as for polynomials
+    applies, with step 2 replaced: on the reference x_k the conditions
+    f(x_k) - p(x_k)/q(x_k) = (-1)^k E read p(x_k) - f(x_k) q(x_k) =
+    -(-1)^k E q(x_k), linear in the coefficients of p and q for a given E.
+    All m+n+2 of them (coefficients of p and q, q unnormalised) form the
+    generalised eigenproblem A c = E B c; the level E is the eigenvalue of
+    smallest magnitude whose q keeps one sign on [a, b] (no pole).  p and q
+    are carried in the Chebyshev basis of [a, b] for conditioning and
+    expanded to monomials at the end, with q(0) scaled to 1.  The exchange
+    stops when the extrema are level to 1e-7 (the quotient's FP64 rounding
+    resolves no finer).
+    """
+    from numpy.polynomial import chebyshev as C
+    from scipy.linalg import eig
+
+    N = m + n + 2
+    mid, half = 0.5 * (a + b), 0.5 * (b - a)
+    k = np.arange(N)
+    t = -np.cos(np.pi * k / (N - 1))   # reference in [-1, 1] (Chebyshev extrema)
+    ts = np.linspace(-1.0, 1.0, grid)
+    zs = mid + half * ts
+    fz = f(zs)
+    sgn = (-1.0) ** k
+
+    def solve(t):
+        fx = f(mid + half * t)
+        Tp = C.chebvander(t, m)                 # N x (m+1)
+        Tq = C.chebvander(t, n)                 # N x (n+1)
+        A = np.hstack([Tp, -fx[:, None] * Tq])
+        B = np.hstack([np.zeros_like(Tp), -(sgn[:, None] * Tq)])
+        w, V = eig(A, B)
+        best = None
+        for lam, v in zip(w, V.T):
+            if not np.isfinite(lam) or abs(lam.imag) > 1e-9 * max(1.0, abs(lam.real)):
+                continue
+            v = np.real(v)
+            q = C.chebval(ts, v[m + 1:])
+            if not (np.all(q > 0.0) or np.all(q < 0.0)):
+                continue
+            if best is None or abs(lam.real) < abs(best[0]):
+                best = (lam.real, v)
+        if best is None:
+            raise RuntimeError("no pole-free rational on the reference")
+        E, v = best
+        return E, v[: m + 1], v[m + 1:]
+
+    def err_of(pc, qc):
+        def err(tt):
+            tt = np.atleast_1d(np.asarray(tt, dtype=np.float64))
+            return f(mid + half * tt) - C.chebval(tt, pc) / C.chebval(tt, qc)
+        return err
+
+    E, pc, qc = 0.0, None, None
+    emax = np.inf
+    for it in range(1, max_iter + 1):
+        E, pc, qc = solve(t)
+        err = err_of(pc, qc)
+        e = fz - C.chebval(ts, pc) / C.chebval(ts, qc)
+        de = np.diff(e)
+        turn = np.nonzero((de[:-1] * de[1:] <= 0.0) & (e[1:-1] != 0.0))[0] + 1
+        cand = [0] + [int(i) for i in turn] + [grid - 1]
+        pts, vals_e = [], []
+        for i in cand:
+            if i in (0, grid - 1):
+                xi = ts[i]
+            else:
+                s = np.sign(e[i])
+                xi = _golden_max(lambda u, s=s: s * float(err(u)[0]), ts[i - 1], ts[i + 1])
+            ei = float(err(xi)[0])
+            if pts and np.sign(ei) == np.sign(vals_e[-1]):
+                if abs(ei) > abs(vals_e[-1]):
+                    pts[-1], vals_e[-1] = xi, ei
+            else:
+                pts.append(xi)
+                vals_e.append(ei)
+        while len(pts) > N:
+            if abs(vals_e[0]) < abs(vals_e[-1]):
+                pts.pop(0)
+                vals_e.pop(0)
+            else:
+                pts.pop()
+                vals_e.pop()
+        emax = max(abs(v) for v in vals_e)
+        emin = min(abs(v) for v in vals_e)
+        if len(pts) == N:
+            t = np.array(pts)
+            sgn = np.sign(np.array(vals_e))
+        if emin > 0.0 and emax / emin - 1.0 < tol:
+            break
+        if emax <= 1e-13 * float(np.max(np.abs(fz))):
+            break  # at the FP64 rounding level of the quotient: nothing to level
+    # monomial coefficients in z: substitute t = (z - mid) / half
+    pm = _cheb_to_monomial(pc, mid, half)
+    qm = _cheb_to_monomial(qc, mid, half)
+    pm, qm = pm / qm[0], qm / qm[0]
+    e_final = np.abs(fz - npoly.polyval(zs, pm) / npoly.polyval(zs, qm))
+    eps = max(float(e_final.max()), emax)
+    return RationalFit(pm, qm, eps, abs(E), mid + half * t, a, b, it)
+
+
+def _cheb_to_monomial(c, mid: float, half: float) -> np.ndarray:
+    """Monomial coefficients in z of sum_j c_j T_j((z - mid) / half)."""
+    from numpy.polynomial import chebyshev as C
+    pt = C.cheb2poly(c)                      # coefficients in t
+    out = np.zeros(len(pt))
+    lin = np.array([-mid / half, 1.0 / half])  # t as a polynomial in z
+    powt = np.array([1.0])
+    for j, cj in enumerate(pt):
+        out[: len(powt)] += cj * powt
+        powt = npoly.polymul(powt, lin)
+    return out

@@ -31,14 +31,16 @@ const double kEntRatDen[5] = {1.532270e-02, 3.987796e-01, 1.461793, 6.827004e-01
 const double kEntRatEps = 7.342477e-07;
 
 struct FitKey {
+  int kind;  // 0 polynomial, 1 (degree, degree) rational
   int fn, degree;
   double lo, hi;
   bool operator<(const FitKey& o) const {
-    return std::tie(fn, degree, lo, hi) < std::tie(o.fn, o.degree, o.lo, o.hi);
+    return std::tie(kind, fn, degree, lo, hi) < std::tie(o.kind, o.fn, o.degree, o.lo, o.hi);
   }
 };
 struct FitVal {
-  double coef[8];
+  double coef[8];  // polynomial, or the rational's numerator
+  double den[8];   // rational denominator (den[0] = 1)
   double eps;
 };
 
@@ -65,11 +67,21 @@ vf_status fail(vf_ctx* ctx, vf_status s, const std::string& msg) {
 }
 
 const FitVal* get_fit(vf_ctx* ctx, int fn, int degree, double lo, double hi) {
-  FitKey k{fn, degree, lo, hi};
+  FitKey k{0, fn, degree, lo, hi};
   auto it = ctx->fits.find(k);
   if (it != ctx->fits.end()) return &it->second;
   FitVal v{};
   if (!remez_fit(fn, degree, lo, hi, v.coef, &v.eps)) return nullptr;
+  return &(ctx->fits[k] = v);
+}
+
+// The library's own best (degree, degree) rational of function fn on [lo, hi].
+const FitVal* get_rational_fit(vf_ctx* ctx, int fn, int degree, double lo, double hi) {
+  FitKey k{1, fn, degree, lo, hi};
+  auto it = ctx->fits.find(k);
+  if (it != ctx->fits.end()) return &it->second;
+  FitVal v{};
+  if (!remez_rational_fit(fn, degree, degree, lo, hi, v.coef, v.den, &v.eps)) return nullptr;
   return &(ctx->fits[k] = v);
 }
 
@@ -154,6 +166,17 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
     *eps = fn == VF_FN_EXP ? kExpRatEps : kEntRatEps;
     return VF_OK;
   }
+  if (approx == VF_MINIMAX_RATIONAL_FIT) {
+    if (degree < 2 || degree > 4) return fail(ctx, VF_ERR_ARG, "rational degree must be 2..4");
+    if ((int)fn < 0 || (int)fn > 3 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
+    const FitVal* f = get_rational_fit(ctx, (int)fn, degree, lo, hi);
+    if (!f) return fail(ctx, VF_ERR_ARG, "rational minimax fit failed (pole on the interval)");
+    for (int k = 0; k <= degree; ++k) num[k] = f->coef[k], den[k] = f->den[k];
+    *num_len = degree + 1;
+    *den_len = degree + 1;
+    *eps = f->eps;
+    return VF_OK;
+  }
   if (approx != VF_MINIMAX_POLY) return fail(ctx, VF_ERR_ARG, "approx must be poly or rational");
   if (degree < 2 || degree > 6) return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
   if ((int)fn < 0 || (int)fn > 3 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
@@ -180,7 +203,7 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   if (in_pitch < (size_t)width * channels || out_pitch < (size_t)width * channels)
     return fail(ctx, VF_ERR_ARG, "pitch smaller than a row");
   if ((int)p->criterion < 0 || (int)p->criterion > 4) return fail(ctx, VF_ERR_ARG, "bad criterion");
-  if ((int)p->approx < 0 || (int)p->approx > 2) return fail(ctx, VF_ERR_ARG, "bad approximation");
+  if ((int)p->approx < 0 || (int)p->approx > 3) return fail(ctx, VF_ERR_ARG, "bad approximation");
   if ((int)p->precision < 0 || (int)p->precision > 2) return fail(ctx, VF_ERR_ARG, "bad precision");
   if (p->window < 1 || (p->window & 1) == 0 || p->window > 15)
     return fail(ctx, VF_ERR_ARG, "window must be odd, 1..15");
@@ -188,6 +211,8 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
     return fail(ctx, VF_ERR_UNSUPPORTED, "windows 3, 5 and 7 are built");
   if (p->approx == VF_MINIMAX_POLY && (p->degree < 2 || p->degree > 6))
     return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
+  if (p->approx == VF_MINIMAX_RATIONAL_FIT && (p->degree < 2 || p->degree > 4))
+    return fail(ctx, VF_ERR_ARG, "rational degree must be 2..4");
   if (!(p->kappa >= 0.0f) || !(p->exp_cutoff > 0.0f)) return fail(ctx, VF_ERR_ARG, "bad kappa/cut-off");
   if (p->precision != VF_FP32 && p->criterion == VF_BVDF && p->approx != VF_MINIMAX_POLY)
     return fail(ctx, VF_ERR_UNSUPPORTED, "packed BVDF runs the minimax polynomial only");
@@ -198,7 +223,9 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
 
   const int w = p->window, n = w * w;
   const int crit = (int)p->criterion;
-  int apx = (int)p->approx;
+  // the library's own rational runs the rational kernels with its coefficients
+  const bool rfit = p->approx == VF_MINIMAX_RATIONAL_FIT;
+  int apx = rfit ? kRational : (int)p->approx;
   if (crit == kVMF) apx = kExact;  // the vector median has no elementary function
   if (apx == kRational && crit == kBVDF)
     return fail(ctx, VF_ERR_UNSUPPORTED, "the paper gives no rational for arccos");
@@ -231,7 +258,12 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
       put(L.c.a, lo->coef, p->degree + 1);
       put(L.c.b, hi->coef, p->degree + 1);
     } else if (crit == kAMNFE || crit == kAMNFG) {
-      if (apx == kRational) {
+      if (apx == kRational && rfit) {
+        const FitVal* f = get_rational_fit(ctx, 2, p->degree, 0.0, (double)p->exp_cutoff);
+        if (!f) return fail(ctx, VF_ERR_ARG, "rational minimax fit failed");
+        put(L.c.a, f->coef, p->degree + 1);
+        put(L.c.b, f->den, p->degree + 1);
+      } else if (apx == kRational) {
         if (p->exp_cutoff != 10.0f)
           return fail(ctx, VF_ERR_UNSUPPORTED, "the paper's EXP rational is fitted on [0, 10]");
         put(L.c.a, kExpRatNum, 5);
@@ -242,7 +274,14 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
         put(L.c.a, f->coef, p->degree + 1);
       }
     } else if (crit == kEVMF) {
-      if (apx == kRational) {
+      if (apx == kRational && rfit) {
+        if (!(L.ent_cutoff > 0.0f) || L.ent_cutoff >= 1.0f)
+          return fail(ctx, VF_ERR_ARG, "the ENT rational fit needs a cut-off in (0, 1)");
+        const FitVal* f = get_rational_fit(ctx, 3, p->degree, (double)L.ent_cutoff, 1.0);
+        if (!f) return fail(ctx, VF_ERR_ARG, "rational minimax fit failed");
+        put(L.c.a, f->coef, p->degree + 1);
+        put(L.c.b, f->den, p->degree + 1);
+      } else if (apx == kRational) {
         put(L.c.a, kEntRatNum, 5);
         put(L.c.b, kEntRatDen, 5);
       } else {
@@ -268,8 +307,17 @@ vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg) { return fail(ctx
 bool gate_tensor_cores(const vf_ctx* ctx) { return ctx->gate_tc != 0; }
 
 const double* cached_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi) {
-  auto it = ctx->fits.find(FitKey{fn, degree, lo, hi});
+  auto it = ctx->fits.find(FitKey{0, fn, degree, lo, hi});
   return it == ctx->fits.end() ? nullptr : it->second.coef;
+}
+
+bool cached_rational_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi,
+                         const double** num, const double** den) {
+  auto it = ctx->fits.find(FitKey{1, fn, degree, lo, hi});
+  if (it == ctx->fits.end()) return false;
+  *num = it->second.coef;
+  *den = it->second.den;
+  return true;
 }
 
 void paper_rational(int fn, const double** num, const double** den) {

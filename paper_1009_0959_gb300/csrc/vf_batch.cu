@@ -437,18 +437,20 @@ vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* 
   if (d.height < 1 || d.width < 1 || (d.channels != 3 && d.channels != 4)) return VF_ERR_ARG;
   const size_t row = (size_t)d.width * d.channels;
   if (d.in_pitch < row || d.out_pitch < row) return VF_ERR_ARG;
-  if ((int)p->criterion < 0 || (int)p->criterion > 4 || (int)p->approx < 0 || (int)p->approx > 2)
+  if ((int)p->criterion < 0 || (int)p->criterion > 4 || (int)p->approx < 0 || (int)p->approx > 3)
     return VF_ERR_ARG;
   if (p->window < 1 || (p->window & 1) == 0 || p->window > 15) return VF_ERR_ARG;
   if (p->window != 3 && p->window != 5 && p->window != 7) return VF_ERR_UNSUPPORTED;
   if (p->approx == VF_MINIMAX_POLY && (p->degree < 2 || p->degree > 6)) return VF_ERR_ARG;
+  if (p->approx == VF_MINIMAX_RATIONAL_FIT && (p->degree < 2 || p->degree > 4)) return VF_ERR_ARG;
   if (!(p->kappa >= 0.0f) || !(p->exp_cutoff > 0.0f)) return VF_ERR_ARG;
   if (p->precision != VF_FP32) return VF_ERR_UNSUPPORTED;
   const size_t in_bytes = (size_t)(d.height - 1) * d.in_pitch + row;
   const size_t out_bytes = (size_t)(d.height - 1) * d.out_pitch + row;
   if (d.d_in < d.d_out + out_bytes && d.d_out < d.d_in + in_bytes) return VF_ERR_ALIAS;
   const int w = p->window, n = w * w, crit = (int)p->criterion;
-  int apx = crit == kVMF ? kExact : (int)p->approx;
+  const bool rfit = p->approx == VF_MINIMAX_RATIONAL_FIT;
+  int apx = crit == kVMF ? kExact : (rfit ? kRational : (int)p->approx);
   if (apx == kRational && crit == kBVDF) return VF_ERR_UNSUPPORTED;
   Launch& L = out->L;
   L = Launch{};
@@ -483,6 +485,15 @@ vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* 
     }
     if (!a) return VF_ERR_UNSUPPORTED;
     put(L.c.a, a, p->degree + 1);
+  } else if (apx == kRational && rfit) {
+    const double *num = nullptr, *den = nullptr;
+    const bool ok = crit == kEVMF
+                        ? cached_rational_fit(ctx, 3, p->degree, (double)L.ent_cutoff, 1.0, &num, &den)
+                        : cached_rational_fit(ctx, 2, p->degree, 0.0, (double)p->exp_cutoff, &num,
+                                              &den);
+    if (!ok) return VF_ERR_UNSUPPORTED;
+    put(L.c.a, num, p->degree + 1);
+    put(L.c.b, den, p->degree + 1);
   } else if (apx == kRational) {
     if ((crit == kAMNFE || crit == kAMNFG) && p->exp_cutoff != 10.0f) return VF_ERR_UNSUPPORTED;
     const double *num = nullptr, *den = nullptr;

@@ -143,6 +143,9 @@ vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg);
 // Coefficients of a fit already in the context's cache, or null; never fits
 // or allocates.
 const double* cached_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi);
+// The same for the library's (degree, degree) rational fits.
+bool cached_rational_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi,
+                         const double** num, const double** den);
 
 // The paper's (4,4) rationals (fn 2: exp(-z), fn 3: z ln z), 5 coefficients each.
 void paper_rational(int fn, const double** num, const double** den);
@@ -151,5 +154,12 @@ void paper_rational(int fn, const double** num, const double** den);
 // `degree` for function id (0 acos, 1 2 asin(t/sqrt2), 2 exp(-z), 3 z ln z)
 // on [lo, hi]; coefficients in increasing powers of the argument.
 bool remez_fit(int fn, int degree, double lo, double hi, double* coef, double* eps);
+
+// Host rational Remez (FP64, Sec. 2, the class R^n_m): the best p/q with
+// deg p <= m, deg q <= n for function id fn on [lo, hi]; monomial
+// coefficients num[0..m], den[0..n] with den[0] = 1.  False when the exchange
+// meets a denominator with a zero on [lo, hi].
+bool remez_rational_fit(int fn, int m, int n, double lo, double hi, double* num, double* den,
+                        double* eps);
 
 }  // namespace vf

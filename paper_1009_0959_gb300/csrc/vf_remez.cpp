@@ -178,4 +178,172 @@ bool remez_fit(int fn, int degree, double lo, double hi, double* coef, double* e
   return true;
 }
 
+// ---------------------------------------------------------------- rationals
+//
+// Best rational approximation p/q, deg p <= m, deg q <= n, of f in the
+// maximum norm (Sec. 2, the class R^n_m).  A non-degenerate best
+// approximation has an error that equioscillates on m+n+2 points, so the
+// exchange above carries over; only the solve on the reference changes.  On
+// the reference t_k the conditions f - p/q = (-1)^k E, i.e.
+//   p(t_k) - f(t_k) q(t_k) + (-1)^k E q(t_k) = 0,
+// are bilinear in (q, E).  They are solved by fixed-point iteration: with
+// q(t_k) in the E term taken from the previous iterate, the system is linear
+// in the Chebyshev coefficients of p (m+1), of q with its T_0 coefficient
+// fixed to 1 (n), and E; it is re-solved until E settles (a few rounds).
+// Starting from q = 1 this is the polynomial solve.
+namespace {
+
+struct RFit {
+  int fn, m, n;
+  double lo, hi;
+  std::vector<double> p, q;  // Chebyshev coefficients in t; q[0] = 1
+  double x_of(double t) const { return 0.5 * (lo + hi) + 0.5 * (hi - lo) * t; }
+  double qv(double t) const {
+    double T[16];
+    cheb(t, n, T);
+    double s = 0.0;
+    for (int j = 0; j <= n; ++j) s += q[j] * T[j];
+    return s;
+  }
+  double err(double t) const {
+    double T[16];
+    cheb(t, m, T);
+    double s = 0.0;
+    for (int j = 0; j <= m; ++j) s += p[j] * T[j];
+    return target(fn, x_of(t)) - s / qv(t);
+  }
+};
+
+// Monomial coefficients in x of sum_j c_j T_j((x - mid) / half).
+std::vector<double> to_monomial(const std::vector<double>& c, double mid, double half) {
+  const int d = (int)c.size() - 1;
+  std::vector<std::vector<double>> Tm(d + 1, std::vector<double>(d + 1, 0.0));
+  Tm[0][0] = 1.0;
+  if (d >= 1) Tm[1][1] = 1.0;
+  for (int m = 2; m <= d; ++m)
+    for (int k = 0; k <= m; ++k) Tm[m][k] = (k > 0 ? 2.0 * Tm[m - 1][k - 1] : 0.0) - Tm[m - 2][k];
+  std::vector<double> in_t(d + 1, 0.0), out(d + 1, 0.0);
+  for (int m = 0; m <= d; ++m)
+    for (int k = 0; k <= m; ++k) in_t[k] += c[m] * Tm[m][k];
+  for (int k = 0; k <= d; ++k) {
+    const double scale = in_t[k] / std::pow(half, k);
+    double binom = 1.0;
+    for (int j = 0; j <= k; ++j) {
+      out[j] += scale * binom * std::pow(-mid, k - j);
+      binom = binom * (k - j) / (j + 1);
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+bool remez_rational_fit(int fn, int m, int n, double lo, double hi, double* num, double* den,
+                        double* eps) {
+  const int N = m + n + 2;
+  if (m < 1 || n < 1 || m > 8 || n > 8 || !(hi > lo)) return false;
+  RFit F{fn, m, n, lo, hi, std::vector<double>(m + 1, 0.0), std::vector<double>(n + 1, 0.0)};
+  F.q[0] = 1.0;
+  std::vector<double> ref(N);
+  for (int k = 0; k < N; ++k) ref[k] = -std::cos(M_PI * k / (N - 1));
+  std::vector<double> sg(N);
+  for (int k = 0; k < N; ++k) sg[k] = (k & 1) ? -1.0 : 1.0;
+  double fmax = 0.0;
+  for (int g = 0; g <= 200; ++g) fmax = std::max(fmax, std::fabs(target(fn, F.x_of(-1.0 + g / 100.0))));
+
+  const int G = 8193;
+  double level = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    // solve on the reference: fixed point in the E q(t_k) term
+    std::vector<double> qprev(N);
+    for (int k = 0; k < N; ++k) qprev[k] = F.qv(ref[k]);
+    double E = 0.0;
+    for (int s = 0; s < 50; ++s) {
+      std::vector<double> A(N * N, 0.0), b(N);
+      for (int k = 0; k < N; ++k) {
+        double Tp[16], Tq[16];
+        cheb(ref[k], m, Tp);
+        cheb(ref[k], n, Tq);
+        const double fk = target(fn, F.x_of(ref[k]));
+        for (int j = 0; j <= m; ++j) A[k * N + j] = Tp[j];
+        for (int j = 1; j <= n; ++j) A[k * N + m + j] = -fk * Tq[j];
+        A[k * N + m + n + 1] = sg[k] * qprev[k];
+        b[k] = fk;  // the fixed q_0 = 1 term moved to the right
+      }
+      if (!solve(A, b, N)) return false;
+      for (int j = 0; j <= m; ++j) F.p[j] = b[j];
+      for (int j = 1; j <= n; ++j) F.q[j] = b[m + j];
+      const double Enew = b[m + n + 1];
+      for (int k = 0; k < N; ++k) qprev[k] = F.qv(ref[k]);
+      const bool settled = std::fabs(Enew - E) <= 1e-14 * std::fabs(Enew);
+      E = Enew;
+      if (settled) break;
+    }
+    level = std::fabs(E);
+    // the denominator must keep its sign on [-1, 1] (no pole)
+    for (int g = 0; g < G; ++g)
+      if (!(F.qv(-1.0 + 2.0 * g / (G - 1)) > 0.0)) return false;
+
+    // error extrema, one per run of one sign, refined by ternary search
+    std::vector<double> ts, es;
+    double run_t = -1.0, run_e = F.err(-1.0);
+    for (int g = 1; g < G; ++g) {
+      const double t = -1.0 + 2.0 * g / (G - 1), e = F.err(t);
+      if ((e > 0) == (run_e > 0)) {
+        if (std::fabs(e) > std::fabs(run_e)) run_t = t, run_e = e;
+      } else {
+        ts.push_back(run_t);
+        es.push_back(run_e);
+        run_t = t;
+        run_e = e;
+      }
+    }
+    ts.push_back(run_t);
+    es.push_back(run_e);
+    const double h = 2.0 / (G - 1);
+    for (size_t k = 0; k < ts.size(); ++k) {
+      if (ts[k] <= -1.0 || ts[k] >= 1.0) continue;
+      double a = std::max(-1.0, ts[k] - h), c = std::min(1.0, ts[k] + h);
+      const double s = es[k] > 0 ? 1.0 : -1.0;
+      for (int r = 0; r < 100; ++r) {
+        const double m1 = a + (c - a) / 3.0, m2 = c - (c - a) / 3.0;
+        if (s * F.err(m1) < s * F.err(m2)) a = m1; else c = m2;
+      }
+      ts[k] = 0.5 * (a + c);
+      es[k] = F.err(ts[k]);
+    }
+    while ((int)ts.size() > N) {
+      if (std::fabs(es.front()) < std::fabs(es.back())) {
+        ts.erase(ts.begin());
+        es.erase(es.begin());
+      } else {
+        ts.pop_back();
+        es.pop_back();
+      }
+    }
+    if ((int)ts.size() < N) break;
+    double emax = 0.0, emin = 1e300;
+    for (double e : es) emax = std::max(emax, std::fabs(e)), emin = std::min(emin, std::fabs(e));
+    ref = ts;
+    for (int k = 0; k < N; ++k) sg[k] = es[k] > 0 ? 1.0 : -1.0;
+    if (emax - emin <= 1e-7 * emax || emax <= 1e-13 * fmax) break;
+  }
+
+  const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+  std::vector<double> pm = to_monomial(F.p, mid, half), qm = to_monomial(F.q, mid, half);
+  if (qm[0] == 0.0) return false;
+  for (int j = 0; j <= m; ++j) num[j] = pm[j] / qm[0];
+  for (int j = 0; j <= n; ++j) den[j] = qm[j] / qm[0];  // den[0] = 1 exactly
+  double e = 0.0;
+  for (int g = 0; g <= 20000; ++g) {
+    const double x = lo + (hi - lo) * g / 20000.0;
+    double pv = 0.0, qv = 0.0;
+    for (int k = m; k >= 0; --k) pv = pv * x + num[k];
+    for (int k = n; k >= 0; --k) qv = qv * x + den[k];
+    e = std::max(e, std::fabs(target(fn, x) - pv / qv));
+  }
+  *eps = std::max(e, level);
+  return true;
+}
+
 }  // namespace vf

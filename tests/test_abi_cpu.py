@@ -94,3 +94,33 @@ def test_options(vf):
     vf.set_option("tile_rows", 4)
     with pytest.raises(vf.VFError):
         vf.set_option("tile_rows", 3)
+
+
+@pytest.mark.parametrize("fn,interval", [("exp", (0.0, 10.0)), ("ent", (0.05, 1.0)),
+                                         ("exp", (0.0, 1.534)), ("ent", (0.018, 1.0))])
+def test_library_rational_remez_matches_oracle(vf, fn, interval):
+    """The library's rational Remez (C++, fixed-point solve on the reference)
+    and the oracle's (numpy, generalised eigenproblem) are written apart;
+    they agree on eps and on the rational's values."""
+    import numpy as np
+    from oracle import approximants as AP
+    from oracle import remez as R
+    a, b = interval
+    for d in (2, 3, 4):
+        num, den, eps = vf.get_approximant(fn, "rational_fit", d, a, b)
+        assert len(num) == d + 1 and len(den) == d + 1 and den[0] == 1.0
+        r = R.rational_remez(AP.TARGETS[fn], a, b, d, d)
+        if r.eps > 1e-10:
+            assert eps == pytest.approx(r.eps, rel=1e-5)
+        else:
+            assert eps < 1e-10
+        z = np.linspace(a, b, 10001)
+        lib = np.polynomial.polynomial.polyval(z, num) / np.polynomial.polynomial.polyval(z, den)
+        assert np.max(np.abs(lib - r(z))) <= 1e-3 * max(r.eps, 1e-9)
+
+
+def test_library_rational_fit_errors(vf):
+    with pytest.raises(vf.VFError):
+        vf.get_approximant("exp", "rational_fit", 5, 0.0, 10.0)
+    with pytest.raises(vf.VFError):
+        vf.get_approximant("exp", "rational_fit", 3, 1.0, 1.0)

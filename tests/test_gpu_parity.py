@@ -59,7 +59,10 @@ CASES = [("vmf", "exact", 0), ("bvdf", "exact", 0), ("bvdf", "poly", 2), ("bvdf"
          ("bvdf", "poly", 6), ("amnfe", "exact", 0), ("amnfe", "poly", 2), ("amnfe", "poly", 4),
          ("amnfe", "poly", 6), ("amnfe", "rational", 4), ("amnfg", "exact", 0),
          ("amnfg", "poly", 4), ("amnfg", "rational", 4), ("evmf", "exact", 0),
-         ("evmf", "poly", 3), ("evmf", "poly", 5), ("evmf", "rational", 4)]
+         ("evmf", "poly", 3), ("evmf", "poly", 5), ("evmf", "rational", 4),
+         # the library's own best (d,d) rationals (GPU) against the oracle's own
+         ("amnfe", "rational_fit", 2), ("amnfe", "rational_fit", 4),
+         ("amnfg", "rational_fit", 3), ("evmf", "rational_fit", 2), ("evmf", "rational_fit", 4)]
 
 
 @pytest.mark.parametrize("w", [3, 5, 7])
