@@ -23,7 +23,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libvfo.so")
 _lock = threading.Lock()
 _lib = None
 
-CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4}
+CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4, "evbdf": 5}
 APPROX = {"exact": 0, "poly": 1, "rational": 2, "rational_fit": 2}  # C side: any rational
 MAXC = 16
 
@@ -115,12 +115,14 @@ class Config:
         p.window, p.criterion, p.approx = window, CRITERIA[criterion], APPROX[approx]
         p.kappa, p.exp_cutoff, p.ent_cutoff = self.kappa, self.exp_cutoff, self.ent_cutoff
         if approx != "exact":
-            if criterion == "bvdf":
+            if criterion in ("bvdf", "evbdf"):
                 if approx != "poly":
                     raise ValueError("the paper gives no rational for arccos")
                 lo, hi = AP.acos_pieces(degree, coeffs)
                 _fill(p.acos_lo, lo)
                 _fill(p.acos_hi, hi)
+                if criterion == "evbdf":  # the switch's ENT polynomial, same degree
+                    _fill(p.ent, AP.ent_approximant(approx, degree, self.ent_cutoff))
             elif criterion in ("amnfe", "amnfg"):
                 _fill(p.expo, AP.exp_approximant(approx, degree, self.exp_cutoff, coeffs))
             elif criterion == "evmf":

@@ -44,7 +44,7 @@
 #include <string.h>
 
 /* criterion codes (mirrored by the Python wrapper, not shared with CUDA) */
-enum { VFO_VMF = 0, VFO_BVDF = 1, VFO_AMNFE = 2, VFO_AMNFG = 3, VFO_EVMF = 4 };
+enum { VFO_VMF = 0, VFO_BVDF = 1, VFO_AMNFE = 2, VFO_AMNFG = 3, VFO_EVMF = 4, VFO_EVBDF = 5 };
 /* approximation codes */
 enum { VFO_EXACT = 0, VFO_POLY = 1, VFO_RATIONAL = 2 };
 
@@ -344,11 +344,16 @@ int vfo_filter_rows(const uint8_t* img, int H, int W, int C, const vfo_params* p
           if (dg && dg->yreal)
             for (int k = 0; k < 3; ++k) dg->yreal[pix * 3 + k] = y[k];
           break;
-        case VFO_EVMF: {
+        case VFO_EVMF:
+        case VFO_EVBDF: {
+          /* EVBDF: the generalised entropy vector filter of Sec. 3.3 (the
+           * Euclidean distance of the filtering branch replaced by the angle
+           * of Sec. 3.1); the switch is EVMF's */
           double sgap;
           sw = vfo_evmf_switch(p, n, x, &sgap);
           if (sw) {
-            sel = vfo_vmf_select(n, x, &gap);
+            sel = p->criterion == VFO_EVMF ? vfo_vmf_select(n, x, &gap)
+                                           : vfo_bvdf_select(p, n, x, &gap);
             gap = fmin(gap, sgap);
           } else {
             sel = Cc;

@@ -356,3 +356,39 @@ def test_metrics():
     d = c + 2
     assert M.psnr(c, d) == pytest.approx(10 * math.log10(255 ** 2 / 4))
     assert M.mae(c, d) == pytest.approx(2.0)
+
+
+# ---------------------------------------------------------------- generalised EVF (EVBDF)
+
+
+@pytest.mark.parametrize("w", [3, 5])
+@pytest.mark.parametrize("approx,deg", [("exact", 4), ("poly", 4)])
+def test_evbdf_is_switch_then_bvdf(w, approx, deg):
+    """Sec. 3.3 generalised EVF with the angle of Sec. 3.1 in the filtering
+    branch: wherever EVMF's switch fires the output is BVDF's, elsewhere the
+    centre; the switch is EVMF's own (same ENT approximant)."""
+    clean, noisy = synth.noisy(30, 41, 0.2, 31 + w)
+    o_ev, d_ev = F.filter_image(noisy, F.Config("evbdf", w, approx, deg))
+    o_em, d_em = F.filter_image(noisy, F.Config("evmf", w, approx, deg))
+    o_bv, _ = F.filter_image(noisy, F.Config("bvdf", w, approx, deg))
+    np.testing.assert_array_equal(d_ev["sw"], d_em["sw"])
+    sw = d_ev["sw"].astype(bool)
+    assert 0 < sw.mean() < 1
+    np.testing.assert_array_equal(o_ev[sw], o_bv[sw])
+    np.testing.assert_array_equal(o_ev[~sw], noisy[~sw])
+
+
+@pytest.mark.parametrize("w", [3, 5])
+def test_evbdf_worked_example(w):
+    """Flat window with a centre impulse of another direction: switched (as
+    for EVMF), and the angular selection returns the flat colour; with an
+    impulse parallel to the flat colour the angles cannot tell them apart
+    (all zero): the lowest index, a flat sample, again."""
+    n = w * w
+    for imp in ([250.0, 10.0, 30.0], [100.0, 160.0, 240.0]):  # other direction; 2x flat
+        xs = np.tile([50.0, 80.0, 120.0], (n, 1))
+        xs[n // 2] = imp
+        img = xs.reshape(w, w, 3).astype(np.uint8)
+        out, d = F.filter_image(img, F.Config("evbdf", w, ent_cutoff=0.0))
+        assert d["sw"][w // 2, w // 2] == 1
+        np.testing.assert_array_equal(out[w // 2, w // 2], (50, 80, 120))
