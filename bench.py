@@ -379,6 +379,7 @@ def main():
         line["precision"] = bench_precision()
         line["rational_fit"] = bench_rational_fit()
         line["quality_study"] = bench_quality_study()
+        line["generalized_evf"] = bench_generalized_evf()
     if not args.no_gate:
         line["gate"] = bench_gate()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -584,6 +585,60 @@ def bench_rational_fit(reps=3):
     return {"workload": "3 x 1024x1024 RGBX (p=5/15/30%), AMNFE/AMNFG/EVMF, w=3,5: exact, "
                         "the paper's (4,4) rational, the library's own (d,d) rationals",
             "variants": res}
+
+
+def bench_generalized_evf(reps=3):
+    """The generalised entropy vector filter with the angular distance
+    (EVBDF: EVMF's switch, BVDF's selection), exact and minimax (degree 2-6
+    for both the arccos pieces and the ENT polynomial), beside EVMF and BVDF,
+    3 x 3 and 5 x 5, on the benchmark step's three 1024 x 1024 images.
+    Mpix/s from CUDA events; quality against the exact EVBDF (changed
+    fraction, PSNR drop, NCD difference, worst image) and PSNR vs clean."""
+    import numpy as np
+    import torch
+
+    from paper_1009_0959_gb300 import synth, vfilt
+    imgs = [synth.noisy(H, W, p, seed) for p, seed in NOISE]
+    dev = [torch.from_numpy(synth.to_rgbx(n)).cuda() for _, n in imgs]
+    out = torch.empty_like(dev[0])
+    stream = torch.cuda.current_stream()
+    res = {}
+    for w in WINDOWS:
+        exact = []
+        for k in range(3):
+            vfilt.filter(dev[k], out, criterion="evbdf", window=w)
+            torch.cuda.synchronize()
+            exact.append(out.cpu().numpy()[..., :3])
+        runs = [("evbdf", "exact", 0)] + [("evbdf", "poly", d) for d in range(2, 7)] + \
+               [("evmf", "exact", 0), ("bvdf", "exact", 0), ("bvdf", "poly", 4)]
+        for crit, approx, d in runs:
+            kw = dict(criterion=crit, window=w, approx=approx, degree=max(d, 2))
+            vfilt.filter(dev[0], out, stream=stream, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                for k in range(3):
+                    vfilt.filter(dev[k], out, stream=stream, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (3 * reps)
+            q, ps = [], []
+            for k in range(3):
+                vfilt.filter(dev[k], out, **kw)
+                torch.cuda.synchronize()
+                o = out.cpu().numpy()[..., :3]
+                q.append(_quality(imgs[k][0], exact[k], o))
+                mse = ((imgs[k][0].astype(np.float64) - o) ** 2).mean()
+                ps.append(10 * math.log10(255 ** 2 / mse))
+            name = approx if approx != "poly" else "poly%d" % d
+            res["%s/w%d/%s" % (crit, w, name)] = {
+                "mpix_s": round(H * W / ms / 1e3, 1),
+                "psnr_db_mean": round(float(np.mean(ps)), 3),
+                "changed_vs_exact_evbdf_max": max(r["changed_vs_fp32_exact"] for r in q),
+                "psnr_drop_db_max": max(r["psnr_drop_db"] for r in q)}
+    return {"workload": "3 x 1024x1024 RGBX (p=5/15/30%), w=3,5: EVBDF exact / poly 2-6, "
+                        "EVMF and BVDF for comparison", "variants": res}
 
 
 def bench_quality_study(count=64, size=512, reps=3):

@@ -53,7 +53,19 @@ typedef enum {
   VF_ERR_OOM = 6          /* device or host allocation failed */
 } vf_status;
 
-typedef enum { VF_VMF = 0, VF_BVDF = 1, VF_AMNFE = 2, VF_AMNFG = 3, VF_EVMF = 4 } vf_criterion;
+/* VF_EVBDF: the generalised entropy vector filter of Sec. 3.3 with the angle
+ * of Sec. 3.1 as its distance: EVMF's switch (P_C > beta_C), BVDF's selection
+ * in the switched windows, the centre elsewhere.  VF_EXACT or
+ * VF_MINIMAX_POLY (one degree for the arccos pieces and the ENT
+ * polynomial); single-image FP32 calls only (vf_filter, vf_filter_host). */
+typedef enum {
+  VF_VMF = 0,
+  VF_BVDF = 1,
+  VF_AMNFE = 2,
+  VF_AMNFG = 3,
+  VF_EVMF = 4,
+  VF_EVBDF = 5
+} vf_criterion;
 
 /* VF_MINIMAX_RATIONAL: the paper's printed (4,4) rationals (EXP and ENT);
  * VF_MINIMAX_RATIONAL_FIT: the library's own best (d,d) rational, d = degree

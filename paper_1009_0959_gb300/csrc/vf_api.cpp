@@ -202,7 +202,7 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   if (channels != 3 && channels != 4) return fail(ctx, VF_ERR_ARG, "channels must be 3 or 4");
   if (in_pitch < (size_t)width * channels || out_pitch < (size_t)width * channels)
     return fail(ctx, VF_ERR_ARG, "pitch smaller than a row");
-  if ((int)p->criterion < 0 || (int)p->criterion > 4) return fail(ctx, VF_ERR_ARG, "bad criterion");
+  if ((int)p->criterion < 0 || (int)p->criterion > 5) return fail(ctx, VF_ERR_ARG, "bad criterion");
   if ((int)p->approx < 0 || (int)p->approx > 3) return fail(ctx, VF_ERR_ARG, "bad approximation");
   if ((int)p->precision < 0 || (int)p->precision > 2) return fail(ctx, VF_ERR_ARG, "bad precision");
   if (p->window < 1 || (p->window & 1) == 0 || p->window > 15)
@@ -227,8 +227,10 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   const bool rfit = p->approx == VF_MINIMAX_RATIONAL_FIT;
   int apx = rfit ? kRational : (int)p->approx;
   if (crit == kVMF) apx = kExact;  // the vector median has no elementary function
-  if (apx == kRational && crit == kBVDF)
+  if (apx == kRational && (crit == kBVDF || crit == kEVBDF))
     return fail(ctx, VF_ERR_UNSUPPORTED, "the paper gives no rational for arccos");
+  if (crit == kEVBDF && p->precision != VF_FP32)
+    return fail(ctx, VF_ERR_UNSUPPORTED, "EVBDF runs in FP32 only");
 
   Launch L{};
   L.in = d_in;
@@ -251,12 +253,19 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
     auto put = [](float* dst, const double* src, int len) {
       for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
     };
-    if (crit == kBVDF) {
+    if (crit == kBVDF || crit == kEVBDF) {
       const FitVal* lo = get_fit(ctx, 0, p->degree, 0.0, 0.5);
       const FitVal* hi = get_fit(ctx, 1, p->degree, 0.0, 1.0 / std::sqrt(2.0));
       if (!lo || !hi) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
       put(L.c.a, lo->coef, p->degree + 1);
       put(L.c.b, hi->coef, p->degree + 1);
+      if (crit == kEVBDF) {  // the switch's ENT polynomial, same degree
+        if (!(L.ent_cutoff > 0.0f) || L.ent_cutoff >= 1.0f)
+          return fail(ctx, VF_ERR_ARG, "the ENT polynomial needs a cut-off in (0, 1)");
+        const FitVal* f = get_fit(ctx, 3, p->degree, (double)L.ent_cutoff, 1.0);
+        if (!f) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
+        put(L.c.e, f->coef, p->degree + 1);
+      }
     } else if (crit == kAMNFE || crit == kAMNFG) {
       if (apx == kRational && rfit) {
         const FitVal* f = get_rational_fit(ctx, 2, p->degree, 0.0, (double)p->exp_cutoff);

@@ -246,6 +246,8 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
                                   d.in_pitch, d.out_pitch, &d.params, nullptr, &imgs[i].L, &c);
     if (st == VF_OK && c.precision != VF_FP32)
       st = set_error(ctx, VF_ERR_UNSUPPORTED, "the batched form runs in FP32 only");
+    if (st == VF_OK && c.crit == kEVBDF)
+      st = set_error(ctx, VF_ERR_UNSUPPORTED, "EVBDF runs through vf_filter only");
     if (st != VF_OK) {
       delete b;
       return st;
@@ -437,8 +439,9 @@ vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* 
   if (d.height < 1 || d.width < 1 || (d.channels != 3 && d.channels != 4)) return VF_ERR_ARG;
   const size_t row = (size_t)d.width * d.channels;
   if (d.in_pitch < row || d.out_pitch < row) return VF_ERR_ARG;
-  if ((int)p->criterion < 0 || (int)p->criterion > 4 || (int)p->approx < 0 || (int)p->approx > 3)
+  if ((int)p->criterion < 0 || (int)p->criterion > 5 || (int)p->approx < 0 || (int)p->approx > 3)
     return VF_ERR_ARG;
+  if (p->criterion == VF_EVBDF) return VF_ERR_UNSUPPORTED;
   if (p->window < 1 || (p->window & 1) == 0 || p->window > 15) return VF_ERR_ARG;
   if (p->window != 3 && p->window != 5 && p->window != 7) return VF_ERR_UNSUPPORTED;
   if (p->approx == VF_MINIMAX_POLY && (p->degree < 2 || p->degree > 6)) return VF_ERR_ARG;

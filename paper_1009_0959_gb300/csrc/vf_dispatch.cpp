@@ -19,6 +19,7 @@ cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int
     case kAMNFE: VF_CASE(amnfe)
     case kAMNFG: VF_CASE(amnfg)
     case kEVMF: VF_CASE(evmf)
+    case kEVBDF: VF_CASE(evbdf)
     default: return cudaErrorInvalidValue;
   }
 }

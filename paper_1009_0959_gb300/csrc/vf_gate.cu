@@ -800,7 +800,7 @@ vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int 
   vf_status st = prepare_launch(ctx, d_in, d_out, height, width, channels, in_pitch, out_pitch, p,
                                 d_stats, &L, &cls);
   if (st != VF_OK) return st;
-  if (cls.crit == kEVMF || cls.precision != VF_FP32)
+  if (cls.crit == kEVMF || cls.crit == kEVBDF || cls.precision != VF_FP32)
     return set_error(ctx, VF_ERR_UNSUPPORTED, "the gated form runs VMF, BVDF and AMNF in FP32");
   const int ty = 4;
   L.tiles_x = (width + kTX - 1) / kTX;

@@ -12,15 +12,17 @@ namespace vf {
 
 constexpr int kTX = 32;  // output pixels per tile row (one warp)
 
-enum { kVMF = 0, kBVDF = 1, kAMNFE = 2, kAMNFG = 3, kEVMF = 4 };
+enum { kVMF = 0, kBVDF = 1, kAMNFE = 2, kAMNFG = 3, kEVMF = 4, kEVBDF = 5 };
 enum { kExact = 0, kPoly = 1, kRational = 2 };
 
 // Approximant coefficients rounded to FP32, increasing powers.
 //   BVDF: a = arccos piece on [0, 0.5], b = 2 arcsin(tau/sqrt2) piece
 //   AMNF / EVMF polynomial: a; rational: a = numerator, b = denominator
+//   EVBDF: a, b the arccos pieces as for BVDF, e the ENT polynomial
 struct Coeffs {
   float a[8];
   float b[8];
+  float e[8];
 };
 
 // Everything a launch needs, passed by value as the kernel parameter.
@@ -41,7 +43,9 @@ struct Launch {
 
 // Register aggregates (fully unrolled pair loop) or shared-memory aggregate
 // slots (rolled row-pair loop) for a window / criterion.
-constexpr bool uses_reg_path(int w, int crit) { return w == 3 || (w == 5 && crit != kBVDF); }
+constexpr bool uses_reg_path(int w, int crit) {
+  return w == 3 || (w == 5 && crit != kBVDF && crit != kEVBDF);
+}
 
 // Output rows per thread of the single-image per-window kernels: two for
 // VMF and AMNF with w <= 5 (two vertically adjacent windows share w(w - 1)
@@ -73,6 +77,7 @@ VF_DECLARE_LAUNCH(bvdf)
 VF_DECLARE_LAUNCH(amnfe)
 VF_DECLARE_LAUNCH(amnfg)
 VF_DECLARE_LAUNCH(evmf)
+VF_DECLARE_LAUNCH(evbdf)
 #undef VF_DECLARE_LAUNCH
 
 // Packed-precision launchers (vf_p_<fp16|bf16>_w<w>.cu); one CTA covers
@@ -107,7 +112,7 @@ cudaError_t launch_reuse_amnf_w5(const Launch&, int, int, int, int, cudaStream_t
 cudaError_t launch_reuse_sel_w7(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w7(const Launch&, int, int, int, int, cudaStream_t);
 inline bool has_reuse_kernel(int w, int crit) {
-  return (w == 3 || w == 5 || w == 7) && crit != kEVMF;
+  return (w == 3 || w == 5 || w == 7) && crit != kEVMF && crit != kEVBDF;
 }
 // Where the reuse kernels are the faster choice (measured on GB300 at
 // 1024 x 1024): the angle terms (BVDF), 2.0 - 3.4x; for the cheap L2 / L1

@@ -349,14 +349,15 @@ __device__ __forceinline__ float expneg(const Launch& L, float u) {
   return (u > L.exp_cutoff) ? 0.0f : e;
 }
 
-// Sec. 3.3: z ln z with the cut-off (0 below T).
-template <int APX, int DEG>
+// Sec. 3.3: z ln z with the cut-off (0 below T).  ALT: the polynomial of
+// the EVBDF switch (L.c.e; a and b hold its arccos pieces).
+template <int APX, int DEG, bool ALT = false>
 __device__ __forceinline__ float ent(const Launch& L, float z) {
   float e;
   if constexpr (APX == kExact) {
     e = z * logf(z);
   } else if constexpr (APX == kPoly) {
-    e = horner<DEG + 1>(L.c.a, z);
+    e = horner<DEG + 1>(ALT ? L.c.e : L.c.a, z);
   } else {
     e = horner<5>(L.c.a, z) * rcp_approx(horner<5>(L.c.b, z));
   }
@@ -402,7 +403,7 @@ __device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, i
     if constexpr (!FLOATS) continue;
     float r = (float)(v & 255u), g = (float)((v >> 8) & 255u), b = (float)((v >> 16) & 255u);
     float w = 0.0f;
-    if (CRIT == kBVDF) {
+    if (CRIT == kBVDF || CRIT == kEVBDF) {
       float n2 = fmaf(r, r, fmaf(g, g, b * b));
       if (n2 > 0.0f) {
         float y = rsqrtf(n2);
@@ -673,7 +674,7 @@ __device__ __forceinline__ void two_window_aggregates(const uint32_t* raw, int s
 // loops run row by row; for w <= 5 the n distances r_i stay in registers
 // between the sum and the entropy pass, for w = 7 the row loop stays rolled
 // and the entropy pass recomputes r_i (one sqrt per sample) instead.
-template <int W, int APX, int DEG>
+template <int W, int APX, int DEG, bool ALT = false>
 __device__ __forceinline__ bool evmf_switch(const Launch& L, const TileSmem& t, int px, int py,
                                             bool& tie) {
   constexpr int N = W * W, C = N / 2;
@@ -725,14 +726,14 @@ __device__ __forceinline__ bool evmf_switch(const Launch& L, const TileSmem& t, 
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       const float ri = KEEP_R ? r[KEEP_R ? a * W + i : 0] : dist(a, i);
-      esum += ent<APX, DEG>(L, ri * rs);
+      esum += ent<APX, DEG, ALT>(L, ri * rs);
     }
   }
   if (esum == 0.0f) return false;  // nothing left after the cut-off: identity
   const float4 xc = t.px[(py + C / W) * t.sw + px + C % W];
   const float dx = xc.x - mx, dy = xc.y - my, dz = xc.z - mz;
   const float PC = sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * rs;
-  const float beta = ent<APX, DEG>(L, PC) / esum;
+  const float beta = ent<APX, DEG, ALT>(L, PC) / esum;
   if (L.stats) tie = fabsf(PC - beta) <= 1e-5f * fmaxf(fabsf(PC), fabsf(beta));
   return PC > beta;
 }
@@ -777,12 +778,12 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
       store_px(L, gx, gy, v);
       ties = tie;
     }
-  } else {  // kEVMF: switch, then the vector median on the compacted list
+  } else {  // kEVMF / kEVBDF: switch, then the selection on the compacted list
     __shared__ int s_count;
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
     bool tie = false;
-    bool sw = valid && evmf_switch<W, APX, DEG>(L, t, px, py, tie);
+    bool sw = valid && evmf_switch<W, APX, DEG, CRIT == kEVBDF>(L, t, px, py, tie);
     if (valid && !sw) store_px(L, gx, gy, t.raw[(py + R) * t.sw + px + R]);
     if (sw) t.list[atomicAdd(&s_count, 1)] = threadIdx.x;
     ties = valid && tie;
@@ -792,7 +793,15 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
     for (int k = threadIdx.x; k < count; k += blockDim.x) {
       const int id = t.list[k];
       const int qx = id % kTX, qy = id / kTX;
-      Selection s = window_select<W, REG>(t.raw, t.sw, qx, qy, TermL2U8{}, sagg, stride, want_tie);
+      Selection s;
+      if constexpr (CRIT == kEVMF) {
+        s = window_select<W, REG>(t.raw, t.sw, qx, qy, TermL2U8{}, sagg, stride, want_tie);
+      } else if constexpr (APX == kExact) {  // EVBDF: the angle of Sec. 3.1
+        s = window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleExact{}, sagg, stride, want_tie);
+      } else {
+        s = window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleApprox<DEG>(L.c.a, L.c.b), sagg,
+                                  stride, want_tie);
+      }
       store_px(L, x0 + qx, y0 + qy, t.raw[(qy + s.best / W) * t.sw + qx + s.best % W]);
       ties += s.near_tie;
     }

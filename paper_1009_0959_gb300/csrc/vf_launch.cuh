@@ -54,7 +54,7 @@ cudaError_t launch_apx(const Launch& L, int approx, int degree, int ty, int grid
     case kExact: return launch_one<W, CRIT, kExact, 0>(L, ty, grid, s);
     case kPoly: return launch_deg<W, CRIT, kPoly>(L, degree, ty, grid, s);
     case kRational:
-      if constexpr (CRIT == kBVDF) return cudaErrorInvalidValue;
+      if constexpr (CRIT == kBVDF || CRIT == kEVBDF) return cudaErrorInvalidValue;
       else return launch_one<W, CRIT, kRational, 4>(L, ty, grid, s);
     default: return cudaErrorInvalidValue;
   }

@@ -13,7 +13,7 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libvfilt.so")
 
-CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4}
+CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4, "evbdf": 5}
 APPROX = {"exact": 0, "poly": 1, "rational": 2, "rational_fit": 3}
 PRECISION = {"fp32": 0, "fp16x2": 1, "bf16x2": 2}
 FUNCTIONS = {"acos_lo": 0, "acos_hi": 1, "exp": 2, "ent": 3}

@@ -124,3 +124,13 @@ def test_library_rational_fit_errors(vf):
         vf.get_approximant("exp", "rational_fit", 5, 0.0, 10.0)
     with pytest.raises(vf.VFError):
         vf.get_approximant("exp", "rational_fit", 3, 1.0, 1.0)
+
+
+def test_evbdf_argument_checks(vf):
+    """EVBDF: exact or polynomial, FP32, single-image calls only (checked on
+    the host, before any launch; VF_ERR_UNSUPPORTED = 3)."""
+    base = 1 << 20
+    assert vf.filter_ptr(base, base + 4096, 8, 8, 4, 32, 32, criterion="evbdf",
+                         approx="rational") == 3
+    assert vf.filter_ptr(base, base + 4096, 8, 8, 4, 32, 32, criterion="evbdf", approx="poly",
+                         precision="fp16x2") == 3

@@ -62,7 +62,9 @@ CASES = [("vmf", "exact", 0), ("bvdf", "exact", 0), ("bvdf", "poly", 2), ("bvdf"
          ("evmf", "poly", 3), ("evmf", "poly", 5), ("evmf", "rational", 4),
          # the library's own best (d,d) rationals (GPU) against the oracle's own
          ("amnfe", "rational_fit", 2), ("amnfe", "rational_fit", 4),
-         ("amnfg", "rational_fit", 3), ("evmf", "rational_fit", 2), ("evmf", "rational_fit", 4)]
+         ("amnfg", "rational_fit", 3), ("evmf", "rational_fit", 2), ("evmf", "rational_fit", 4),
+         # the generalised entropy vector filter with the angular distance
+         ("evbdf", "exact", 0), ("evbdf", "poly", 3), ("evbdf", "poly", 5)]
 
 
 @pytest.mark.parametrize("w", [3, 5, 7])
