@@ -203,6 +203,26 @@ vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int h
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
                          void* stream);
 
+/* Pipelined host-buffer filtering for many images: the same work as
+ * vf_filter_host, but the call returns once the copies and the kernel are
+ * enqueued.  The context keeps VF_HOST_SLOTS staging slots, each with its
+ * own stream (non-blocking, created on first use); consecutive calls take the
+ * slots in turn, so the copies of one image overlap the filtering of the
+ * others.  A call starts after the work enqueued on `stream` before it (an
+ * event); it reads h_in and writes h_out asynchronously, so both must stay
+ * valid and h_in unchanged until vf_host_sync returns.  Host memory must be
+ * pinned (cudaHostAlloc / cudaHostRegister) for the overlap.
+ * Errors: as vf_filter_host; an error of an enqueued copy or kernel is
+ * reported by vf_host_sync. */
+#define VF_HOST_SLOTS 3
+vf_status vf_filter_host_async(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height,
+                               int width, int channels, size_t in_pitch, size_t out_pitch,
+                               const vf_params* p, void* stream);
+
+/* Waits until every vf_filter_host_async call of the context has completed
+ * (its output is in host memory).  VF_ERR_CUDA if one of them failed. */
+vf_status vf_host_sync(vf_ctx* ctx);
+
 /* ---- batched form: many images in one persistent launch ------------------ */
 
 /* One image of a batch: device buffers (caller-owned, as in vf_filter) and its

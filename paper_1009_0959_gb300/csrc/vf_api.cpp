@@ -57,6 +57,16 @@ struct vf_ctx {
   uint8_t* d_stage = nullptr;
   size_t stage_bytes = 0;
   int stage_device = -1;
+  // vf_filter_host_async: staging slots, each with its own stream
+  struct HostSlot {
+    uint8_t* d_buf = nullptr;
+    size_t bytes = 0;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr;  // orders the slot's work after the caller's stream
+  };
+  HostSlot slots[VF_HOST_SLOTS];
+  int next_slot = 0;
 };
 
 namespace {
@@ -104,6 +114,14 @@ vf_status vf_create(vf_ctx** ctx) {
 void vf_destroy(vf_ctx* ctx) {
   if (!ctx) return;
   if (ctx->d_stage) cudaFree(ctx->d_stage);
+  for (auto& sl : ctx->slots) {
+    if (sl.stream) {
+      cudaStreamSynchronize(sl.stream);
+      cudaStreamDestroy(sl.stream);
+    }
+    if (sl.start) cudaEventDestroy(sl.start);
+    if (sl.d_buf) cudaFree(sl.d_buf);
+  }
   delete ctx;
 }
 
@@ -410,6 +428,74 @@ vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int h
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
   return VF_OK;
+}
+
+vf_status vf_filter_host_async(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height,
+                               int width, int channels, size_t in_pitch, size_t out_pitch,
+                               const vf_params* p, void* stream) {
+  if (!ctx) return VF_ERR_ARG;
+  if (!h_in || !h_out || !p) return fail(ctx, VF_ERR_ARG, "null pointer");
+  if (height < 1 || width < 1) return fail(ctx, VF_ERR_ARG, "image size must be >= 1 x 1");
+  if (channels != 3 && channels != 4) return fail(ctx, VF_ERR_ARG, "channels must be 3 or 4");
+  const size_t row = (size_t)width * channels;
+  if (in_pitch < row || out_pitch < row) return fail(ctx, VF_ERR_ARG, "pitch smaller than a row");
+  const size_t dpitch = (row + 15) / 16 * 16;
+  const size_t need = 2 * dpitch * (size_t)height;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  vf_ctx::HostSlot& sl = ctx->slots[ctx->next_slot];
+  if (sl.stream && sl.device != dev) {  // slot made on another device: rebuild it here
+    cudaStreamSynchronize(sl.stream);
+    cudaStreamDestroy(sl.stream);
+    cudaEventDestroy(sl.start);
+    cudaFree(sl.d_buf);
+    sl = vf_ctx::HostSlot{};
+  }
+  if (!sl.stream) {
+    if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&sl.start, cudaEventDisableTiming)) != cudaSuccess)
+      return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    sl.device = dev;
+  }
+  if (need > sl.bytes) {  // grow: the slot's earlier work may still read the old buffer
+    if ((e = cudaStreamSynchronize(sl.stream)) != cudaSuccess)
+      return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    if (sl.d_buf) cudaFree(sl.d_buf);
+    sl.d_buf = nullptr;
+    sl.bytes = 0;
+    if (cudaMalloc(&sl.d_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, VF_ERR_OOM, "device staging allocation failed");
+    }
+    sl.bytes = need;
+  }
+  ctx->next_slot = (ctx->next_slot + 1) % VF_HOST_SLOTS;
+  uint8_t* d_in = sl.d_buf;
+  uint8_t* d_out = sl.d_buf + dpitch * (size_t)height;
+  if ((e = cudaEventRecord(sl.start, (cudaStream_t)stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(sl.stream, sl.start, 0)) != cudaSuccess ||
+      (e = cudaMemcpy2DAsync(d_in, dpitch, h_in, in_pitch, row, height, cudaMemcpyHostToDevice,
+                             sl.stream)) != cudaSuccess)
+    return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  vf_status st = vf_filter(ctx, d_in, d_out, height, width, channels, dpitch, dpitch, p, sl.stream,
+                           nullptr);
+  if (st != VF_OK) return st;
+  e = cudaMemcpy2DAsync(h_out, out_pitch, d_out, dpitch, row, height, cudaMemcpyDeviceToHost,
+                        sl.stream);
+  if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+vf_status vf_host_sync(vf_ctx* ctx) {
+  if (!ctx) return VF_ERR_ARG;
+  vf_status st = VF_OK;
+  for (auto& sl : ctx->slots) {
+    if (!sl.stream) continue;
+    cudaError_t e = cudaStreamSynchronize(sl.stream);
+    if (e != cudaSuccess && st == VF_OK) st = fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return st;
 }
 
 }  // extern "C"

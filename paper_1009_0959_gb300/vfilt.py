@@ -81,6 +81,10 @@ def lib():
             L.vf_filter.restype = I
             L.vf_filter_host.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P]
             L.vf_filter_host.restype = I
+            L.vf_filter_host_async.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P]
+            L.vf_filter_host_async.restype = I
+            L.vf_host_sync.argtypes = [P]
+            L.vf_host_sync.restype = I
             L.vf_batch_create.argtypes = [P, P, I, ctypes.POINTER(P)]
             L.vf_batch_create.restype = I
             L.vf_batch_launch.argtypes = [P, P]
@@ -218,6 +222,32 @@ def filter_host(inp, out=None, *, stream=None, **params):
                                 int(out.stride(0)), ctypes.byref(p),
                                 ctypes.c_void_p(s.cuda_stream)), ctx)
     return out
+
+
+def filter_host_async(inp, out, *, stream=None, **params):
+    """vf_filter_host_async on H x W x C uint8 CPU tensors (pinned for the
+    copies to overlap): enqueues the copies and the filter and returns; call
+    host_sync() before reading `out` or changing `inp`."""
+    import torch
+    if inp.is_cuda or inp.dim() != 3 or inp.dtype != torch.uint8:
+        raise ValueError("expected an H x W x C uint8 CPU tensor")
+    if inp.stride(2) != 1 or inp.stride(1) != inp.shape[2] or out.stride(1) != out.shape[2]:
+        raise ValueError("pixels must be interleaved and rows dense")
+    p = make_params(**params)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ctx = context()
+    _check(lib().vf_filter_host_async(ctx, inp.data_ptr(), out.data_ptr(), int(inp.shape[0]),
+                                      int(inp.shape[1]), int(inp.shape[2]), int(inp.stride(0)),
+                                      int(out.stride(0)), ctypes.byref(p),
+                                      ctypes.c_void_p(s.cuda_stream)), ctx)
+    return out
+
+
+def host_sync():
+    """vf_host_sync: wait for every filter_host_async call of this thread's
+    context."""
+    ctx = context()
+    _check(lib().vf_host_sync(ctx), ctx)
 
 
 class Batch:

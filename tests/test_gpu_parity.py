@@ -276,3 +276,30 @@ def test_overlapped_launches_keep_stream_order(vf):
         vf.set_option("overlap_launch", 1)
     for _ in range(3):
         assert torch.equal(run(), plain)
+
+
+def test_host_entry_points(vf):
+    """vf_filter_host and the pipelined vf_filter_host_async / vf_host_sync
+    give the device call's bytes: images of different sizes (the staging
+    slots grow), RGB and RGBX, pinned and pageable, more images than slots."""
+    cases = [(37, 67, 4, 5, "vmf"), (120, 300, 4, 5, "bvdf"), (64, 64, 3, 3, "amnfe"),
+             (200, 150, 4, 7, "evmf"), (33, 97, 3, 5, "amnfg"), (256, 256, 4, 5, "evmf"),
+             (17, 40, 4, 3, "bvdf")]
+    host_in, expect = [], []
+    for k, (h, w, c, win, crit) in enumerate(cases):
+        clean, noisy = synth.noisy(h, w, 0.2, 300 + k)
+        src = synth.to_rgbx(noisy) if c == 4 else np.ascontiguousarray(noisy)
+        t = torch.from_numpy(src)
+        host_in.append(t.pin_memory() if k % 2 == 0 else t.clone())
+        expect.append(vf.filter(t.cuda(), criterion=crit, window=win, approx="poly",
+                                degree=4).cpu())
+    torch.cuda.synchronize()
+    for (h, w, c, win, crit), t, e in zip(cases, host_in, expect):
+        o = vf.filter_host(t, criterion=crit, window=win, approx="poly", degree=4)
+        assert torch.equal(o, e)
+    outs = [torch.zeros_like(t).pin_memory() for t in host_in]
+    for (h, w, c, win, crit), t, o in zip(cases, host_in, outs):
+        vf.filter_host_async(t, o, criterion=crit, window=win, approx="poly", degree=4)
+    vf.host_sync()
+    for o, e in zip(outs, expect):
+        assert torch.equal(o, e)
