@@ -139,16 +139,20 @@ __device__ __forceinline__ float cross2(float4 a, float4 b) {
   return fmaf(cx, cx, fmaf(cy, cy, cz * cz));
 }
 
-// Sec. 3.1, exact angle A = arccos(a.b / (|a||b|)).  Evaluated as
-// atan2(|a x b|, a.b) from exact integer dot and cross products, which is the
-// same angle without the loss of arccos near 1.  .w holds 1/|x| (0 for the
+// Sec. 3.1, exact angle A = arccos(a.b / (|a||b|)).  Evaluated through the
+// half-angle identity tan(A/2) = |a x b| / (|a||b| + a.b): colour vectors
+// are non-negative, so a.b >= 0, A is in [0, pi/2] and the argument of the
+// arctangent is in [0, 1) -- the same angle without the loss of arccos near
+// 1, from the exact integer cross and dot products, and one arctangent
+// without quadrant cases (no divergent branches).  .w holds 1/|x| (0 for the
 // zero vector); a pair with a zero vector has angle pi/2.
 struct TermAngleExact {
   __device__ __forceinline__ float operator()(float4 a, float4 b) const {
-    float dot = fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
-    float s = sqrt_approx(cross2(a, b));
-    float ang = atan2f(s, dot);
-    return (a.w * b.w == 0.0f) ? 1.57079632679f : ang;
+    const float dot = fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+    const float s = sqrt_approx(cross2(a, b));
+    const float rr = a.w * b.w;  // 1 / (|a||b|)
+    const float ang = 2.0f * atanf(s * rr * rcp_approx(fmaf(dot, rr, 1.0f)));  // 1 + cos in [1, 2]
+    return rr == 0.0f ? 1.57079632679f : ang;
   }
 };
 
