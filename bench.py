@@ -106,9 +106,19 @@ class Clocks:
 # with the predicate on; the kernels' instruction counts are not fixed by the
 # source: atan2f, the EVMF switch fraction, the pair-reuse tile borders).
 # Keyed (criterion, approx, degree, window); degree 0 for exact / rational.
-MEASURED_INST_PER_PIXEL = {("bvdf", "exact", 0, 5): 3970, ("bvdf", "poly", 4, 5): 2851}
+MEASURED_INST_PER_PIXEL = {
+    ("bvdf", "exact", 0, 5): 3261, ("bvdf", "poly", 2, 5): 2667, ("bvdf", "poly", 3, 5): 2759,
+    ("bvdf", "poly", 4, 5): 2854, ("bvdf", "poly", 5, 5): 2946, ("bvdf", "poly", 6, 5): 3040,
+    ("evmf", "exact", 0, 5): 2433, ("evmf", "poly", 4, 5): 1921, ("evmf", "rational", 0, 5): 2069,
+    ("amnfe", "exact", 0, 5): 1289, ("amnfe", "rational", 0, 5): 1349,
+    ("amnfg", "rational", 0, 5): 1399, ("vmf", "exact", 0, 5): 1466}
 # DRAM bytes (read + write) per output pixel from the same captures
-MEASURED_DRAM_BYTES_PER_PIXEL = {("bvdf", "exact", 0, 5): 7.07, ("bvdf", "poly", 4, 5): 7.06}
+MEASURED_DRAM_BYTES_PER_PIXEL = {
+    ("bvdf", "exact", 0, 5): 7.03, ("bvdf", "poly", 2, 5): 7.03, ("bvdf", "poly", 3, 5): 7.04,
+    ("bvdf", "poly", 4, 5): 7.01, ("bvdf", "poly", 5, 5): 7.03, ("bvdf", "poly", 6, 5): 7.04,
+    ("evmf", "exact", 0, 5): 6.91, ("evmf", "poly", 4, 5): 6.88, ("evmf", "rational", 0, 5): 6.94,
+    ("amnfe", "exact", 0, 5): 7.04, ("amnfe", "rational", 0, 5): 7.04,
+    ("amnfg", "rational", 0, 5): 7.05, ("vmf", "exact", 0, 5): 7.05}
 
 
 def main():
@@ -348,7 +358,7 @@ def main():
         roof.update({"achieved": round(ach, 3), "frac": round(ach / peak_tinst, 4),
                      "inst_per_pixel": inst,
                      "inst_source": "thread instructions (predicated on) per pixel, ncu on "
-                                    "6144 x 6144 (profiles/kernels_w5_6144.md)"})
+                                    "6144 x 6144 (profiles/inst_counts_w5_6144.md)"})
     else:
         roof.update({"achieved": None, "frac": None,
                      "note": "no instruction count measured for this kernel"})
