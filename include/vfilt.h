@@ -126,13 +126,16 @@ const char* vf_last_error(const vf_ctx* ctx);
 
 /* Context options (execution choices; results agree within the parity bar).
  *   VF_OPT_PAIR_REUSE  pair-reuse kernels (each pairwise term computed once
- *                      per 32 x 8 tile and shared by every window holding the
+ *                      per 32 x 8 (BVDF 3 x 3: 32 x 14, 5 x 5: 32 x 20) tile
+ *                      and shared by every window holding the
  *                      pair), for FP32 VMF, BVDF, AMNFE, AMNFG with 3 x 3,
  *                      5 x 5 and 7 x 7 windows: 0 never (per-window
  *                      kernels), 1 where they are faster (default: BVDF),
  *                      2 always.
- *   VF_OPT_TILE_ROWS   rows of the per-window kernels' 32 x TY tiles: 2, 4
- *                      (default) or 8.
+ *   VF_OPT_TILE_ROWS   thread rows TY of the per-window kernels' CTAs: 2, 4
+ *                      (default) or 8 (32 x TY outputs; 32 x 2TY for VMF
+ *                      and AMNF with w <= 5, whose threads filter two
+ *                      windows; the EVMF work-queue kernel picks its own).
  *   VF_OPT_GATE_TENSOR_CORES  1 (default): vf_gate_infer runs the three
  *                      convolutions on the tensor cores (mma, BF16 operands:
  *                      activations rounded to BF16 between layers, FP32
@@ -182,11 +185,14 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
  *   stream        CUDA stream (cudaStream_t) the kernel is launched on
  *   d_stats       optional device counters (see VF_STAT_*), or NULL; when
  *                 given, the kernel also detects near ties (a little slower)
+ * The call only enqueues work on `stream`: with VF_OPT_OVERLAP_LAUNCH (the
+ * default) the kernel is a programmatic dependent of the stream's previous
+ * kernel and waits for it before reading d_in, so stream order holds.
  * Errors: VF_ERR_ARG (null pointers, sizes < 1, channels not 3/4, pitch too
- * small, bad enums, degree out of 2..6), VF_ERR_ALIAS, VF_ERR_UNSUPPORTED
- * (window not 3/5/7, a rational for BVDF, EXP rational with a cut-off other
- * than 10, FP16X2/BF16X2 for a criterion without a packed path),
- * VF_ERR_CUDA. */
+ * small, bad enums, degree out of 2..6 (2..4 for VF_MINIMAX_RATIONAL_FIT), a
+ * failed minimax fit), VF_ERR_ALIAS, VF_ERR_UNSUPPORTED (window not 3/5/7, a
+ * rational for BVDF or EVBDF, the printed EXP rational with a cut-off other
+ * than 10, FP16X2/BF16X2 for a criterion without a packed path), VF_ERR_CUDA. */
 vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
                     int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
                     void* stream, unsigned long long* d_stats);
