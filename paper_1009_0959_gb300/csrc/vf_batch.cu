@@ -51,12 +51,35 @@ constexpr bool batch_reg(int w, int crit) {
   return w == 3 || (w == 5 && (crit == kAMNFE || crit == kAMNFG));
 }
 
+// Class decoding (inverse of class_of for window and criterion).
+__host__ __device__ constexpr int class_window(int cls) { return 3 + 2 * (cls / kClassesPerWindow); }
+__host__ __device__ constexpr int class_crit(int cls) {
+  const int k = cls % kClassesPerWindow;
+  return k == 0 ? kVMF : (k <= 2 ? kBVDF : (k <= 5 ? kAMNFE : (k <= 8 ? kAMNFG : kEVMF)));
+}
+
+// AMNF with w <= 5 and VMF 3 x 3 run the two-windows-per-thread body: their
+// tiles are 32 x 2TY, the others 32 x TY.  (The 5 x 5 VMF two-window body
+// needs about 128 registers, which would spill in the shared kernel.)
+__host__ __device__ constexpr int batch_rows_per_thread(int w, int crit) {
+  return (outputs_per_thread(w, crit) == 2 && !(crit == kVMF && w == 5)) ? 2 : 1;
+}
+
+template <int W, int CRIT, int APX, int DEG, bool REG>
+__device__ __forceinline__ void run_one(const Launch& L, int tile) {
+  if constexpr (batch_rows_per_thread(W, CRIT) == 2) {
+    process_tile2<W, CRIT, APX, DEG>(L, tile);
+  } else {
+    process_tile<W, CRIT, APX, DEG, REG>(L, tile);
+  }
+}
+
 template <int W>
 __device__ __forceinline__ void run_class(int k, const Launch& L, int tile) {
   constexpr bool RG = batch_reg(W, kVMF);
   constexpr bool RA = batch_reg(W, kAMNFE);
   switch (k) {
-    case 0: process_tile<W, kVMF, kExact, 0, RG>(L, tile); break;
+    case 0: run_one<W, kVMF, kExact, 0, RG>(L, tile); break;
     // BVDF: with 32 x 8 tiles (256 threads) the pair-reuse body, whose tile
     // grid is the same; otherwise the per-window body
     case 1:
@@ -67,12 +90,12 @@ __device__ __forceinline__ void run_class(int k, const Launch& L, int tile) {
       if (blockDim.x == kRTX * kRTY) reuse_any_tile<W, kBVDF, kPoly, 6>(L, tile);
       else process_tile<W, kBVDF, kPoly, 6, RG>(L, tile);
       break;
-    case 3: process_tile<W, kAMNFE, kExact, 0, RA>(L, tile); break;
-    case 4: process_tile<W, kAMNFE, kPoly, 6, RA>(L, tile); break;
-    case 5: process_tile<W, kAMNFE, kRational, 4, RA>(L, tile); break;
-    case 6: process_tile<W, kAMNFG, kExact, 0, RA>(L, tile); break;
-    case 7: process_tile<W, kAMNFG, kPoly, 6, RA>(L, tile); break;
-    case 8: process_tile<W, kAMNFG, kRational, 4, RA>(L, tile); break;
+    case 3: run_one<W, kAMNFE, kExact, 0, RA>(L, tile); break;
+    case 4: run_one<W, kAMNFE, kPoly, 6, RA>(L, tile); break;
+    case 5: run_one<W, kAMNFE, kRational, 4, RA>(L, tile); break;
+    case 6: run_one<W, kAMNFG, kExact, 0, RA>(L, tile); break;
+    case 7: run_one<W, kAMNFG, kPoly, 6, RA>(L, tile); break;
+    case 8: run_one<W, kAMNFG, kRational, 4, RA>(L, tile); break;
     case 9: process_tile<W, kEVMF, kExact, 0, RG>(L, tile); break;
     case 10: process_tile<W, kEVMF, kPoly, 6, RG>(L, tile); break;
     default: process_tile<W, kEVMF, kRational, 4, RG>(L, tile); break;
@@ -152,15 +175,18 @@ struct vf_batch {
 
 namespace {
 
+// Shared memory of one class's body with CTAs of 32 x ty threads.
+size_t class_smem(int w, int crit, int ty) {
+  if (batch_rows_per_thread(w, crit) == 2) return smem_bytes(w, crit, 2 * ty, true);
+  size_t m = smem_bytes(w, crit, ty, batch_reg(w, crit));
+  if (crit == kBVDF && kTX * ty == kRTX * kRTY) m = std::max(m, reuse_any_smem_bytes(w));
+  return m;
+}
+
 size_t batch_smem(const vf_batch* b, int ty) {
   size_t m = 0;
-  for (const BatchImage& im : b->host) {
-    int wi = im.cls / kClassesPerWindow, k = im.cls % kClassesPerWindow;
-    int w = 3 + 2 * wi;
-    int crit = k == 0 ? kVMF : (k <= 2 ? kBVDF : (k <= 5 ? kAMNFE : (k <= 8 ? kAMNFG : kEVMF)));
-    m = std::max(m, smem_bytes(w, crit, ty, batch_reg(w, crit)));
-    if (crit == kBVDF && kTX * ty == kRTX * kRTY) m = std::max(m, reuse_any_smem_bytes(w));
-  }
+  for (const BatchImage& im : b->host)
+    m = std::max(m, class_smem(class_window(im.cls), class_crit(im.cls), ty));
   return m;
 }
 
@@ -169,8 +195,10 @@ vf_status upload(vf_batch* b, int ty) {
   std::vector<int> begin(b->count + 1, 0);
   for (int i = 0; i < b->count; ++i) {
     Launch& L = b->host[i].L;
+    const int cls = b->host[i].cls;
+    const int rows = ty * batch_rows_per_thread(class_window(cls), class_crit(cls));
     L.tiles_x = (L.width + kTX - 1) / kTX;
-    long long tiles = (long long)L.tiles_x * ((L.height + ty - 1) / ty);
+    long long tiles = (long long)L.tiles_x * ((L.height + rows - 1) / rows);
     long long next = (long long)begin[i] + tiles;
     if (next > 0x7fffffffLL) return set_error(b->ctx, VF_ERR_UNSUPPORTED, "batch too large");
     begin[i + 1] = (int)next;
@@ -545,11 +573,12 @@ vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count
     const int i = g_static_order[q];
     staged[q] = unordered[i];
     Launch& L = staged[q].L;
+    const int rows = ty * batch_rows_per_thread(cls[i].w, cls[i].crit);
     L.tiles_x = (L.width + kTX - 1) / kTX;
     H.begin[q] = (int)total;
-    total += (long long)L.tiles_x * ((L.height + ty - 1) / ty);
+    total += (long long)L.tiles_x * ((L.height + rows - 1) / rows);
     if (total > 0x7fffffffLL) return VF_ERR_UNSUPPORTED;
-    smem = std::max(smem, smem_bytes(cls[i].w, cls[i].crit, ty, batch_reg(cls[i].w, cls[i].crit)));
+    smem = std::max(smem, class_smem(cls[i].w, cls[i].crit, ty));
   }
   H.begin[count] = (int)total;
   cudaStream_t s = (cudaStream_t)stream;
