@@ -103,7 +103,7 @@ constexpr int kReuseTileRows = 8;
 // for the exact / degree-4 5 x 5 filter against 3,681 / 6,801 with 32 x 8
 // tiles); 8 otherwise.  The batched kernel always uses 8.
 constexpr int reuse_tile_rows(int w, int crit) {
-  return crit != kBVDF ? 8 : (w == 5 ? 20 : (w == 3 ? 14 : 8));
+  return (crit != kBVDF && crit != kEVBDF) ? 8 : (w == 5 ? 20 : (w == 3 ? 14 : 8));
 }
 cudaError_t launch_reuse_sel_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w5(const Launch&, int, int, int, int, cudaStream_t);
@@ -112,12 +112,14 @@ cudaError_t launch_reuse_amnf_w5(const Launch&, int, int, int, int, cudaStream_t
 cudaError_t launch_reuse_sel_w7(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w7(const Launch&, int, int, int, int, cudaStream_t);
 inline bool has_reuse_kernel(int w, int crit) {
-  return (w == 3 || w == 5 || w == 7) && crit != kEVMF && crit != kEVBDF;
+  return (w == 3 || w == 5 || w == 7) && crit != kEVMF;
 }
 // Where the reuse kernels are the faster choice (measured on GB300 at
 // 1024 x 1024): the angle terms (BVDF), 2.0 - 3.4x; for the cheap L2 / L1
 // terms the table and box-sum traffic costs more than the terms it saves.
-inline bool reuse_pays(int w, int crit) { return has_reuse_kernel(w, crit) && crit == kBVDF; }
+inline bool reuse_pays(int w, int crit) {
+  return has_reuse_kernel(w, crit) && (crit == kBVDF || crit == kEVBDF);
+}
 cudaError_t launch_reuse(const Launch& L, int crit, int w, int apx, int degree, int grid,
                          cudaStream_t s);
 

@@ -74,7 +74,7 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
   const bool mine = (int)threadIdx.x < G::OUT;
   const bool valid = mine && gx < L.width && gy < L.height;
   const float* sagg = A + threadIdx.x;
-  int ties = 0;
+  int ties = 0, switched = 0;
   if (!mine) {
   } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
     const float4 xc = px[(oy + R) * RX + ox + R];
@@ -108,13 +108,34 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
       v = pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
     }
     if (valid) store_px(L, gx, gy, v);
+  } else if constexpr (CRIT == kEVBDF) {
+    // the generalised EVF: EVMF's switch on this output's window (the staged
+    // region is laid out as a per-window tile of pitch RX), BVDF's selection
+    // from the aggregates when it fires, the centre otherwise
+    TileSmem ts;
+    ts.px = const_cast<float4*>(px);
+    ts.raw = const_cast<uint32_t*>(raw);
+    ts.sw = RX;
+    ts.sh = G::RY;
+    bool tie = false;
+    const bool sw = valid && evmf_switch<W, APX, DEG, true>(L, ts, ox, oy, tie);
+    uint32_t v = raw[(oy + R) * RX + ox + R];
+    if (sw) {
+      const Selection s =
+          select_min<W, false>(nullptr, sagg, G::OUT, px, RX, ox, oy, L.stats != nullptr);
+      v = raw[(oy + s.best / W) * RX + ox + s.best % W];
+      tie = tie || s.near_tie;
+    }
+    if (valid) store_px(L, gx, gy, v);
+    ties = tie;
+    switched = sw;
   } else {
     const Selection s =
         select_min<W, false>(nullptr, sagg, G::OUT, px, RX, ox, oy, L.stats != nullptr);
     if (valid) store_px(L, gx, gy, raw[(oy + s.best / W) * RX + ox + s.best % W]);
     ties = s.near_tie;
   }
-  block_stats(L, valid ? 1 : 0, valid ? ties : 0, 0);
+  block_stats(L, valid ? 1 : 0, valid ? ties : 0, switched);
 }
 
 // The w sums of w consecutive values of v[0 .. 2w-2]: out[e] = v[e] + ... +
@@ -415,21 +436,28 @@ cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
 
 
 
-// VMF and BVDF
+// BVDF and EVBDF: exact or polynomial angle
+template <int W, int CRIT>
+cudaError_t launch_reuse_angle(const Launch& L, int apx, int degree, int grid, cudaStream_t s) {
+  if (apx == kExact) return launch_reuse_one<W, CRIT, kExact, 0>(L, grid, s);
+  switch (degree) {
+    case 2: return launch_reuse_one<W, CRIT, kPoly, 2>(L, grid, s);
+    case 3: return launch_reuse_one<W, CRIT, kPoly, 3>(L, grid, s);
+    case 4: return launch_reuse_one<W, CRIT, kPoly, 4>(L, grid, s);
+    case 5: return launch_reuse_one<W, CRIT, kPoly, 5>(L, grid, s);
+    case 6: return launch_reuse_one<W, CRIT, kPoly, 6>(L, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// VMF, BVDF and EVBDF
 template <int W>
 cudaError_t launch_reuse_sel(const Launch& L, int crit, int apx, int degree, int grid,
                              cudaStream_t s) {
   if (crit == kVMF) return launch_reuse_one<W, kVMF, kExact, 0>(L, grid, s);
-  if (crit != kBVDF) return cudaErrorInvalidValue;
-  if (apx == kExact) return launch_reuse_one<W, kBVDF, kExact, 0>(L, grid, s);
-  switch (degree) {
-    case 2: return launch_reuse_one<W, kBVDF, kPoly, 2>(L, grid, s);
-    case 3: return launch_reuse_one<W, kBVDF, kPoly, 3>(L, grid, s);
-    case 4: return launch_reuse_one<W, kBVDF, kPoly, 4>(L, grid, s);
-    case 5: return launch_reuse_one<W, kBVDF, kPoly, 5>(L, grid, s);
-    case 6: return launch_reuse_one<W, kBVDF, kPoly, 6>(L, grid, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (crit == kBVDF) return launch_reuse_angle<W, kBVDF>(L, apx, degree, grid, s);
+  if (crit == kEVBDF) return launch_reuse_angle<W, kEVBDF>(L, apx, degree, grid, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int W, int CRIT>

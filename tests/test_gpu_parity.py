@@ -201,11 +201,12 @@ def test_alias_rejected(vf):
 @pytest.mark.parametrize("w", [3, 5, 7])
 @pytest.mark.parametrize("crit,approx,deg", [("vmf", "exact", 4), ("bvdf", "exact", 4),
                                              ("bvdf", "poly", 3), ("amnfe", "poly", 5),
-                                             ("amnfg", "rational", 4), ("amnfe", "exact", 4)])
+                                             ("amnfg", "rational", 4), ("amnfe", "exact", 4),
+                                             ("evbdf", "exact", 4), ("evbdf", "poly", 4)])
 def test_pair_reuse_and_per_window_agree(vf, crit, approx, deg, w):
-    """Both execution paths (pair-reuse tiles of 32 x 8 and per-window tiles)
-    meet the oracle parity bar on the same 75 x 100 image (ragged in both
-    tile shapes)."""
+    """Both execution paths (pair-reuse tiles and per-window tiles) meet the
+    oracle parity bar on the same 75 x 100 image (ragged in both tile
+    shapes)."""
     clean, noisy = synth.noisy(75, 100, 0.2, 300 + w)
     o, d = F.filter_image(noisy, F.Config(crit, w, approx, deg))
     try:

@@ -69,3 +69,25 @@ def test_static_batch_limits(vf):
     assert vf.status_string(vf.batch_run_static(too_many)) == "unsupported combination"
     assert vf.batch_run_static([(t, t, {})]) == 2  # VF_ERR_ALIAS
     assert vf.batch_run_static([(t, o, {"window": 9})]) == 3
+
+
+def test_static_batch_rational_fits(vf):
+    """The library's own rationals in the allocation-free call: they must be
+    in the context's cache (an ordinary call fits them), else the call is
+    refused before anything is launched; once fitted, the call gives the
+    ordinary batched call's bytes."""
+    noisy = synth.noisy(40, 70, 0.2, 77)[1]
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    params = [dict(criterion="amnfe", window=5, approx="rational_fit", degree=3, exp_cutoff=7.5),
+              dict(criterion="evmf", window=3, approx="rational_fit", degree=2)]
+    outs = [(t, torch.zeros_like(t), p) for p in params]
+    assert vf.batch_run_static(outs[:1]) == 3  # not fitted yet: VF_ERR_UNSUPPORTED
+    ref = [(t, torch.zeros_like(t), p) for p in params]
+    b = vf.Batch(ref)  # fits and caches both rationals
+    b.launch()
+    torch.cuda.synchronize()
+    assert vf.batch_run_static(outs) == 0
+    torch.cuda.synchronize()
+    for (_, o, _), (_, r, _) in zip(outs, ref):
+        assert torch.equal(o, r)
+    b.close()
