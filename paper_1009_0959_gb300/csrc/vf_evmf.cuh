@@ -21,10 +21,11 @@
 
 namespace vf {
 
-// Tile rows of the queue kernel: 8 for 5 x 5 (less halo per output, fuller
-// batches; measured 4-13 % faster than 4), 4 for 7 x 7 (whose shared-memory
-// aggregate slots and 196-byte queue entries would leave one CTA per SM).
-constexpr int evmf_queue_rows(int w) { return w == 5 ? 8 : 4; }
+// Tile rows of the queue kernel: 8 at 5 x 5 (less halo per output, fuller
+// batches; measured 4-13 % faster than 4); 4 for larger windows, whose
+// shared-memory aggregate slots and larger queue entries would leave one CTA
+// per SM.
+constexpr int evmf_queue_rows(int w) { return w <= 5 ? 8 : 4; }
 
 // Queue of 2 * threads entries: fewer than `threads` wait after a batch, and
 // one tile adds at most `threads`.

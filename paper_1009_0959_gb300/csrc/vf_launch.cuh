@@ -8,9 +8,11 @@ namespace vf {
 
 template <int W, int CRIT, int APX, int DEG>
 cudaError_t launch_one(const Launch& L, int ty, int grid, cudaStream_t s) {
-  // EVMF with w >= 5: persistent kernel with a work queue (for w = 3 the
-  // 36-pair median is too cheap for the queue copies to pay, measured)
-  if constexpr (CRIT == kEVMF && W >= 5) {
+  // EVMF 5 x 5: persistent kernel with a work queue (measured: for w = 3 the
+  // 36-pair median is too cheap for the queue copies to pay; for w = 7 the
+  // 196-byte entries and the shared-memory aggregate slots leave two CTAs per
+  // SM, and the one-tile kernel is 20 % faster)
+  if constexpr (CRIT == kEVMF && W == 5) {
     return launch_evmf_queue<W, APX, DEG>(L, ty, grid, s);
   } else if constexpr (outputs_per_thread(W, CRIT) == 2) {
     // 32 x ty threads, 32 x 2ty outputs
