@@ -62,7 +62,7 @@ __host__ __device__ constexpr int class_crit(int cls) {
 // tiles are 32 x 2TY, the others 32 x TY.  (The 5 x 5 VMF two-window body
 // needs about 128 registers, which would spill in the shared kernel.)
 __host__ __device__ constexpr int batch_rows_per_thread(int w, int crit) {
-  return (outputs_per_thread(w, crit) == 2 && !(crit == kVMF && w == 5)) ? 2 : 1;
+  return (outputs_per_thread(w, crit) == 2 && w <= 5 && !(crit == kVMF && w == 5)) ? 2 : 1;
 }
 
 template <int W, int CRIT, int APX, int DEG, bool REG>

@@ -48,10 +48,10 @@ constexpr bool uses_reg_path(int w, int crit) {
 }
 
 // Output rows per thread of the single-image per-window kernels: two for
-// VMF and AMNF with w <= 5 (two vertically adjacent windows share w(w - 1)
-// samples and their pairs), one otherwise.
+// VMF and AMNF (two vertically adjacent windows share w(w - 1) samples and
+// their pairs), one otherwise.
 constexpr int outputs_per_thread(int w, int crit) {
-  return (w <= 5 && (crit == kVMF || crit == kAMNFE || crit == kAMNFG)) ? 2 : 1;
+  return (w <= 7 && (crit == kVMF || crit == kAMNFE || crit == kAMNFG)) ? 2 : 1;
 }
 
 // Shared memory bytes of one CTA of 32 x ty threads for window w (reg: the

@@ -813,14 +813,112 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
   block_stats(L, valid ? 1 : 0, ties, switched);
 }
 
+// The same two windows with the row loops rolled and the aggregates in
+// shared-memory slots sA[i * stride], sB[i * stride] (w = 7, where n = 49
+// register aggregates per window would not fit): the shared rows' pairs go to
+// the upper window's slots, which are then copied to the lower window's, and
+// each window adds the pairs of its own extra row.  Pair terms per output at
+// w = 7: 745.5 instead of 1176.
+template <int W, class P>
+__device__ __forceinline__ void two_window_extra_row(const uint32_t* raw, int sw, int px, int py,
+                                                     int extra, int row_lo,
+                                                     typename P::Acc* slots, int stride) {
+  // `extra`: the extra row's offset from py (0 or w); `row_lo`: the slot row
+  // of tile row py + 1 (1 for the upper window, 0 for the lower); the extra
+  // row's own slots are row 0 (upper) or w - 1 (lower)
+  using Acc = typename P::Acc;
+  const int own = extra == 0 ? 0 : W - 1;
+  uint32_t E[W];
+  Acc re[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    E[c] = load_sample(raw + (py + extra) * sw + px + c);
+    re[c] = P::zero();
+  }
+#pragma unroll
+  for (int c1 = 0; c1 < W; ++c1)
+#pragma unroll
+    for (int c2 = c1 + 1; c2 < W; ++c2) P::pair(E[c1], E[c2], re[c1], re[c2]);
+#pragma unroll 1
+  for (int r = 1; r < W; ++r) {
+    uint32_t Y[W];
+    Acc ry[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      Y[c] = load_sample(raw + (py + r) * sw + px + c);
+      ry[c] = P::zero();
+    }
+#pragma unroll
+    for (int c1 = 0; c1 < W; ++c1)
+#pragma unroll
+      for (int c2 = 0; c2 < W; ++c2) P::pair(E[c1], Y[c2], re[c1], ry[c2]);
+    Acc* row = slots + (row_lo + r - 1) * W * stride;
+#pragma unroll
+    for (int c = 0; c < W; ++c) row[c * stride] += ry[c];
+  }
+#pragma unroll
+  for (int c = 0; c < W; ++c) slots[(own * W + c) * stride] = re[c];
+}
+
+template <int W, class P>
+__device__ __forceinline__ void two_window_aggregates_smem(const uint32_t* raw, int sw, int px,
+                                                           int py, typename P::Acc* sA,
+                                                           typename P::Acc* sB, int stride) {
+  using Acc = typename P::Acc;
+#pragma unroll
+  for (int i = 0; i < W * W; ++i) sA[i * stride] = P::zero();
+  // pairs of the shared rows py + 1 .. py + w - 1 into the upper window's slots
+#pragma unroll 1
+  for (int a = 1; a < W; ++a) {
+    uint32_t X[W];
+    Acc ra[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      X[c] = load_sample(raw + (py + a) * sw + px + c);
+      ra[c] = P::zero();
+    }
+#pragma unroll
+    for (int c1 = 0; c1 < W; ++c1)
+#pragma unroll
+      for (int c2 = c1 + 1; c2 < W; ++c2) P::pair(X[c1], X[c2], ra[c1], ra[c2]);
+#pragma unroll 1
+    for (int b = a + 1; b < W; ++b) {
+      uint32_t Y[W];
+      Acc rb[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        Y[c] = load_sample(raw + (py + b) * sw + px + c);
+        rb[c] = P::zero();
+      }
+#pragma unroll
+      for (int c1 = 0; c1 < W; ++c1)
+#pragma unroll
+        for (int c2 = 0; c2 < W; ++c2) P::pair(X[c1], Y[c2], ra[c1], rb[c2]);
+#pragma unroll
+      for (int c = 0; c < W; ++c) sA[(b * W + c) * stride] += rb[c];
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) sA[(a * W + c) * stride] += ra[c];
+  }
+  // the lower window starts from the same shared-row sums
+#pragma unroll 1
+  for (int r = 1; r < W; ++r)
+#pragma unroll
+    for (int c = 0; c < W; ++c) sB[((r - 1) * W + c) * stride] = sA[(r * W + c) * stride];
+  two_window_extra_row<W, P>(raw, sw, px, py, 0, 1, sA, stride);  // row py: upper window
+  two_window_extra_row<W, P>(raw, sw, px, py, W, 0, sB, stride);  // row py + w: lower window
+}
+
 // Per-window VMF / AMNF with two outputs per thread (w <= 5): a CTA of
 // 32 x T threads covers a 32 x 2T tile, thread (px, r) the windows of rows 2r
 // and 2r + 1, formed together by two_window_aggregates.
 template <int W, int CRIT, int APX, int DEG>
 __device__ __forceinline__ void process_tile2(const Launch& L, int tile) {
   constexpr int R = W / 2, N = W * W;
+  constexpr bool REG = uses_reg_path(W, CRIT);
   const int TY = 2 * (blockDim.x / kTX);
-  const TileSmem t = carve(W, true, TY, blockDim.x);
+  // rolled form: 2 x n slots per thread (upper and lower window)
+  const TileSmem t = carve(W, REG, TY, REG ? blockDim.x : 2 * blockDim.x);
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kTX, y0 = tyi * TY;
   stage_tile<CRIT, CRIT != kVMF>(L, t, x0, y0, R);
@@ -830,12 +928,22 @@ __device__ __forceinline__ void process_tile2(const Launch& L, int tile) {
   const bool va = gx < L.width && gy < L.height;
   const bool vb = gx < L.width && gy + 1 < L.height;
   int ties = 0;
+  const int T = blockDim.x;
   if constexpr (CRIT == kVMF) {
     const bool want_tie = L.stats != nullptr;
-    float A[N], B[N];
-    two_window_aggregates<W, PairL2>(t.raw, t.sw, px, py, A, B);
-    const Selection sa = select_min<W, true>(A, nullptr, 0, t.raw, t.sw, px, py, want_tie);
-    const Selection sb = select_min<W, true>(B, nullptr, 0, t.raw, t.sw, px, py + 1, want_tie);
+    Selection sa, sb;
+    if constexpr (REG) {
+      float A[N], B[N];
+      two_window_aggregates<W, PairL2>(t.raw, t.sw, px, py, A, B);
+      sa = select_min<W, true>(A, nullptr, 0, t.raw, t.sw, px, py, want_tie);
+      sb = select_min<W, true>(B, nullptr, 0, t.raw, t.sw, px, py + 1, want_tie);
+    } else {
+      float* sA = t.agg + threadIdx.x;
+      float* sB = sA + N * T;
+      two_window_aggregates_smem<W, PairL2>(t.raw, t.sw, px, py, sA, sB, T);
+      sa = select_min<W, false>(nullptr, sA, T, t.raw, t.sw, px, py, want_tie);
+      sb = select_min<W, false>(nullptr, sB, T, t.raw, t.sw, px, py + 1, want_tie);
+    }
     if (va) {
       store_px(L, gx, gy, t.raw[(py + sa.best / W) * t.sw + px + sa.best % W]);
       ties += sa.near_tie;
@@ -845,13 +953,23 @@ __device__ __forceinline__ void process_tile2(const Launch& L, int tile) {
       ties += sb.near_tie;
     }
   } else {
-    uint32_t A[N], B[N];
-    two_window_aggregates<W, PairL1Int>(t.raw, t.sw, px, py, A, B);
     bool ta = false, tb = false;
-    const uint32_t oa =
-        amnf_finish<W, CRIT, APX, DEG>(L, t, px, py, [&](int i) { return (float)A[i]; }, ta);
-    const uint32_t ob =
-        amnf_finish<W, CRIT, APX, DEG>(L, t, px, py + 1, [&](int i) { return (float)B[i]; }, tb);
+    uint32_t oa, ob;
+    if constexpr (REG) {
+      uint32_t A[N], B[N];
+      two_window_aggregates<W, PairL1Int>(t.raw, t.sw, px, py, A, B);
+      oa = amnf_finish<W, CRIT, APX, DEG>(L, t, px, py, [&](int i) { return (float)A[i]; }, ta);
+      ob = amnf_finish<W, CRIT, APX, DEG>(L, t, px, py + 1, [&](int i) { return (float)B[i]; },
+                                          tb);
+    } else {  // integer sums in the float slots' storage
+      uint32_t* sA = reinterpret_cast<uint32_t*>(t.agg + threadIdx.x);
+      uint32_t* sB = sA + N * T;
+      two_window_aggregates_smem<W, PairL1Int>(t.raw, t.sw, px, py, sA, sB, T);
+      oa = amnf_finish<W, CRIT, APX, DEG>(L, t, px, py, [&](int i) { return (float)sA[i * T]; },
+                                          ta);
+      ob = amnf_finish<W, CRIT, APX, DEG>(L, t, px, py + 1,
+                                          [&](int i) { return (float)sB[i * T]; }, tb);
+    }
     if (va) {
       store_px(L, gx, gy, oa);
       ties += ta;
