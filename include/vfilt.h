@@ -264,11 +264,13 @@ vf_status vf_batch_launch(vf_batch* b, void* stream);
  * replayed with cudaGraphLaunch on `stream`. */
 vf_status vf_batch_graph_launch(vf_batch* b, void* stream);
 
-/* Autotuner: times every tile shape (32 x TY outputs, TY = 2, 4, 8) with every
- * resident CTA count (1 .. occupancy maximum) on the batch itself (one warm-up
- * and three timed launches each, CUDA events on `stream`), keeps the fastest
- * and reports it (any out pointer may be NULL).  Synchronous; writes the
- * outputs (the same values each time). */
+/* Autotuner: times every tile shape (32 x TY thread rows, TY = 2, 4, 8) and
+ * pixels-per-thread setting (see vf_batch_set_pixels_per_thread) with every
+ * resident CTA count (1 .. occupancy maximum) on the batch itself (one
+ * warm-up and three timed launches each, CUDA events on `stream`), keeps the
+ * fastest and reports it (any out pointer may be NULL; the pixels per thread
+ * through vf_batch_get_config).  Synchronous; writes the outputs (the same
+ * values each time). */
 vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas_per_sm,
                             float* best_ms);
 
@@ -276,6 +278,19 @@ vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas
  * occupancy maximum) up to that maximum.  Synchronous; not while a launch of
  * the batch is in flight. */
 vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm);
+
+/* Pixels per thread of the VMF and AMNF tiles with 3 x 3 and 5 x 5 windows:
+ * 1 (one window per thread, 32 x TY output tiles), 2 (two vertically
+ * adjacent windows per thread sharing their common samples' pairs, 32 x 2TY
+ * tiles), or 0 (the default: 2 for AMNF and 3 x 3 VMF, 1 for 5 x 5 VMF,
+ * whose two-window body needs more registers than the shared kernel has).
+ * Other images always take one window per thread.  Synchronous; not while a
+ * launch of the batch is in flight. */
+vf_status vf_batch_set_pixels_per_thread(vf_batch* b, int pixels_per_thread);
+
+/* The current configuration (any out pointer may be NULL). */
+vf_status vf_batch_get_config(const vf_batch* b, int* tile_rows, int* ctas_per_sm,
+                              int* pixels_per_thread);
 
 void vf_batch_destroy(vf_batch* b);
 

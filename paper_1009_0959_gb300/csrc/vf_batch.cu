@@ -40,6 +40,7 @@ __host__ __device__ constexpr int class_of(int w, int crit, int apx) {
 struct BatchImage {
   Launch L;
   int cls;
+  int two;  // 1: two windows per thread (tiles of 32 x 2TY outputs)
 };
 
 // Inside the batch kernel 3 x 3 keeps its aggregates in registers, and so
@@ -65,21 +66,37 @@ __host__ __device__ constexpr int batch_rows_per_thread(int w, int crit) {
   return (outputs_per_thread(w, crit) == 2 && w <= 5 && !(crit == kVMF && w == 5)) ? 2 : 1;
 }
 
+// The in-register two-window body exists for VMF and AMNF with w <= 5.
+__host__ __device__ constexpr bool batch_two_available(int w, int crit) {
+  return outputs_per_thread(w, crit) == 2 && w <= 5;
+}
+
+// Whether an image runs two windows per thread under the batch's
+// pixels-per-thread setting: 0 the per-class default above, 1 never, 2
+// wherever the body exists.
+__host__ __device__ constexpr int batch_two(int ppt, int w, int crit) {
+  return !batch_two_available(w, crit) ? 0
+         : ppt == 0                     ? (batch_rows_per_thread(w, crit) == 2 ? 1 : 0)
+                                        : (ppt == 2 ? 1 : 0);
+}
+
 template <int W, int CRIT, int APX, int DEG, bool REG>
-__device__ __forceinline__ void run_one(const Launch& L, int tile) {
-  if constexpr (batch_rows_per_thread(W, CRIT) == 2) {
-    process_tile2<W, CRIT, APX, DEG>(L, tile);
-  } else {
-    process_tile<W, CRIT, APX, DEG, REG>(L, tile);
+__device__ __forceinline__ void run_one(const Launch& L, int tile, int two) {
+  if constexpr (batch_two_available(W, CRIT)) {
+    if (two) {
+      process_tile2<W, CRIT, APX, DEG>(L, tile);
+      return;
+    }
   }
+  process_tile<W, CRIT, APX, DEG, REG>(L, tile);
 }
 
 template <int W>
-__device__ __forceinline__ void run_class(int k, const Launch& L, int tile) {
+__device__ __forceinline__ void run_class(int k, const Launch& L, int tile, int two) {
   constexpr bool RG = batch_reg(W, kVMF);
   constexpr bool RA = batch_reg(W, kAMNFE);
   switch (k) {
-    case 0: run_one<W, kVMF, kExact, 0, RG>(L, tile); break;
+    case 0: run_one<W, kVMF, kExact, 0, RG>(L, tile, two); break;
     // BVDF: with 32 x 8 tiles (256 threads) the pair-reuse body, whose tile
     // grid is the same; otherwise the per-window body
     case 1:
@@ -90,12 +107,12 @@ __device__ __forceinline__ void run_class(int k, const Launch& L, int tile) {
       if (blockDim.x == kRTX * kRTY) reuse_any_tile<W, kBVDF, kPoly, 6>(L, tile);
       else process_tile<W, kBVDF, kPoly, 6, RG>(L, tile);
       break;
-    case 3: run_one<W, kAMNFE, kExact, 0, RA>(L, tile); break;
-    case 4: run_one<W, kAMNFE, kPoly, 6, RA>(L, tile); break;
-    case 5: run_one<W, kAMNFE, kRational, 4, RA>(L, tile); break;
-    case 6: run_one<W, kAMNFG, kExact, 0, RA>(L, tile); break;
-    case 7: run_one<W, kAMNFG, kPoly, 6, RA>(L, tile); break;
-    case 8: run_one<W, kAMNFG, kRational, 4, RA>(L, tile); break;
+    case 3: run_one<W, kAMNFE, kExact, 0, RA>(L, tile, two); break;
+    case 4: run_one<W, kAMNFE, kPoly, 6, RA>(L, tile, two); break;
+    case 5: run_one<W, kAMNFE, kRational, 4, RA>(L, tile, two); break;
+    case 6: run_one<W, kAMNFG, kExact, 0, RA>(L, tile, two); break;
+    case 7: run_one<W, kAMNFG, kPoly, 6, RA>(L, tile, two); break;
+    case 8: run_one<W, kAMNFG, kRational, 4, RA>(L, tile, two); break;
     case 9: process_tile<W, kEVMF, kExact, 0, RG>(L, tile); break;
     case 10: process_tile<W, kEVMF, kPoly, 6, RG>(L, tile); break;
     default: process_tile<W, kEVMF, kRational, 4, RG>(L, tile); break;
@@ -130,11 +147,11 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BatchImage* __restr
     }
     __syncthreads();
     const Launch& L = s_img.L;
-    const int cls = s_img.cls;
+    const int cls = s_img.cls, two = s_img.two;
     const int wi = cls / kClassesPerWindow, k = cls - wi * kClassesPerWindow;
-    if (wi == 0) run_class<3>(k, L, tile);
-    else if (wi == 1) run_class<5>(k, L, tile);
-    else run_class<7>(k, L, tile);
+    if (wi == 0) run_class<3>(k, L, tile, two);
+    else if (wi == 1) run_class<5>(k, L, tile, two);
+    else run_class<7>(k, L, tile, two);
   }
 }
 
@@ -167,6 +184,7 @@ struct vf_batch {
   unsigned int* d_counter = nullptr;
   int count = 0;
   int ty = 4, ctas_per_sm = 0;  // 0: occupancy maximum
+  int ppt = 0;                  // pixels per thread: 0 per-class default, 1, 2
   size_t smem = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -176,8 +194,8 @@ struct vf_batch {
 namespace {
 
 // Shared memory of one class's body with CTAs of 32 x ty threads.
-size_t class_smem(int w, int crit, int ty) {
-  if (batch_rows_per_thread(w, crit) == 2) return smem_bytes(w, crit, 2 * ty, true);
+size_t class_smem(int w, int crit, int ty, int two) {
+  if (two) return smem_bytes(w, crit, 2 * ty, true);
   size_t m = smem_bytes(w, crit, ty, batch_reg(w, crit));
   if (crit == kBVDF && kTX * ty == kRTX * kRTY) m = std::max(m, reuse_any_smem_bytes(w));
   return m;
@@ -185,8 +203,10 @@ size_t class_smem(int w, int crit, int ty) {
 
 size_t batch_smem(const vf_batch* b, int ty) {
   size_t m = 0;
-  for (const BatchImage& im : b->host)
-    m = std::max(m, class_smem(class_window(im.cls), class_crit(im.cls), ty));
+  for (const BatchImage& im : b->host) {
+    const int w = class_window(im.cls), crit = class_crit(im.cls);
+    m = std::max(m, class_smem(w, crit, ty, batch_two(b->ppt, w, crit)));
+  }
   return m;
 }
 
@@ -196,7 +216,8 @@ vf_status upload(vf_batch* b, int ty) {
   for (int i = 0; i < b->count; ++i) {
     Launch& L = b->host[i].L;
     const int cls = b->host[i].cls;
-    const int rows = ty * batch_rows_per_thread(class_window(cls), class_crit(cls));
+    b->host[i].two = batch_two(b->ppt, class_window(cls), class_crit(cls));
+    const int rows = ty * (b->host[i].two ? 2 : 1);
     L.tiles_x = (L.width + kTX - 1) / kTX;
     long long tiles = (long long)L.tiles_x * ((L.height + rows - 1) / rows);
     long long next = (long long)begin[i] + tiles;
@@ -349,10 +370,12 @@ vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas
     return set_error(b->ctx, VF_ERR_CUDA, "event creation failed");
   }
   float best = 1e30f;
-  int best_ty = b->ty, best_ctas = b->ctas_per_sm;
+  int best_ty = b->ty, best_ctas = b->ctas_per_sm, best_ppt = b->ppt;
   vf_status st = VF_OK;
   const int tys[3] = {2, 4, 8};
-  for (int ti = 0; ti < 3 && st == VF_OK; ++ti) {
+  for (int pp = 0; pp < 9 && st == VF_OK; ++pp) {
+    const int ti = pp % 3;
+    b->ppt = pp / 3;  // pixels per thread: class default, 1, 2
     st = upload(b, tys[ti]);
     if (st != VF_OK) break;
     const int maxc = resident_ctas(b, tys[ti]);
@@ -373,11 +396,13 @@ vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas
         best = ms_min;
         best_ty = tys[ti];
         best_ctas = c;
+        best_ppt = b->ppt;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->ppt = best_ppt;
   if (st != VF_OK) return st;
   st = upload(b, best_ty);
   b->ctas_per_sm = best_ctas;
@@ -398,6 +423,25 @@ vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm) {
   b->ctas_per_sm = ctas_per_sm;
   drop_graph(b);
   return st;
+}
+
+vf_status vf_batch_set_pixels_per_thread(vf_batch* b, int pixels_per_thread) {
+  if (!b) return VF_ERR_ARG;
+  if (pixels_per_thread < 0 || pixels_per_thread > 2)
+    return set_error(b->ctx, VF_ERR_ARG, "pixels per thread must be 0, 1 or 2");
+  b->ppt = pixels_per_thread;
+  vf_status st = upload(b, b->ty);
+  drop_graph(b);
+  return st;
+}
+
+vf_status vf_batch_get_config(const vf_batch* b, int* tile_rows, int* ctas_per_sm,
+                              int* pixels_per_thread) {
+  if (!b) return VF_ERR_ARG;
+  if (tile_rows) *tile_rows = b->ty;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (pixels_per_thread) *pixels_per_thread = b->ppt;
+  return VF_OK;
 }
 
 void vf_batch_destroy(vf_batch* b) {
@@ -573,12 +617,13 @@ vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count
     const int i = g_static_order[q];
     staged[q] = unordered[i];
     Launch& L = staged[q].L;
-    const int rows = ty * batch_rows_per_thread(cls[i].w, cls[i].crit);
+    staged[q].two = batch_two(0, cls[i].w, cls[i].crit);
+    const int rows = ty * (staged[q].two ? 2 : 1);
     L.tiles_x = (L.width + kTX - 1) / kTX;
     H.begin[q] = (int)total;
     total += (long long)L.tiles_x * ((L.height + rows - 1) / rows);
     if (total > 0x7fffffffLL) return VF_ERR_UNSUPPORTED;
-    smem = std::max(smem, class_smem(cls[i].w, cls[i].crit, ty));
+    smem = std::max(smem, class_smem(cls[i].w, cls[i].crit, ty, staged[q].two));
   }
   H.begin[count] = (int)total;
   cudaStream_t s = (cudaStream_t)stream;

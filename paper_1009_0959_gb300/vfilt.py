@@ -96,6 +96,11 @@ def lib():
             L.vf_batch_autotune.restype = I
             L.vf_batch_configure.argtypes = [P, I, I]
             L.vf_batch_configure.restype = I
+            L.vf_batch_set_pixels_per_thread.argtypes = [P, I]
+            L.vf_batch_set_pixels_per_thread.restype = I
+            L.vf_batch_get_config.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I),
+                                              ctypes.POINTER(I)]
+            L.vf_batch_get_config.restype = I
             L.vf_batch_destroy.argtypes = [P]
             L.vf_batch_destroy.restype = None
             L.vf_batch_run_static.argtypes = [P, P, I, P]
@@ -290,10 +295,23 @@ class Batch:
         ty, ctas, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         _check(lib().vf_batch_autotune(self.handle, self._stream(stream), ctypes.byref(ty),
                                        ctypes.byref(ctas), ctypes.byref(ms)), self.ctx)
-        return {"tile_rows": ty.value, "ctas_per_sm": ctas.value, "ms": ms.value}
+        cfg = self.config()
+        cfg["ms"] = ms.value
+        return cfg
 
-    def configure(self, tile_rows=4, ctas_per_sm=0):
+    def configure(self, tile_rows=4, ctas_per_sm=0, pixels_per_thread=None):
+        if pixels_per_thread is not None:
+            _check(lib().vf_batch_set_pixels_per_thread(self.handle, int(pixels_per_thread)),
+                   self.ctx)
         _check(lib().vf_batch_configure(self.handle, int(tile_rows), int(ctas_per_sm)), self.ctx)
+
+    def config(self):
+        """tile_rows, ctas_per_sm (0: occupancy maximum) and pixels_per_thread."""
+        ty, ctas, ppt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().vf_batch_get_config(self.handle, ctypes.byref(ty), ctypes.byref(ctas),
+                                         ctypes.byref(ppt)), self.ctx)
+        return {"tile_rows": ty.value, "ctas_per_sm": ctas.value,
+                "pixels_per_thread": ppt.value}
 
     def close(self):
         if self.handle:

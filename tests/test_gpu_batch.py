@@ -88,10 +88,15 @@ def test_batch_graph_autotune_identical(vf):
     run_and_check()
     cfg = b.autotune()
     assert cfg["tile_rows"] in (2, 4, 8) and cfg["ctas_per_sm"] >= 1 and cfg["ms"] > 0
+    assert cfg["pixels_per_thread"] in (0, 1, 2)
     run_and_check()
     for ty in (2, 8):
-        b.configure(ty, 1)
-        run_and_check()
+        for ppt in (0, 1, 2):
+            b.configure(ty, 1, pixels_per_thread=ppt)
+            assert b.config() == {"tile_rows": ty, "ctas_per_sm": 1, "pixels_per_thread": ppt}
+            run_and_check()
+    with pytest.raises(vf.VFError):
+        b.configure(4, 0, pixels_per_thread=3)
     b.close()
 
 
