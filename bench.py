@@ -390,8 +390,8 @@ def main():
     # timing): every launch of a step copies its image in and its result out
     hin = [torch.from_numpy(synth.to_rgbx(n)).pin_memory() for _, n in imgs]
     # outputs: 12 pinned buffers, call i writes buffer i % 12 (a multiple of the
-    # library's 3 staging slots, so one buffer is only written from one slot's
-    # stream, in order)
+    # library's VF_HOST_SLOTS = 6 staging slots, so one buffer is only written
+    # from one slot's stream, in order)
     hout = [torch.empty_like(hin[0]).pin_memory() for _ in range(12)]
     for (c, a, d) in V[:2]:
         vfilt.filter_host(hin[0], hout[0], criterion=c, window=3, approx=a, degree=max(d, 2))

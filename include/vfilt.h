@@ -220,7 +220,7 @@ vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int h
  * pinned (cudaHostAlloc / cudaHostRegister) for the overlap.
  * Errors: as vf_filter_host; an error of an enqueued copy or kernel is
  * reported by vf_host_sync. */
-#define VF_HOST_SLOTS 3
+#define VF_HOST_SLOTS 6
 vf_status vf_filter_host_async(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height,
                                int width, int channels, size_t in_pitch, size_t out_pitch,
                                const vf_params* p, void* stream);
