@@ -112,6 +112,11 @@ MEASURED_INST_PER_PIXEL = {
     ("evmf", "exact", 0, 5): 2433, ("evmf", "poly", 4, 5): 1921, ("evmf", "rational", 0, 5): 2069,
     ("amnfe", "exact", 0, 5): 1289, ("amnfe", "rational", 0, 5): 1349,
     ("amnfg", "rational", 0, 5): 1399, ("vmf", "exact", 0, 5): 1466}
+# Pipe utilisation of the dominant kernel (ncu --set full on 6144 x 6144,
+# profiles/bvdf_exact_w5_reuse_6144.md): FP32 FMA pipe and XU (SFU / MUFU)
+# pipe, fractions of their peak issue rate
+MEASURED_PIPES = {("bvdf", "exact", 0, 5): {"fma_pipe": 0.401, "xu_pipe": 0.132,
+                                            "issue_active": 0.737}}
 # DRAM bytes (read + write) per output pixel from the same captures
 MEASURED_DRAM_BYTES_PER_PIXEL = {
     ("bvdf", "exact", 0, 5): 7.03, ("bvdf", "poly", 2, 5): 7.03, ("bvdf", "poly", 3, 5): 7.04,
@@ -353,6 +358,11 @@ def main():
         roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled "
                                 "from a 6144 x 6144 capture by pixels; algorithmic 8 B/px")
     roof["launch_ms"] = round(dom_ms, 4)
+    if mkey in MEASURED_PIPES:
+        roof["pipes_ncu"] = dict(MEASURED_PIPES[mkey], source="ncu --set full, 6144 x 6144 "
+                                 "(profiles/bvdf_exact_w5_reuse_6144.md)")
+    roof["hbm_gbs"] = (round(dram * H * W / (dom_ms / 1e3) / 1e9, 1) if dram is not None
+                       else None)
     if inst is not None:
         ach = inst * H * W / (dom_ms / 1e3) / 1e12
         roof.update({"achieved": round(ach, 3), "frac": round(ach / peak_tinst, 4),
