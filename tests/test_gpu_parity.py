@@ -100,8 +100,8 @@ def test_parity_rgb_odd_pitch(vf, crit, approx):
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (2, 3), (5, 70), (3, 33)])
-@pytest.mark.parametrize("w", [3, 7])
-@pytest.mark.parametrize("crit", ["vmf", "bvdf", "amnfg", "evmf"])
+@pytest.mark.parametrize("w", [3, 5, 7])
+@pytest.mark.parametrize("crit", ["vmf", "bvdf", "amnfg", "evmf", "evbdf"])
 def test_edge_shapes(vf, shape, w, crit):
     """Images smaller than the window and than a tile (replicated borders)."""
     clean, noisy = synth.noisy(shape[0], shape[1], 0.3, 9)
@@ -155,6 +155,31 @@ def test_stats_counters(vf):
     band = int((d["gap"] <= SEL_GAP).sum())
     assert abs(switched - ref) <= band
     assert ties >= 0
+
+
+@pytest.mark.parametrize("crit,w,approx", [("vmf", 5, "exact"), ("amnfe", 5, "rational"),
+                                            ("bvdf", 5, "poly"), ("bvdf", 3, "exact"),
+                                            ("evmf", 5, "poly"), ("evmf", 7, "exact"),
+                                            ("evbdf", 5, "poly"), ("vmf", 7, "exact")])
+def test_stats_counters_every_kernel(vf, crit, w, approx):
+    """The device counters from every kernel family (two windows per thread,
+    the tall pair-reuse tiles, the EVMF work queue): every pixel counted once,
+    and the switched count of the entropy filters within the oracle's near-tie
+    band of its own count."""
+    clean, noisy = synth.noisy(77, 130, 0.2, 23)
+    st = torch.zeros(3, dtype=torch.int64, device="cuda")
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    out = vf.filter(t, criterion=crit, window=w, approx=approx, degree=4, stats=st)
+    torch.cuda.synchronize()
+    pixels, ties, switched = st.tolist()
+    assert pixels == 77 * 130 and ties >= 0
+    o, d = F.filter_image(noisy, F.Config(crit, w, approx, 4))
+    check(crit, o, d, out.cpu().numpy())
+    if crit.startswith("ev"):
+        band = int((d["gap"] <= SEL_GAP).sum())
+        assert abs(switched - int(d["sw"].sum())) <= band
+    else:
+        assert switched == 0
 
 
 def test_minimax_quality_bar(vf):
