@@ -145,6 +145,8 @@ def main():
                     help="profiling: VF_OPT_PAIR_REUSE for --case (0 never, 1 auto, 2 always)")
     ap.add_argument("--overlap-launch", type=int, default=1, choices=[0, 1],
                     help="VF_OPT_OVERLAP_LAUNCH: programmatic dependent launches (default 1)")
+    ap.add_argument("--tile-rows", type=int, default=4, choices=[2, 4, 8],
+                    help="VF_OPT_TILE_ROWS of the per-window kernels (default 4)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -178,6 +180,7 @@ def main():
     pool_out = [torch.empty_like(pool_in[0]) for _ in range(POOL)]
     V = variants()
     vfilt.set_option("overlap_launch", args.overlap_launch)
+    vfilt.set_option("tile_rows", args.tile_rows)
     launches = [(c, a, d, w, k) for w in WINDOWS for (c, a, d) in V for k in range(3)]
 
     # quality (outside the timed region): PSNR vs clean, drop vs the exact path
@@ -926,6 +929,7 @@ def run_case(args):
                           "mpix_s": round(n * n / ms / 1e3, 1)}))
         return 0
     vfilt.set_option("pair_reuse", args.pair_reuse)
+    vfilt.set_option("tile_rows", args.tile_rows)
     c, a, w = args.case.split("/")
     d = int(a[4:]) if a.startswith("poly") else 4
     a = "poly" if a.startswith("poly") else a
