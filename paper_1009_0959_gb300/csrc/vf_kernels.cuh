@@ -1,10 +1,13 @@
-// vf_kernels.cuh -- sm_103a kernels of the sliding-window vector filters.
+// vf_kernels.cuh -- sm_103a per-window kernels of the sliding-window vector
+// filters (Sec. 3: y(r,c) = F(W(r,c))).
 //
-// One CTA filters a tile of 32 x TY output pixels.  It stages the tile plus a
-// (w-1)/2 halo into shared memory once (coalesced 32-bit RGBX loads, borders
-// replicated), converted to FP32; every thread then owns one output pixel and
-// walks the n(n-1)/2 pairs of its window, each pairwise term computed once
-// and added to the aggregates of both samples (Sec. 3: y(r,c) = F(W(r,c))).
+// One CTA filters a tile of 32 x TY output pixels (32 x 2TY when each thread
+// filters two windows).  It stages the tile plus a (w-1)/2 halo into shared
+// memory once (coalesced 32-bit RGBX loads, borders replicated): the packed
+// pixels, and FP32 colours where a term needs them.  Each thread walks the
+// n(n-1)/2 pairs of its window, each pairwise term computed once and added to
+// the aggregates of both samples; the L2 and L1 terms are formed on the
+// packed bytes with integer SIMD instructions (exact integers).
 //
 // Pair loop organisation: the window is processed as blocks of two rows
 // (a <= b); a block's samples are held in registers while its w*w (or
@@ -12,7 +15,10 @@
 // cheap distance terms) everything is unrolled and the n aggregates live in
 // registers; otherwise the row-pair loop stays rolled (keeping the code small
 // enough for the instruction cache) and each block's partial sums are added
-// to per-thread aggregate slots in shared memory.
+// to per-thread aggregate slots in shared memory.  VMF and AMNF threads filter
+// two vertically adjacent windows and form their shared samples' pairs once
+// (process_tile2).  The pair-reuse kernels (vf_reuse.cuh) and the EVMF work
+// queue (vf_evmf.cuh) build on the helpers here.
 #pragma once
 
 #include <cstdint>
@@ -595,7 +601,8 @@ __device__ __forceinline__ uint32_t amnf_pixel(const Launch& L, const TileSmem& 
 // extra row (row py for the upper, py + w for the lower window), starting
 // from Cm.  Pair terms for the two outputs: m(m - 1)/2 among the m = w(w - 1)
 // shared samples plus, per window, w(w - 1)/2 + w m with its extra row: 410
-// at w = 5 (205 per output instead of 300), 57 at w = 3 (28.5 instead of 36).
+// at w = 5 (205 per output instead of 300), 57 at w = 3 (28.5 instead of 36);
+// registers for w <= 5, the rolled form below for w = 7.
 // P::pair(a, b, x, y) adds the term of samples a, b to accumulators x and y.
 struct PairL1Int {  // AMNF: city-block distance, exact integer sums
   using Acc = uint32_t;
