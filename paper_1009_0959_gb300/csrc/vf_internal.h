@@ -96,14 +96,18 @@ constexpr int kPackedTileCols = 64;
 // offset row at a time), VMF / BVDF / AMNFE / AMNFG in FP32.
 constexpr int kReuseTileRows = 8;
 // Output rows of a single-image pair-reuse tile: taller tiles for BVDF 3 x 3
-// (14 rows) and 5 x 5 (20 rows), whose CTA has one thread per region pixel
-// (34 x 16 = 544, 36 x 24 = 864): fewer region pixels per output (1.35 at
-// w = 5 instead of 36 x 12 / 256 = 1.69), both phases in whole rounds and,
-// at w = 5, 27 warps per SM instead of 16 (measured 5,350 / 9,278 Mpix/s
-// for the exact / degree-4 5 x 5 filter against 3,681 / 6,801 with 32 x 8
-// tiles); 8 otherwise.  The batched kernel always uses 8.
+// (14 rows), 5 x 5 (20 rows) and 7 x 7 (16 rows), whose CTA has one thread
+// per region pixel (34 x 16 = 544, 36 x 24 = 864, 38 x 22 = 836 -> 864):
+// fewer region pixels per output (1.35 at w = 5 instead of 36 x 12 / 256 =
+// 1.69), both phases in whole rounds and, at w = 5, 27 warps per SM instead
+// of 16 (measured 5,350 / 9,278 Mpix/s for the exact / degree-4 5 x 5 filter
+// against 3,681 / 6,801 with 32 x 8 tiles).  At w = 7 the thread keeps its
+// pixel's 49 window sums in registers (3,188 / 3,606 Mpix/s at 4096^2
+// against 1,791 for degree 4 with 32 x 8 tiles and shared-memory sums; 12
+// rows 2,750 / 3,095, 20 rows spill and gain nothing).  8 otherwise; the
+// batched kernel always uses 8.
 constexpr int reuse_tile_rows(int w, int crit) {
-  return (crit != kBVDF && crit != kEVBDF) ? 8 : (w == 5 ? 20 : (w == 3 ? 14 : 8));
+  return (crit != kBVDF && crit != kEVBDF) ? 8 : (w == 5 ? 20 : (w == 3 ? 14 : 16));
 }
 cudaError_t launch_reuse_sel_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w5(const Launch&, int, int, int, int, cudaStream_t);

@@ -395,11 +395,141 @@ __device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
   reuse_finish<W, CRIT, APX, DEG>(L, px, raw, A, x0, y0);
 }
 
+// The chunked form with one thread per region pixel (NT >= NR): every thread
+// keeps the w^2 box sums of its own distance field in registers across the
+// offset rows and writes them to the window slots once at the end, instead
+// of adding each field row's contributions to the slots in shared memory
+// (w^2 read-modify-writes per field row).  Same sums, another order.
+inline size_t reuse_chunked_reg_smem_bytes(int w, int rty) {
+  size_t rx = kRTX + w - 1, ry = rty + w - 1, nr = rx * ry;
+  return nr * 20 + (size_t)(2 * w - 1) * nr * 4 + (size_t)w * w * kRTX * rty * 4;
+}
+
+template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
+__device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile) {
+  using G = ReuseGeom<W, RTY, NT>;
+  constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M;
+  constexpr int ROW = 2 * M + 1;  // entries of one offset row
+  static_assert(NT >= NR, "one thread per region pixel");
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* px = reinterpret_cast<float4*>(smem);
+  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
+  float* T = reinterpret_cast<float*>(smem + NR * 20);  // [ROW][NR]: T[dx + M][p]
+  float* A = T + ROW * NR;                                // [N][OUT]
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  const int x0 = txi * kRTX, y0 = tyi * RTY;
+
+  TileSmem t;
+  t.px = px;
+  t.raw = raw;
+  t.sw = RX;
+  t.sh = RY;
+  stage_tile<CRIT>(L, t, x0, y0, R);
+  __syncthreads();
+
+  const int p = threadIdx.x;
+  const bool mine = p < NR;
+  const int r = p / RX, c = p - r * RX;
+  float agg[W][W];  // [ey + R][ex + R]: window centred at region (r + ey, c + ex)
+#pragma unroll
+  for (int i = 0; i < W; ++i)
+#pragma unroll
+    for (int j = 0; j < W; ++j) agg[i][j] = 0.0f;
+  // adds field row dy (values d[dx + M]) to the windows whose rows hold it
+  auto add_row = [&](int dy, const float (&d)[ROW]) {
+    float h[W];  // h[ex + R] = d[ex - R + M] + ... + d[ex + R + M], a sliding sum
+    float s = 0.0f;
+#pragma unroll
+    for (int q = 0; q < W; ++q) s += d[q];
+    h[0] = s;
+#pragma unroll
+    for (int ex = -R + 1; ex <= R; ++ex) {
+      s += d[ex + R + M] - d[ex - R - 1 + M];
+      h[ex + R] = s;
+    }
+#pragma unroll
+    for (int ey = -R; ey <= R; ++ey) {
+      if (dy < ey - R || dy > ey + R) continue;
+#pragma unroll
+      for (int ex = -R; ex <= R; ++ex) agg[ey + R][ex + R] += h[ex + R];
+    }
+  };
+
+#pragma unroll 1
+  for (int k = 0; k <= M; ++k) {
+    // term row k: T[dx + M][p] = term(x_p, x_{p + (k, dx)}), 0 outside the region
+    auto row_terms = [&](const auto& term, const auto* src) {
+      if (!mine) return;
+      const bool row_in = r + k < RY;
+      const auto xp = load_sample(src + p);
+#pragma unroll
+      for (int dx = -M; dx <= M; ++dx) {
+        if (k == 0 && dx <= 0) continue;
+        float v = 0.0f;
+        if (row_in && c + dx >= 0 && c + dx < RX) v = term(xp, load_sample(src + p + k * RX + dx));
+        T[(dx + M) * NR + p] = v;
+      }
+    };
+    if constexpr (CRIT == kVMF) {
+      row_terms(TermL2U8{}, raw);
+    } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
+      row_terms(TermL1{}, px);
+    } else if constexpr (APX == kExact) {
+      row_terms(TermAngleExact{}, px);
+    } else {
+      row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b), px);
+    }
+    __syncthreads();
+    if (mine) {  // field rows +k and -k of this pixel
+      float d[ROW];
+#pragma unroll
+      for (int dx = -M; dx <= M; ++dx) {
+        const int cq = c + dx;
+        float v = 0.0f;
+        if (k > 0 || dx > 0) {
+          v = T[(dx + M) * NR + p];  // 0 when p + (k, dx) is outside
+        } else if (dx < 0 && cq >= 0) {
+          v = T[(-dx + M) * NR + p + dx];
+        }
+        d[dx + M] = v;
+      }
+      add_row(k, d);
+      if (k > 0) {
+        const int rq = r - k;
+#pragma unroll
+        for (int dx = -M; dx <= M; ++dx) {
+          const int cq = c + dx;
+          d[dx + M] = (rq >= 0 && cq >= 0 && cq < RX) ? T[(-dx + M) * NR + rq * RX + cq] : 0.0f;
+        }
+        add_row(-k, d);
+      }
+    }
+    __syncthreads();  // T is rewritten by the next offset row
+  }
+  // window centred at region (r + ey, c + ex) = output (r + ey - R, c + ex - R)
+  if (mine) {
+#pragma unroll
+    for (int ey = -R; ey <= R; ++ey)
+#pragma unroll
+      for (int ex = -R; ex <= R; ++ex) {
+        const int oy = r + ey - R, ox = c + ex - R;
+        if (oy >= 0 && oy < RTY && ox >= 0 && ox < kRTX) {
+          const int j = (R - ey) * W + (R - ex);  // p's index in that window
+          A[j * G::OUT + oy * kRTX + ox] = agg[ey + R][ex + R];
+        }
+      }
+  }
+  __syncthreads();
+  reuse_finish<W, CRIT, APX, DEG, RTY, NT>(L, px, raw, A, x0, y0);
+}
+
 // One 32 x 8 tile per CTA (a 256-thread CTA whose shared memory is reused:
 // callers looping over tiles must __syncthreads() between calls).
 template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
 __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
-  if constexpr (W >= 7) {
+  if constexpr (W >= 7 && NT >= (kRTX + W - 1) * (RTY + W - 1)) {
+    reuse_chunked_reg_tile<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+  } else if constexpr (W >= 7) {
     static_assert(RTY == kRTY && NT == kRTX * kRTY, "the chunked form has 32 x 8 tiles");
     reuse_chunked_tile<W, CRIT, APX, DEG>(L, tile);
   } else {
@@ -408,7 +538,8 @@ __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
 }
 
 inline size_t reuse_any_smem_bytes(int w, int rty = kRTY) {
-  return w >= 7 ? reuse_chunked_smem_bytes(w) : reuse_smem_bytes(w, rty);
+  if (w >= 7) return rty == kRTY ? reuse_chunked_smem_bytes(w) : reuse_chunked_reg_smem_bytes(w, rty);
+  return reuse_smem_bytes(w, rty);
 }
 
 // 32 x RTY outputs per CTA of NT threads: two 256-thread CTAs per SM at
