@@ -126,12 +126,12 @@ const char* vf_last_error(const vf_ctx* ctx);
 
 /* Context options (execution choices; results agree within the parity bar).
  *   VF_OPT_PAIR_REUSE  pair-reuse kernels (each pairwise term computed once
- *                      per 32 x 8 (BVDF 3 x 3: 32 x 14, 5 x 5: 32 x 20) tile
- *                      and shared by every window holding the
- *                      pair), for FP32 VMF, BVDF, AMNFE, AMNFG with 3 x 3,
- *                      5 x 5 and 7 x 7 windows: 0 never (per-window
- *                      kernels), 1 where they are faster (default: BVDF),
- *                      2 always.
+ *                      per 32 x 8 tile (BVDF, EVBDF and EVMF 3 x 3: 32 x 14,
+ *                      5 x 5: 32 x 20; every 7 x 7 filter: 32 x 16) and
+ *                      shared by every window holding the pair), for every
+ *                      FP32 criterion with 3 x 3, 5 x 5 and 7 x 7 windows:
+ *                      0 never (per-window kernels), 1 where they are faster
+ *                      (default: BVDF and EVBDF), 2 always.
  *   VF_OPT_TILE_ROWS   thread rows TY of the per-window kernels' CTAs: 2, 4
  *                      (default) or 8 (32 x TY outputs; 32 x 2TY for VMF
  *                      and AMNF with w <= 5, whose threads filter two

@@ -29,6 +29,12 @@ cudaError_t launch_filter(const Launch& L, int criterion, int w, int approx, int
 cudaError_t launch_reuse(const Launch& L, int crit, int w, int apx, int degree, int grid,
                          cudaStream_t s) {
   const bool amnf = crit == kAMNFE || crit == kAMNFG;
+  if (crit == kEVMF) {
+    if (w == 3) return launch_reuse_evmf_w3(L, apx, degree, grid, s);
+    if (w == 5) return launch_reuse_evmf_w5(L, apx, degree, grid, s);
+    if (w == 7) return launch_reuse_evmf_w7(L, apx, degree, grid, s);
+    return cudaErrorInvalidValue;
+  }
   if (w == 3) return amnf ? launch_reuse_amnf_w3(L, crit, apx, degree, grid, s)
                           : launch_reuse_sel_w3(L, crit, apx, degree, grid, s);
   if (w == 5) return amnf ? launch_reuse_amnf_w5(L, crit, apx, degree, grid, s)

@@ -91,12 +91,13 @@ VF_DECLARE_PACKED(bf16)
 #undef VF_DECLARE_PACKED
 constexpr int kPackedTileCols = 64;
 
-// Pair-reuse launchers (vf_r_w<w>_<sel|amnf>.cu): one CTA covers 32 x 8 or
-// 32 x 16 outputs; windows 3, 5 (whole term table) and 7 (table built one
-// offset row at a time), VMF / BVDF / AMNFE / AMNFG in FP32.
+// Pair-reuse launchers (vf_r_w<w>_<sel|amnf|evmf>.cu): one CTA covers 32 x
+// RTY outputs; windows 3, 5 (whole term table) and 7 (table built one offset
+// row at a time), every criterion in FP32.
 constexpr int kReuseTileRows = 8;
-// Output rows of a single-image pair-reuse tile: taller tiles for BVDF 3 x 3
-// (14 rows), 5 x 5 (20 rows) and 7 x 7 (16 rows), whose CTA has one thread
+// Output rows of a single-image pair-reuse tile: taller tiles for BVDF (and
+// EVBDF, EVMF) 3 x 3 (14 rows), 5 x 5 (20 rows) and every 7 x 7 filter
+// (16 rows), whose CTA has one thread
 // per region pixel (34 x 16 = 544, 36 x 24 = 864, 38 x 22 = 836 -> 864):
 // fewer region pixels per output (1.35 at w = 5 instead of 36 x 12 / 256 =
 // 1.69), both phases in whole rounds and, at w = 5, 27 warps per SM instead
@@ -107,7 +108,7 @@ constexpr int kReuseTileRows = 8;
 // rows 2,750 / 3,095, 20 rows spill and gain nothing).  8 otherwise; the
 // batched kernel always uses 8.
 constexpr int reuse_tile_rows(int w, int crit) {
-  return (crit != kBVDF && crit != kEVBDF) ? 8 : (w == 5 ? 20 : (w == 3 ? 14 : 16));
+  return w == 7 ? 16 : ((crit != kBVDF && crit != kEVBDF && crit != kEVMF) ? 8 : (w == 5 ? 20 : 14));
 }
 cudaError_t launch_reuse_sel_w3(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w5(const Launch&, int, int, int, int, cudaStream_t);
@@ -115,12 +116,16 @@ cudaError_t launch_reuse_amnf_w3(const Launch&, int, int, int, int, cudaStream_t
 cudaError_t launch_reuse_amnf_w5(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_sel_w7(const Launch&, int, int, int, int, cudaStream_t);
 cudaError_t launch_reuse_amnf_w7(const Launch&, int, int, int, int, cudaStream_t);
-inline bool has_reuse_kernel(int w, int crit) {
-  return (w == 3 || w == 5 || w == 7) && crit != kEVMF;
-}
+cudaError_t launch_reuse_evmf_w3(const Launch&, int, int, int, cudaStream_t);
+cudaError_t launch_reuse_evmf_w5(const Launch&, int, int, int, cudaStream_t);
+cudaError_t launch_reuse_evmf_w7(const Launch&, int, int, int, cudaStream_t);
+inline bool has_reuse_kernel(int w, int crit) { return w == 3 || w == 5 || w == 7; }
 // Where the reuse kernels are the faster choice (measured on GB300 at
 // 1024 x 1024): the angle terms (BVDF), 2.0 - 3.4x; for the cheap L2 / L1
-// terms the table and box-sum traffic costs more than the terms it saves.
+// terms the table and box-sum traffic costs more than the terms it saves
+// (EVMF 20.5k / 8.8k / 3.7k Mpix/s at w = 3 / 5 / 7 against 32.1k / 9.7k /
+// 3.7k for the per-window kernels and the work queue; AMNF 7 x 7 4.4k against
+// 6.5k; VMF 7 x 7 5.5k against 5.3k, within the noise).
 inline bool reuse_pays(int w, int crit) {
   return has_reuse_kernel(w, crit) && (crit == kBVDF || crit == kEVBDF);
 }

@@ -108,17 +108,19 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
       v = pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
     }
     if (valid) store_px(L, gx, gy, v);
-  } else if constexpr (CRIT == kEVBDF) {
-    // the generalised EVF: EVMF's switch on this output's window (the staged
-    // region is laid out as a per-window tile of pitch RX), BVDF's selection
-    // from the aggregates when it fires, the centre otherwise
+  } else if constexpr (CRIT == kEVMF || CRIT == kEVBDF) {
+    // the EVMF (Eq. equ_evf) and the generalised EVF: the entropy switch on
+    // this output's window (the staged region is laid out as a per-window
+    // tile of pitch RX), the vector median (EVMF: Euclidean aggregates) or
+    // BVDF's selection (EVBDF: angle aggregates) when it fires, the centre
+    // otherwise
     TileSmem ts;
     ts.px = const_cast<float4*>(px);
     ts.raw = const_cast<uint32_t*>(raw);
     ts.sw = RX;
     ts.sh = G::RY;
     bool tie = false;
-    const bool sw = valid && evmf_switch<W, APX, DEG, true>(L, ts, ox, oy, tie);
+    const bool sw = valid && evmf_switch<W, APX, DEG, CRIT == kEVBDF>(L, ts, ox, oy, tie);
     uint32_t v = raw[(oy + R) * RX + ox + R];
     if (sw) {
       const Selection s =
@@ -212,7 +214,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
       }
     }
   };
-  if constexpr (CRIT == kVMF) {
+  if constexpr (CRIT == kVMF || CRIT == kEVMF) {
     row_terms(TermL2U8{}, raw);  // packed bytes: exact squared distances
   } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
     row_terms(TermL1{}, px);
@@ -349,7 +351,7 @@ __device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
         }
       }
     };
-    if constexpr (CRIT == kVMF) {
+    if constexpr (CRIT == kVMF || CRIT == kEVMF) {
       row_terms(TermL2{});
     } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
       row_terms(TermL1{});
@@ -470,7 +472,7 @@ __device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile
         T[(dx + M) * NR + p] = v;
       }
     };
-    if constexpr (CRIT == kVMF) {
+    if constexpr (CRIT == kVMF || CRIT == kEVMF) {
       row_terms(TermL2U8{}, raw);
     } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
       row_terms(TermL1{}, px);
@@ -612,6 +614,12 @@ cudaError_t launch_reuse_amnf(const Launch& L, int crit, int apx, int degree, in
   if (crit == kAMNFE) return launch_reuse_amnf_c<W, kAMNFE>(L, apx, degree, grid, s);
   if (crit == kAMNFG) return launch_reuse_amnf_c<W, kAMNFG>(L, apx, degree, grid, s);
   return cudaErrorInvalidValue;
+}
+
+// EVMF: the ENT function exact, polynomial or rational, as for AMNF's EXP
+template <int W>
+cudaError_t launch_reuse_evmf(const Launch& L, int apx, int degree, int grid, cudaStream_t s) {
+  return launch_reuse_amnf_c<W, kEVMF>(L, apx, degree, grid, s);
 }
 
 }  // namespace vf

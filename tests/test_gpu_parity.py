@@ -182,6 +182,31 @@ def test_stats_counters_every_kernel(vf, crit, w, approx):
         assert switched == 0
 
 
+@pytest.mark.parametrize("w", [3, 5, 7])
+def test_stats_counters_reuse_evmf(vf, w):
+    """The EVMF in the pair-reuse tiles (the switch in the finish phase):
+    every pixel counted once, the switched count within the oracle's near-tie
+    band, the same counts as the per-window kernels."""
+    clean, noisy = synth.noisy(77, 130, 0.2, 29)
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    counts = []
+    try:
+        for mode in (2, 0):
+            vf.set_option("pair_reuse", mode)
+            st = torch.zeros(3, dtype=torch.int64, device="cuda")
+            vf.filter(t, criterion="evmf", window=w, approx="poly", degree=4, stats=st)
+            torch.cuda.synchronize()
+            counts.append(st.tolist())
+    finally:
+        vf.set_option("pair_reuse", 1)
+    _, d = F.filter_image(noisy, F.Config("evmf", w, "poly", 4))
+    band = int((d["gap"] <= SEL_GAP).sum())
+    for pixels, ties, switched in counts:
+        assert pixels == 77 * 130 and ties >= 0
+        assert abs(switched - int(d["sw"].sum())) <= band
+    assert counts[0][2] == counts[1][2]
+
+
 def test_minimax_quality_bar(vf):
     """Against the FP64 oracle's exact filter on the 256 x 256, 10 % case:
     the degree-4 arccos (Table 1) changes at most 0.5 % of the selections and
@@ -227,7 +252,9 @@ def test_alias_rejected(vf):
 @pytest.mark.parametrize("crit,approx,deg", [("vmf", "exact", 4), ("bvdf", "exact", 4),
                                              ("bvdf", "poly", 3), ("amnfe", "poly", 5),
                                              ("amnfg", "rational", 4), ("amnfe", "exact", 4),
-                                             ("evbdf", "exact", 4), ("evbdf", "poly", 4)])
+                                             ("evbdf", "exact", 4), ("evbdf", "poly", 4),
+                                             ("evmf", "exact", 4), ("evmf", "poly", 4),
+                                             ("evmf", "rational", 4)])
 def test_pair_reuse_and_per_window_agree(vf, crit, approx, deg, w):
     """Both execution paths (pair-reuse tiles and per-window tiles) meet the
     oracle parity bar on the same 75 x 100 image (ragged in both tile
