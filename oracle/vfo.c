@@ -172,7 +172,10 @@ typedef struct {
                     aggregate of a sample whose vector differs (selection
                     filters), distance of the AMNF output to the nearest
                     rounding boundary, or |P_C - beta_C| / max for the EVMF
-                    switch; +inf when no competitor exists */
+                    switch; each lowered to the relative distance of an
+                    argument of E (AMNF) or of a P_j (EVMF switch) from its
+                    cut-off where that is smaller; +inf when no competitor
+                    exists */
   uint8_t* sw;   /* EVMF: 1 if the noise filtering branch was taken */
   double* yreal; /* AMNF: unrounded output, 3 per pixel */
 } vfo_diag;
@@ -242,8 +245,16 @@ static int vfo_bvdf_select(const vfo_params* p, int n, double x[][3], double* ga
   return vfo_argmin(n, agg, x, gap);
 }
 
-/* Sec. 3.2, Eq. (equ_amnf): kernel-weighted mean of the window. */
-static void vfo_amnf(const vfo_params* p, int n, double x[][3], double y[3]) {
+/* Relative distance of z from the cut-off t (t > 0): the cut-off is a
+ * threshold decision inside E and ENT (Sec. 3.2, 3.3), and a z this close to
+ * it may fall on either side once rounded, like a near tie of the argmin. */
+static double vfo_cut_gap(double z, double t) {
+  return t > 0.0 ? fabs(z - t) / t : INFINITY;
+}
+
+/* Sec. 3.2, Eq. (equ_amnf): kernel-weighted mean of the window.  *cgap
+ * (optional): the smallest vfo_cut_gap of the arguments z of E. */
+static void vfo_amnf(const vfo_params* p, int n, double x[][3], double y[3], double* cgap) {
   int C = (n + 1) / 2 - 1; /* 0-based centre */
   double h[VFO_MAXN];
   double scale = pow((double)n, -p->kappa / 3.0);
@@ -254,6 +265,7 @@ static void vfo_amnf(const vfo_params* p, int n, double x[][3], double y[3]) {
     h[i] = scale * s;
     if (h[i] != 0.0) all_zero = 0;
   }
+  if (cgap) *cgap = INFINITY;
   if (all_zero) { /* constant window: every sample equals the centre */
     for (int k = 0; k < 3; ++k) y[k] = x[C][k];
     return;
@@ -267,6 +279,7 @@ static void vfo_amnf(const vfo_params* p, int n, double x[][3], double y[3]) {
       double d = vfo_l2(x[C], x[i]) / h[i];
       u = 0.5 * d * d; /* 0.5 ||(x_C - x_i)/h_i||_2^2 */
     }
+    if (cgap) *cgap = fmin(*cgap, vfo_cut_gap(u, p->exp_cutoff));
     double wi = pow(h[i], -3.0) * vfo_expneg(p, u);
     wsum += wi;
     for (int k = 0; k < 3; ++k) acc[k] += wi * x[i][k];
@@ -289,14 +302,18 @@ static int vfo_evmf_switch(const vfo_params* p, int n, double x[][3], double* ga
   }
   if (gap) *gap = INFINITY;
   if (rsum == 0.0) return 0; /* constant window: identity */
-  double esum = 0.0;
-  for (int j = 0; j < n; ++j) esum += vfo_ent(p, r[j] / rsum);
+  double esum = 0.0, cgap = INFINITY;
+  for (int j = 0; j < n; ++j) {
+    esum += vfo_ent(p, r[j] / rsum);
+    cgap = fmin(cgap, vfo_cut_gap(r[j] / rsum, p->ent_cutoff));
+  }
+  if (gap) *gap = cgap;
   if (esum == 0.0) return 0; /* no entropy left after the cut-off: identity */
   double PC = r[C] / rsum;
   double beta = vfo_ent(p, PC) / esum;
   if (gap) {
     double m = fmax(fabs(PC), fabs(beta));
-    *gap = m > 0.0 ? fabs(PC - beta) / m : INFINITY;
+    *gap = fmin(cgap, m > 0.0 ? fabs(PC - beta) / m : INFINITY);
   }
   return PC > beta;
 }
@@ -339,8 +356,10 @@ int vfo_filter_rows(const uint8_t* img, int H, int W, int C, const vfo_params* p
           break;
         case VFO_AMNFE:
         case VFO_AMNFG:
-          vfo_amnf(p, n, x, y);
+          double cgap;
+          vfo_amnf(p, n, x, y, &cgap);
           gap = fmin(fmin(vfo_round_gap(y[0]), vfo_round_gap(y[1])), vfo_round_gap(y[2]));
+          gap = fmin(gap, cgap);
           if (dg && dg->yreal)
             for (int k = 0; k < 3; ++k) dg->yreal[pix * 3 + k] = y[k];
           break;
@@ -421,6 +440,6 @@ int vfo_window_evmf_switch(const vfo_params* p, int n, const double* xs, double*
 
 /* AMNF output of one window given as x[n][3], exposed for the tests. */
 int vfo_window_amnf(const vfo_params* p, int n, const double* xs, double* y) {
-  vfo_amnf(p, n, (double (*)[3])xs, y);
+  vfo_amnf(p, n, (double (*)[3])xs, y, NULL);
   return 0;
 }

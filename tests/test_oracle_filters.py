@@ -300,6 +300,46 @@ def test_evmf_cutoff_reading():
     assert sw_cut and not sw_plain
 
 
+def test_evmf_cutoff_tie_reported():
+    """A P_j exactly at the ENT cut-off T = 1/20 (Sec. 3.3) is a threshold
+    decision that rounding may take either way: the diagnostic gap reports it
+    as a near tie.  Blue channel {131, 166 x 6, 236 x 2} (R, G fixed): mean
+    1599/9, distances 420/9, 105/9 and 525/9, sum 2100/9, so P = 105/2100 =
+    1/20 for the six 166s.  With 130 instead of 131 the sum is 2104/9 and
+    P = 104/2104: gap 1 - 20 * 104 / 2104 = 24/2104."""
+    def win(b0):
+        img = np.zeros((3, 3, 3), np.uint8)
+        img[..., 0], img[..., 1] = 173, 169
+        img[..., 2] = np.array([[b0, 166, 166], [166, 236, 166], [166, 236, 166]])
+        return img
+    _, d = F.filter_image(win(131), F.Config("evmf", 3))
+    assert d["gap"][1, 1] < 1e-12
+    _, d = F.filter_image(win(130), F.Config("evmf", 3))
+    assert d["gap"][1, 1] == pytest.approx(24 / 2104, rel=1e-12)
+    _, d = F.filter_image(win(131), F.Config("evmf", 3, ent_cutoff=0.0))
+    assert d["gap"][1, 1] > 0.1  # no cut-off: only the switch's own gap
+
+
+@pytest.mark.parametrize("crit", ["amnfe", "amnfg"])
+def test_amnf_cutoff_tie_reported(crit):
+    """An argument of E exactly at the EXP cut-off (Sec. 3.2) is reported as a
+    near tie: with the cut-off set to sample k's argument z_k =
+    ||(x_C - x_k) / h_k|| (L1 for AMNFE, half the squared L2 for AMNFG; h_k =
+    n^(-kappa/3) sum_j ||x_k - x_j||_1), the centre's gap is 0 up to rounding."""
+    rng = np.random.default_rng(5)
+    img = rng.integers(0, 256, (3, 3, 3)).astype(np.uint8)
+    x = img.reshape(9, 3).astype(np.float64)
+    h = 9.0 ** (-0.33 / 3.0) * np.abs(x[:, None, :] - x[None, :, :]).sum(-1).sum(1)
+    dc = x[4] - x
+    z = np.abs(dc).sum(1) / h if crit == "amnfe" else 0.5 * (dc ** 2).sum(1) / h ** 2
+    k = int(np.argmax(z))
+    _, d = F.filter_image(img, F.Config(crit, 3, exp_cutoff=float(z[k])))
+    assert d["gap"][1, 1] < 1e-12
+    _, d = F.filter_image(img, F.Config(crit, 3))
+    y = d["yreal"][1, 1]
+    assert d["gap"][1, 1] == pytest.approx(np.abs(y - np.floor(y) - 0.5).min(), rel=1e-9)
+
+
 def test_ent_values():
     cfg = F.Config("evmf", 3)
     assert F.ent(cfg, 0.04) == 0.0
