@@ -381,7 +381,9 @@ vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, 
 /* vf_filter restricted to the pixels whose flag byte is non-zero; all other
  * pixels are copied from d_in.  VMF, BVDF, AMNFE and AMNFG in FP32 (EVMF has
  * its own switch: VF_ERR_UNSUPPORTED).  Otherwise as vf_filter; the third
- * counter (VF_STAT_SWITCHED) counts the flagged pixels. */
+ * counter (VF_STAT_SWITCHED) counts the flagged pixels.  Where vf_filter
+ * runs the pair-reuse kernels (VF_OPT_PAIR_REUSE) so does this call, with
+ * the same sums: a flagged pixel gets exactly vf_filter's output. */
 vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
                           int channels, size_t in_pitch, size_t out_pitch, const uint8_t* d_flags,
                           size_t flag_pitch, const vf_params* p, void* stream,

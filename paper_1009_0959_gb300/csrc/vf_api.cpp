@@ -50,7 +50,7 @@ struct vf_ctx {
   std::map<FitKey, FitVal> fits;
   std::string last_error;
   int tile_rows = 4;  // TY of the per-window single-image launches
-  int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF), 2 always (w = 3 / 5)
+  int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF, EVBDF), 2 always
   int gate_tc = 1;     // gate inference on the tensor cores (BF16 activations)
   int overlap = 1;     // programmatic dependent launches for vf_filter
   // device staging of vf_filter_host (grown on demand, freed by vf_destroy)
@@ -333,6 +333,11 @@ vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg) { return fail(ctx
 
 bool gate_tensor_cores(const vf_ctx* ctx) { return ctx->gate_tc != 0; }
 
+bool use_pair_reuse(const vf_ctx* ctx, int w, int crit) {
+  return ctx->pair_reuse == 2 ? has_reuse_kernel(w, crit)
+                              : (ctx->pair_reuse == 1 && reuse_pays(w, crit));
+}
+
 const double* cached_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi) {
   auto it = ctx->fits.find(FitKey{0, fn, degree, lo, hi});
   return it == ctx->fits.end() ? nullptr : it->second.coef;
@@ -365,9 +370,7 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
                                 d_stats, &L, &cls);
   if (st != VF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  const bool reuse = ctx->pair_reuse == 2 ? has_reuse_kernel(cls.w, cls.crit)
-                                           : (ctx->pair_reuse == 1 && reuse_pays(cls.w, cls.crit));
-  if (cls.precision == VF_FP32 && reuse) {
+  if (cls.precision == VF_FP32 && use_pair_reuse(ctx, cls.w, cls.crit)) {
     L.tiles_x = (width + kTX - 1) / kTX;
     const int rows = reuse_tile_rows(cls.w, cls.crit);
     const long long rgrid = (long long)L.tiles_x * ((height + rows - 1) / rows);

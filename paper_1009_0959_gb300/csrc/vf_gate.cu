@@ -802,11 +802,26 @@ vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int 
   if (st != VF_OK) return st;
   if (cls.crit == kEVMF || cls.crit == kEVBDF || cls.precision != VF_FP32)
     return set_error(ctx, VF_ERR_UNSUPPORTED, "the gated form runs VMF, BVDF and AMNF in FP32");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (use_pair_reuse(ctx, cls.w, cls.crit)) {
+    // the pair-reuse tiles with the flags read in the finish phase (and
+    // whole tiles without a flag copied): every pair term of a tile is
+    // computed once, which for the angle terms costs less than the
+    // per-window loop on the flagged pixels alone
+    L.flags = d_flags;
+    L.flag_pitch = (long long)flag_pitch;
+    L.tiles_x = (width + kTX - 1) / kTX;
+    const int rows = reuse_tile_rows(cls.w, cls.crit);
+    const long long rgrid = (long long)L.tiles_x * ((height + rows - 1) / rows);
+    if (rgrid > 0x7fffffffLL) return set_error(ctx, VF_ERR_UNSUPPORTED, "image too large");
+    cudaError_t e = launch_reuse(L, cls.crit, cls.w, cls.apx, cls.deg, (int)rgrid, s);
+    if (e != cudaSuccess) return set_error(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    return VF_OK;
+  }
   const int ty = 4;
   L.tiles_x = (width + kTX - 1) / kTX;
   const long long grid = (long long)L.tiles_x * ((height + ty - 1) / ty);
   if (grid > 0x7fffffffLL) return set_error(ctx, VF_ERR_UNSUPPORTED, "image too large");
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   switch (cls.w) {
     case 3: e = launch_gated_w3(L, d_flags, (long long)flag_pitch, cls.crit, cls.apx, cls.deg, ty, (int)grid, s); break;

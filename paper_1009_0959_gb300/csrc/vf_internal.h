@@ -39,6 +39,10 @@ struct Launch {
   Coeffs c;
   unsigned long long* stats;  // optional device counters
   int pdl;                    // launch as a programmatic dependent (host side)
+  // gated form in the pair-reuse kernels: non-null = filter only the pixels
+  // whose flag byte is non-zero, copy the others (null for every other call)
+  const uint8_t* flags;
+  long long flag_pitch;
 };
 
 // Register aggregates (fully unrolled pair loop) or shared-memory aggregate
@@ -152,6 +156,10 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
 
 // Whether the gate inference runs on the tensor cores (context option).
 bool gate_tensor_cores(const vf_ctx* ctx);
+
+// Whether an FP32 call of window w and criterion crit runs the pair-reuse
+// kernels under the context's VF_OPT_PAIR_REUSE setting.
+bool use_pair_reuse(const vf_ctx* ctx, int w, int crit);
 
 // Record an error text in the context and return s.
 vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg);

@@ -73,6 +73,8 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
   const int gx = x0 + ox, gy = y0 + oy;
   const bool mine = (int)threadIdx.x < G::OUT;
   const bool valid = mine && gx < L.width && gy < L.height;
+  // gated form: only flagged outputs are filtered, the others keep the centre
+  const bool on = valid && (L.flags == nullptr || L.flags[(long long)gy * L.flag_pitch + gx] != 0);
   const float* sagg = A + threadIdx.x;
   int ties = 0, switched = 0;
   if (!mine) {
@@ -107,7 +109,8 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
       }
       v = pack_rgb(round_u8(yx), round_u8(yy), round_u8(yz), rawc);
     }
-    if (valid) store_px(L, gx, gy, v);
+    if (valid) store_px(L, gx, gy, on ? v : rawc);
+    ties = on ? ties : 0;
   } else if constexpr (CRIT == kEVMF || CRIT == kEVBDF) {
     // the EVMF (Eq. equ_evf) and the generalised EVF: the entropy switch on
     // this output's window (the staged region is laid out as a per-window
@@ -134,10 +137,39 @@ __device__ __forceinline__ void reuse_finish(const Launch& L, const float4* px,
   } else {
     const Selection s =
         select_min<W, false>(nullptr, sagg, G::OUT, px, RX, ox, oy, L.stats != nullptr);
-    if (valid) store_px(L, gx, gy, raw[(oy + s.best / W) * RX + ox + s.best % W]);
-    ties = s.near_tie;
+    const int pick = on ? s.best : N / 2;
+    if (valid) store_px(L, gx, gy, raw[(oy + pick / W) * RX + ox + pick % W]);
+    ties = on && s.near_tie;
   }
+  // gated form: the third counter counts the filtered pixels
+  if (L.flags != nullptr) switched = on;
   block_stats(L, valid ? 1 : 0, valid ? ties : 0, switched);
+}
+
+// Gated form: a tile none of whose outputs is flagged is copied without
+// staging or pair terms.  Called by every thread (the test is a barrier);
+// true when the tile was copied.
+template <int RTY, int NT>
+__device__ __forceinline__ bool reuse_gated_skip(const Launch& L, int tile) {
+  constexpr int OUT = kRTX * RTY;
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  const int x0 = txi * kRTX, y0 = tyi * RTY;
+  int any = 0;
+  for (int o = threadIdx.x; o < OUT; o += NT) {
+    const int gx = x0 + o % kRTX, gy = y0 + o / kRTX;
+    if (gx < L.width && gy < L.height) any |= L.flags[(long long)gy * L.flag_pitch + gx] != 0;
+  }
+  if (__syncthreads_or(any)) return false;
+  int pixels = 0;
+  for (int o = threadIdx.x; o < OUT; o += NT) {
+    const int gx = x0 + o % kRTX, gy = y0 + o / kRTX;
+    if (gx < L.width && gy < L.height) {
+      store_px(L, gx, gy, load_px(L, gx, gy));
+      ++pixels;
+    }
+  }
+  block_stats(L, pixels, 0, 0);
+  return true;
 }
 
 // The w sums of w consecutive values of v[0 .. 2w-2]: out[e] = v[e] + ... +
@@ -529,6 +561,7 @@ __device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile
 // callers looping over tiles must __syncthreads() between calls).
 template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
 __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
+  if (L.flags != nullptr && reuse_gated_skip<RTY, NT>(L, tile)) return;  // uniform test
   if constexpr (W >= 7 && NT >= (kRTX + W - 1) * (RTY + W - 1)) {
     reuse_chunked_reg_tile<W, CRIT, APX, DEG, RTY, NT>(L, tile);
   } else if constexpr (W >= 7) {

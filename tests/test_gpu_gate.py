@@ -136,32 +136,62 @@ def test_training_deterministic_and_resumable(vf, tmp_path):
         gte.close()
 
 
-def test_gated_filter_identities(vf):
-    """All flags set: the plain filter's per-window kernel (the same body and
-    sums, so the same bytes; the pair-reuse kernels sum in another order and
-    may resolve near ties differently); none set: the input."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gated_filter_identities(vf, mode):
+    """Under one VF_OPT_PAIR_REUSE setting (0: per-window kernels, 1: the
+    pair-reuse tiles for BVDF) the gated call runs the same body and sums as
+    the plain call: all flags set gives the plain filter's bytes, none the
+    input, a mix each of them where it belongs; the third counter counts the
+    flagged pixels."""
     clean, noisy = synth.noisy(45, 77, 0.2, 5)
     t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
     kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
-    vf.set_option("pair_reuse", 0)
+    vf.set_option("pair_reuse", mode)
     try:
         plain = vf.filter(t, **kw)
+        ones = torch.ones((45, 77), dtype=torch.uint8, device="cuda")
+        zeros = torch.zeros_like(ones)
+        assert torch.equal(vf.filter_gated(t, ones, **kw), plain)
+        assert torch.equal(vf.filter_gated(t, zeros, **kw), t)
+        half = torch.from_numpy((np.arange(45 * 77).reshape(45, 77) % 3 == 0).astype(np.uint8))
+        half = half.cuda()
+        st = torch.zeros(3, dtype=torch.int64, device="cuda")
+        mixed = vf.filter_gated(t, half, stats=st, **kw)
+        torch.cuda.synchronize()
     finally:
         vf.set_option("pair_reuse", 1)
-    ones = torch.ones((45, 77), dtype=torch.uint8, device="cuda")
-    zeros = torch.zeros_like(ones)
-    assert torch.equal(vf.filter_gated(t, ones, **kw), plain)
-    assert torch.equal(vf.filter_gated(t, zeros, **kw), t)
-    half = torch.from_numpy((np.arange(45 * 77).reshape(45, 77) % 3 == 0).astype(np.uint8)).cuda()
-    st = torch.zeros(3, dtype=torch.int64, device="cuda")
-    mixed = vf.filter_gated(t, half, stats=st, **kw)
-    torch.cuda.synchronize()
     m = half.bool().unsqueeze(-1).expand_as(t)
     assert torch.equal(mixed[m], plain[m]) and torch.equal(mixed[~m], t[~m])
     assert st[2].item() == int(half.sum().item()) and st[0].item() == 45 * 77
     for crit in ("vmf", "amnfe"):
         assert torch.equal(vf.filter_gated(t, ones, criterion=crit, window=3),
                            vf.filter(t, criterion=crit, window=3))
+
+
+@pytest.mark.parametrize("w", [3, 5, 7])
+@pytest.mark.parametrize("approx", ["exact", "poly"])
+def test_gated_reuse_sparse_flags(vf, w, approx):
+    """BVDF gated in the pair-reuse tiles with flags in one corner block and
+    a few scattered pixels (most tiles have none and are copied whole): the
+    flagged pixels carry the plain filter's bytes, the rest the input; with no
+    flag at all every tile is copied; the counters count every pixel once."""
+    h, wd = 130, 150
+    clean, noisy = synth.noisy(h, wd, 0.2, 40 + w)
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    kw = dict(criterion="bvdf", window=w, approx=approx, degree=4)
+    plain = vf.filter(t, **kw)
+    f = np.zeros((h, wd), np.uint8)
+    f[:9, :13] = 1
+    f[100, 140] = f[64, 3] = f[129, 149] = 1
+    flags = torch.from_numpy(f).cuda()
+    st = torch.zeros(3, dtype=torch.int64, device="cuda")
+    out = vf.filter_gated(t, flags, stats=st, **kw)
+    none = vf.filter_gated(t, torch.zeros_like(flags), **kw)
+    torch.cuda.synchronize()
+    m = flags.bool().unsqueeze(-1).expand_as(t)
+    assert torch.equal(out[m], plain[m]) and torch.equal(out[~m], t[~m])
+    assert torch.equal(none, t)
+    assert st.tolist()[0] == h * wd and st.tolist()[2] == int(f.sum())
 
 
 def test_trained_gate_beats_plain_filter(vf):
