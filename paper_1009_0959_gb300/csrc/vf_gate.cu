@@ -343,12 +343,39 @@ __global__ void __launch_bounds__(IX * IY) gate_infer(Images I, const __nv_bfloa
 // ---- fused inference on the tensor cores: each convolution is an implicit
 // GEMM (rows = output cells, K = input channel x 3 x 3 taps, N = 16 output
 // channels) run with warp-level mma.sync m16n8k16, BF16 operands (activations
-// rounded to BF16 between layers), FP32 accumulation.  Same 32 x 8 tile and
-// halos as gate_infer; activations live in shared memory as BF16
-// [cell][channel] so an A fragment is two 32-bit loads per row.
-constexpr int TC_S1 = S1Y * S1X;                 // 432 layer-1 cells = 27 m-tiles
-constexpr int TC_S2 = S2Y * S2X;                 // 340 layer-2 cells
-constexpr int TC_S2_TILES = (TC_S2 + 15) / 16;   // 22 m-tiles
+// rounded to BF16 between layers), FP32 accumulation.  32 x 16 outputs per
+// CTA of 512 threads (halo 3 / 2 / 1 as in gate_infer; the taller tile
+// recomputes fewer halo cells per output: 1.41 layer-1 and 1.20 layer-2 cells
+// instead of 1.69 and 1.33 at 32 x 8); activations live in shared memory as
+// BF16 [cell][channel] so an A fragment is two 32-bit loads per row.
+constexpr int TX = 32, TY = 16;                  // outputs per CTA
+constexpr int T0X = TX + 6, T0Y = TY + 6;        // input region
+constexpr int T1X = TX + 4, T1Y = TY + 4;        // layer-1 cells
+constexpr int T2X = TX + 2, T2Y = TY + 2;        // layer-2 cells
+constexpr int TC_THREADS = TX * TY;
+constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_S1 = T1Y * T1X;                 // 720 layer-1 cells = 45 m-tiles
+constexpr int TC_S2 = T2Y * T2X;                 // 612 layer-2 cells
+constexpr int TC_S2_TILES = (TC_S2 + 15) / 16;   // 39 m-tiles (the last one partial)
+static_assert(TC_S1 % 16 == 0, "whole layer-1 m-tiles");
+// dynamic shared memory: BF16 weights (copied once per CTA with 32-bit loads,
+// so the B fragments are built from shared memory instead of 2-byte global
+// loads), x0, a1, a2, biases; every part 16-byte aligned
+constexpr size_t tc_round16(size_t b) { return (b + 15) / 16 * 16; }
+constexpr size_t TC_OFF_S0 = tc_round16(NPARAM * 2);
+constexpr size_t TC_OFF_S1 = TC_OFF_S0 + tc_round16(3 * T0Y * T0X * 2);
+constexpr size_t TC_OFF_S2 = TC_OFF_S1 + (size_t)TC_S1 * kC * 2;
+constexpr size_t TC_OFF_BIAS = TC_OFF_S2 + (size_t)TC_S2 * kC * 2;
+constexpr size_t TC_SMEM = TC_OFF_BIAS + (2 * kC + 1) * 4;
+static_assert(TC_SMEM <= 100 * 1024, "two CTAs per SM");
+
+// Word of channel pair w (0..7) of activation cell `cell`: the two 4-word
+// halves of a cell swap places when bit 2 of the cell index is set, so the
+// A-fragment loads of 8 consecutive cells x 4 lanes hit 32 distinct banks
+// (unswizzled, cells g and g + 4 share banks).
+__device__ __forceinline__ int act_word(int cell, int w) {
+  return cell * (kC / 2) + (w ^ (cell & 4));
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -370,26 +397,48 @@ __device__ __forceinline__ uint32_t bf16_pair(const __nv_bfloat16* w, int i0, in
   return lo | (hi << 16);
 }
 
-__global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bfloat16* wb,
-                                                         float logit_threshold, uint8_t* flags,
-                                                         long long flag_pitch, float* prob,
-                                                         int tiles_x) {
-  __shared__ __nv_bfloat16 s0[3 * S0Y * S0X];            // x0, [c][row][col]
-  __shared__ __align__(16) uint32_t s1[TC_S1 * kC / 2];  // a1, [cell][16 ch] as bf16 pairs
-  __shared__ __align__(16) uint32_t s2[TC_S2 * kC / 2];  // a2
-  __shared__ float bias[kC * 2 + 1];
-  const int x0 = (blockIdx.x % tiles_x) * IX, y0 = (blockIdx.x / tiles_x) * IY;
+__global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv_bfloat16* wb,
+                                                            float logit_threshold, uint8_t* flags,
+                                                            long long flag_pitch, float* prob,
+                                                            int tiles_x) {
+  extern __shared__ __align__(16) unsigned char tc_smem[];
+  __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(tc_smem);            // weights
+  __nv_bfloat16* s0 = reinterpret_cast<__nv_bfloat16*>(tc_smem + TC_OFF_S0);  // x0, [c][row][col]
+  uint32_t* s1 = reinterpret_cast<uint32_t*>(tc_smem + TC_OFF_S1);  // a1, [cell][16 ch], bf16 pairs
+  uint32_t* s2 = reinterpret_cast<uint32_t*>(tc_smem + TC_OFF_S2);  // a2
+  float* bias = reinterpret_cast<float*>(tc_smem + TC_OFF_BIAS);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(wb);  // cudaMalloc'd: aligned
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sw);
+    for (int k = threadIdx.x; k < NPARAM / 2; k += blockDim.x) dst[k] = src[k];
+    if ((NPARAM & 1) && threadIdx.x == 0) sw[NPARAM - 1] = wb[NPARAM - 1];
+  }
+  const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  for (int k = threadIdx.x; k < 3 * S0Y * S0X; k += blockDim.x) {
-    int c = k / (S0Y * S0X), r = k - c * S0Y * S0X, ry = r / S0X, rx = r - ry * S0X;
-    int gy = y0 - 3 + ry, gx = x0 - 3 + rx;
-    float v = (gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) ? pixel_channel(I, 0, gy, gx, c) : 0.0f;
-    s0[k] = __float2bfloat16_rn(v);
+  // input region: one pixel per item (a 32-bit load where the layout allows),
+  // its three channels scaled as pixel_channel does
+  const bool word = I.channels == 4 && (reinterpret_cast<uintptr_t>(I.img) & 3) == 0 &&
+                    (I.pitch & 3) == 0;
+  for (int k = threadIdx.x; k < T0Y * T0X; k += blockDim.x) {
+    const int ry = k / T0X, rx = k - ry * T0X;
+    const int gy = y0 - 3 + ry, gx = x0 - 3 + rx;
+    float v[3] = {0.0f, 0.0f, 0.0f};
+    if (gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) {
+      const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
+      uint32_t px;
+      if (word) px = *reinterpret_cast<const uint32_t*>(src);
+      else px = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[c] = (float)((px >> (8 * c)) & 255u) * (1.0f / 255.0f) - 0.5f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s0[c * T0Y * T0X + k] = __float2bfloat16_rn(v[c]);
   }
-  if (threadIdx.x < kC) bias[threadIdx.x] = __bfloat162float(wb[OFF_B1 + threadIdx.x]);
-  else if (threadIdx.x < 2 * kC) bias[threadIdx.x] = __bfloat162float(wb[OFF_B2 + threadIdx.x - kC]);
-  else if (threadIdx.x == 2 * kC) bias[threadIdx.x] = __bfloat162float(wb[OFF_B3]);
+  __syncthreads();  // weights staged
+  if (threadIdx.x < kC) bias[threadIdx.x] = __bfloat162float(sw[OFF_B1 + threadIdx.x]);
+  else if (threadIdx.x < 2 * kC) bias[threadIdx.x] = __bfloat162float(sw[OFF_B2 + threadIdx.x - kC]);
+  else if (threadIdx.x == 2 * kC) bias[threadIdx.x] = __bfloat162float(sw[OFF_B3]);
   __syncthreads();
 
   // layer 1: K = 27 taps (c, u, v) padded to 32 = two k-steps
@@ -404,7 +453,7 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
         int k = ks * 16 + 2 * t + (e & 1) + (e >> 1) * 8;
         kin[ks][e] = k < 27;
         int c = k / 9, r = k - c * 9, u = r / 3, v = r - u * 3;
-        off[ks][e] = kin[ks][e] ? (c * S0Y + u) * S0X + v : 0;
+        off[ks][e] = kin[ks][e] ? (c * T0Y + u) * T0X + v : 0;
       }
 #pragma unroll
       for (int nt = 0; nt < 2; ++nt) {
@@ -412,8 +461,8 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
         int k0 = ks * 16 + 2 * t, k8 = k0 + 8;
         auto wv = [&](int k) { return k < 27 ? OFF_W1 + n * 27 + k : -1; };
         auto pair = [&](int ka, int kb) {
-          uint32_t lo = wv(ka) >= 0 ? *reinterpret_cast<const unsigned short*>(wb + wv(ka)) : 0u;
-          uint32_t hi = wv(kb) >= 0 ? *reinterpret_cast<const unsigned short*>(wb + wv(kb)) : 0u;
+          uint32_t lo = wv(ka) >= 0 ? *reinterpret_cast<const unsigned short*>(sw + wv(ka)) : 0u;
+          uint32_t hi = wv(kb) >= 0 ? *reinterpret_cast<const unsigned short*>(sw + wv(kb)) : 0u;
           return lo | (hi << 16);
         };
         b[ks][nt][0] = pair(k0, k0 + 1);
@@ -421,10 +470,10 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
       }
     }
     const unsigned short* s0u = reinterpret_cast<const unsigned short*>(s0);
-    for (int mt = warp; mt < TC_S1 / 16; mt += IX * IY / 32) {
+    for (int mt = warp; mt < TC_S1 / 16; mt += TC_WARPS) {
       float d[2][4] = {};
       const int m0 = mt * 16 + g, m1 = m0 + 8;
-      const int base0 = (m0 / S1X) * S0X + m0 % S1X, base1 = (m1 / S1X) * S0X + m1 % S1X;
+      const int base0 = (m0 / T1X) * T0X + m0 % T1X, base1 = (m1 / T1X) * T0X + m1 % T1X;
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
         uint32_t a[4];
@@ -439,7 +488,7 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int m = half ? m1 : m0;
-        const int ry = m / S1X, rx = m - ry * S1X;
+        const int ry = m / T1X, rx = m - ry * T1X;
         const int gy = y0 - 2 + ry, gx = x0 - 2 + rx;
         const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
 #pragma unroll
@@ -447,7 +496,7 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
           const int n = nt * 8 + 2 * t;
           float v0 = in ? fmaxf(d[nt][half * 2] + bias[n], 0.0f) : 0.0f;
           float v1 = in ? fmaxf(d[nt][half * 2 + 1] + bias[n + 1], 0.0f) : 0.0f;
-          s1[(m * kC + n) >> 1] = pack_bf16(v0, v1);
+          s1[act_word(m, n >> 1)] = pack_bf16(v0, v1);
         }
       }
     }
@@ -463,20 +512,20 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
       for (int nt = 0; nt < 2; ++nt) {
         const int n = nt * 8 + g;  // W2[n][c][u][v], k-step ks = u * 3 + v, c = K column
         const int base = OFF_W2 + n * 144 + ks;
-        b[ks][nt][0] = bf16_pair(wb, base + (2 * t) * 9, base + (2 * t + 1) * 9);
-        b[ks][nt][1] = bf16_pair(wb, base + (2 * t + 8) * 9, base + (2 * t + 9) * 9);
+        b[ks][nt][0] = bf16_pair(sw, base + (2 * t) * 9, base + (2 * t + 1) * 9);
+        b[ks][nt][1] = bf16_pair(sw, base + (2 * t + 8) * 9, base + (2 * t + 9) * 9);
       }
-    for (int mt = warp; mt < TC_S2_TILES; mt += IX * IY / 32) {
+    for (int mt = warp; mt < TC_S2_TILES; mt += TC_WARPS) {
       float d[2][4] = {};
       const int m0 = mt * 16 + g, m1 = m0 + 8;
       const int c0 = min(m0, TC_S2 - 1), c1 = min(m1, TC_S2 - 1);
-      const int base0 = (c0 / S2X) * S1X + c0 % S2X, base1 = (c1 / S2X) * S1X + c1 % S2X;
+      const int base0 = (c0 / T2X) * T1X + c0 % T2X, base1 = (c1 / T2X) * T1X + c1 % T2X;
 #pragma unroll
       for (int ks = 0; ks < 9; ++ks) {
-        const int o = (ks / 3) * S1X + ks % 3;
-        const uint32_t* r0 = s1 + (((base0 + o) * kC) >> 1);
-        const uint32_t* r1 = s1 + (((base1 + o) * kC) >> 1);
-        uint32_t a[4] = {r0[t], r1[t], r0[t + 4], r1[t + 4]};
+        const int o = (ks / 3) * T1X + ks % 3;
+        const int ca = base0 + o, cb = base1 + o;
+        uint32_t a[4] = {s1[act_word(ca, t)], s1[act_word(cb, t)], s1[act_word(ca, t + 4)],
+                         s1[act_word(cb, t + 4)]};
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) mma_bf16(d[nt], a, b[ks][nt][0], b[ks][nt][1]);
       }
@@ -484,7 +533,7 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
       for (int half = 0; half < 2; ++half) {
         const int m = half ? m1 : m0;
         if (m >= TC_S2) continue;
-        const int ry = m / S2X, rx = m - ry * S2X;
+        const int ry = m / T2X, rx = m - ry * T2X;
         const int gy = y0 - 1 + ry, gx = x0 - 1 + rx;
         const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
 #pragma unroll
@@ -492,7 +541,7 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
           const int n = nt * 8 + 2 * t;
           float v0 = in ? fmaxf(d[nt][half * 2] + bias[kC + n], 0.0f) : 0.0f;
           float v1 = in ? fmaxf(d[nt][half * 2 + 1] + bias[kC + n + 1], 0.0f) : 0.0f;
-          s2[(m * kC + n) >> 1] = pack_bf16(v0, v1);
+          s2[act_word(m, n >> 1)] = pack_bf16(v0, v1);
         }
       }
     }
@@ -505,26 +554,26 @@ __global__ void __launch_bounds__(IX * IY) gate_infer_tc(Images I, const __nv_bf
 #pragma unroll
     for (int ks = 0; ks < 9; ++ks) {
       const int base = OFF_W3 + ks;  // W3[0][c][u][v]
-      b[ks][0] = g == 0 ? bf16_pair(wb, base + (2 * t) * 9, base + (2 * t + 1) * 9) : 0u;
-      b[ks][1] = g == 0 ? bf16_pair(wb, base + (2 * t + 8) * 9, base + (2 * t + 9) * 9) : 0u;
+      b[ks][0] = g == 0 ? bf16_pair(sw, base + (2 * t) * 9, base + (2 * t + 1) * 9) : 0u;
+      b[ks][1] = g == 0 ? bf16_pair(sw, base + (2 * t + 8) * 9, base + (2 * t + 9) * 9) : 0u;
     }
-    for (int mt = warp; mt < IX * IY / 16; mt += IX * IY / 32) {
+    for (int mt = warp; mt < TC_THREADS / 16; mt += TC_WARPS) {
       float d[4] = {};
-      const int m0 = mt * 16 + g, m1 = m0 + 8;  // output pixel (m / IX, m % IX)
-      const int base0 = (m0 / IX) * S2X + m0 % IX, base1 = (m1 / IX) * S2X + m1 % IX;
+      const int m0 = mt * 16 + g, m1 = m0 + 8;  // output pixel (m / TX, m % TX)
+      const int base0 = (m0 / TX) * T2X + m0 % TX, base1 = (m1 / TX) * T2X + m1 % TX;
 #pragma unroll
       for (int ks = 0; ks < 9; ++ks) {
-        const int o = (ks / 3) * S2X + ks % 3;
-        const uint32_t* r0 = s2 + (((base0 + o) * kC) >> 1);
-        const uint32_t* r1 = s2 + (((base1 + o) * kC) >> 1);
-        uint32_t a[4] = {r0[t], r1[t], r0[t + 4], r1[t + 4]};
+        const int o = (ks / 3) * T2X + ks % 3;
+        const int ca = base0 + o, cb = base1 + o;
+        uint32_t a[4] = {s2[act_word(ca, t)], s2[act_word(cb, t)], s2[act_word(ca, t + 4)],
+                         s2[act_word(cb, t + 4)]};
         mma_bf16(d, a, b[ks][0], b[ks][1]);
       }
       if (t == 0) {  // column n = 0 of D: d[0] (row g) and d[2] (row g + 8)
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
           const int m = half ? m1 : m0;
-          const int gx = x0 + m % IX, gy = y0 + m / IX;
+          const int gx = x0 + m % TX, gy = y0 + m / TX;
           const float z = d[half * 2] + bias[2 * kC];
           if (gx < I.W && gy < I.H) {
             if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
@@ -768,14 +817,19 @@ vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, 
   Images I;
   vf_status st = check_images(g, d_in, 1, height, width, channels, pitch, &I);
   if (st != VF_OK) return st;
-  const int tiles_x = (width + IX - 1) / IX, tiles_y = (height + IY - 1) / IY;
   const float thr = std::log(threshold / (1.0f - threshold));
   cudaError_t e = cudaSuccess;
   if (gate_tensor_cores(g->ctx)) {
-    gate_infer_tc<<<tiles_x * tiles_y, IX * IY, 0, (cudaStream_t)stream>>>(
-        I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x);
-    e = cudaGetLastError();
+    const int tiles_x = (width + TX - 1) / TX, tiles_y = (height + TY - 1) / TY;
+    e = cudaFuncSetAttribute(gate_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TC_SMEM);
+    if (e == cudaSuccess) {
+      gate_infer_tc<<<tiles_x * tiles_y, TC_THREADS, TC_SMEM, (cudaStream_t)stream>>>(
+          I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x);
+      e = cudaGetLastError();
+    }
   } else {
+    const int tiles_x = (width + IX - 1) / IX, tiles_y = (height + IY - 1) / IY;
     static_assert(kInferSmem <= 200 * 1024, "inference tile fits in shared memory");
     e = cudaFuncSetAttribute(gate_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kInferSmem);
