@@ -172,6 +172,13 @@ __device__ __forceinline__ bool reuse_gated_skip(const Launch& L, int tile) {
   return true;
 }
 
+// The same, not inlined: for the 7 x 7 tiles, whose 49 register window sums
+// leave no room for the test's values (inlined, it made the main loop spill).
+template <int RTY, int NT>
+__device__ __noinline__ bool reuse_gated_skip_call(const Launch& L, int tile) {
+  return reuse_gated_skip<RTY, NT>(L, tile);
+}
+
 // The w sums of w consecutive values of v[0 .. 2w-2]: out[e] = v[e] + ... +
 // v[e + w - 1].  Neighbouring sums share their overlap (w = 5: 12 additions
 // instead of 20); additions only.
@@ -561,7 +568,13 @@ __device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile
 // callers looping over tiles must __syncthreads() between calls).
 template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
 __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
-  if (L.flags != nullptr && reuse_gated_skip<RTY, NT>(L, tile)) return;  // uniform test
+  if (L.flags != nullptr) {  // uniform test
+    if constexpr (W >= 7) {
+      if (reuse_gated_skip_call<RTY, NT>(L, tile)) return;
+    } else {
+      if (reuse_gated_skip<RTY, NT>(L, tile)) return;
+    }
+  }
   if constexpr (W >= 7 && NT >= (kRTX + W - 1) * (RTY + W - 1)) {
     reuse_chunked_reg_tile<W, CRIT, APX, DEG, RTY, NT>(L, tile);
   } else if constexpr (W >= 7) {
