@@ -61,6 +61,18 @@ def test_argument_errors_without_gpu(vf):
                          approx="rational", exp_cutoff=2.0) == 3
 
 
+def test_image_too_large_rejected_without_gpu(vf):
+    """Images whose tile grid would pass 2^31 - 1 CTAs are refused on the host
+    (VF_ERR_UNSUPPORTED) before any CUDA call: the per-window path (VMF,
+    2^20 x 2^20) and the pair-reuse path (BVDF 5 x 5, 2^21 x 2^20).  The
+    pointers are never dereferenced; they only have to be distinct ranges."""
+    w = 1 << 20
+    a, b = 1 << 40, 1 << 46
+    assert vf.filter_ptr(a, b, 1 << 20, w, 4, 4 * w, 4 * w, criterion="vmf") == 3
+    assert vf.filter_ptr(a, b, 1 << 21, w, 4, 4 * w, 4 * w, criterion="bvdf", window=5,
+                         approx="poly", degree=4) == 3
+
+
 def test_library_remez_matches_paper_table1(vf, golden):
     """The library's own fit (independent of the oracle's) reproduces the
     paper's Table 1 and Table 2 to the printed precision."""

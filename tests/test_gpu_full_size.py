@@ -133,3 +133,35 @@ def test_gated_frame_3840x2160(vf):
         sl = slice(r0, r1)
         diff = np.any(o[sl, :, :3] != g[sl, :, :3], axis=-1)
         assert (diff & mask[sl] & (d["gap"][sl] > 1e-5)).sum() == 0
+
+
+@pytest.mark.parametrize("crit,w,approx", [("vmf", 5, "exact"), ("bvdf", 5, "poly"),
+                                           ("evmf", 5, "poly"), ("amnfe", 7, "rational")])
+def test_image_over_4gib(vf, crit, w, approx):
+    """A 40000 x 32768 RGBX image (5.2 GB in, 5.2 GB out: byte offsets past
+    2^32) made on the device by tiling a 512 x 512 synthetic tile; the rows
+    at the top and bottom borders and the rows around the 4 GiB offset meet
+    the oracle's bar (the oracle sees those rows with their vertical halo and
+    the full width)."""
+    H, W = 40000, 32768
+    free, _ = torch.cuda.mem_get_info()
+    if free < 16 * 2 ** 30:
+        pytest.skip("needs 16 GB of free device memory")
+    tile = synth.to_rgbx(synth.noisy(512, 512, 0.15, 3)[1])
+    big = torch.from_numpy(tile).cuda().repeat((H + 511) // 512, W // 512, 1)[:H].contiguous()
+    out = vf.filter(big, criterion=crit, window=w, approx=approx, degree=4)
+    torch.cuda.synchronize()
+    del big
+    R = w // 2
+    row4g = (2 ** 32) // (W * 4)  # first row past the 4 GiB offset
+    cols = np.arange(W) % 512
+    for r0, r1 in [(0, 2), (row4g - 1, row4g + 2), (H - 2, H)]:
+        lo, hi = max(r0 - R, 0), min(r1 + R, H)
+        sub = tile[np.arange(lo, hi) % 512][:, cols]
+        o, d = F.filter_image(sub, F.Config(crit, w, approx, 4), threads=8,
+                              rows=(r0 - lo, r1 - lo))
+        sl = slice(r0 - lo, r1 - lo)
+        g = out[r0:r1].cpu().numpy()
+        check(crit, o[sl], {k: v[sl] for k, v in d.items()}, g)
+    del out
+    torch.cuda.empty_cache()
