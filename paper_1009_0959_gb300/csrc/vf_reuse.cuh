@@ -3,8 +3,9 @@
 //
 // A pair of pixels (p, q) with |p - q| <= w - 1 (per axis) belongs to every
 // window that contains both, up to w^2 of them; the per-window kernel
-// computes it in each.  Here a CTA of 32 x 8 outputs stages its
-// (32 + w - 1) x (8 + w - 1) region once, then
+// computes it in each.  Here a CTA of 32 x RTY outputs (RTY = 8, or taller
+// tiles with one thread per region pixel) stages its
+// (32 + w - 1) x (RTY + w - 1) region once, then
 //   1. term table: for every region pixel p and each of the 2w(w-1) offsets
 //      delta of the forward half-plane (dy > 0, or dy = 0 and dx > 0) with
 //      p + delta in the region, T[delta][p] = term(x_p, x_{p+delta});
@@ -12,8 +13,10 @@
 //      agg(c, p) = sum_{q in W(c)} term(p, q) as separable box sums of its
 //      distance field D_p(delta) (T[delta][p] or T[-delta][p + delta], 0 at
 //      delta = 0) over the (2w-1)^2 offsets: row sums of width w, then column
-//      sums of height w.  Only additions (no differences of prefix sums, so no
-//      cancellation);
+//      sums of height w.  Only additions at w = 3 and 5 (no differences of
+//      prefix sums, so no cancellation); the 7 x 7 register form slides its
+//      width-7 row sums (one addition and one subtraction of non-negative
+//      terms per step);
 //   3. every output thread reads the n aggregates of its window and selects
 //      (argmin, lowest index) or weights (AMNF), as the per-window kernel.
 // Work per output pixel: 2w(w-1) terms x (region / tile) instead of
