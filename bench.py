@@ -127,6 +127,31 @@ MEASURED_DRAM_BYTES_PER_PIXEL = {
     ("amnfg", "rational", 0, 5): 7.05, ("vmf", "exact", 0, 5): 7.05}
 
 
+# ---------------------------------------------------------------- ranks (replicas)
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of one benchmark image on a rank: every rank filters its own images
+    (replicas, no data shared between ranks)."""
+    return seed + 100 * rank
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest value over the ranks (the job ends with its slowest rank);
+    the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pixels_per_rank_step: float, steps: int, world: int, ms: float) -> float:
+    """Whole-job Mpixels/s: the pixels every rank filtered over `steps` steps,
+    divided by the (max-over-ranks) time in ms."""
+    return pixels_per_rank_step * steps * world / (ms / 1e3) / 1e6
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,7 +199,7 @@ def main():
     # inputs: resident in HBM before timing; rotating pool larger than L2
     imgs = []
     for p, seed in NOISE:
-        clean, noisy = synth.noisy(H, W, p, seed + 100 * rank)
+        clean, noisy = synth.noisy(H, W, p, rank_seed(seed, rank))
         imgs.append((clean, noisy))
     dev_imgs = [torch.from_numpy(synth.to_rgbx(n)).cuda() for _, n in imgs]
     pool_in = [dev_imgs[k % 3].clone() for k in range(POOL)]
@@ -262,11 +287,8 @@ def main():
         host_ms = (time.perf_counter() - h0) * 1e3
         t1.record(stream)
         torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1)
+        ms = max_over_ranks(t0.elapsed_time(t1), dist, "cuda")
         if dist:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
             dist.barrier()
         return ms, host_ms
 
@@ -311,8 +333,8 @@ def main():
 
     pix_per_step = len(launches) * H * W
     ms_total = ms_graph
-    value = pix_per_step * args.steps * world / (ms_total / 1e3) / 1e6
-    value_eager = pix_per_step * args.steps * world / (ms_eager / 1e3) / 1e6
+    value = job_throughput(pix_per_step, args.steps, world, ms_total)
+    value_eager = job_throughput(pix_per_step, args.steps, world, ms_eager)
 
     # per filter / window: exact vs fastest minimax meeting the 0.05 dB bar
     pfw = {}
@@ -419,7 +441,7 @@ def main():
     for (c, a, d, w, k) in launches:
         vfilt.filter_host(hin[k], hout[0], criterion=c, window=w, approx=a, degree=max(d, 2))
     torch.cuda.synchronize()
-    e2e_sync_s = time.perf_counter() - te
+    e2e_sync_s = max_over_ranks(time.perf_counter() - te, dist, "cuda")
     # pipelined: the copies of one image overlap the filtering of the others
     for (c, a, d, w, k) in launches[:6]:
         vfilt.filter_host_async(hin[k], hout[0], criterion=c, window=w, approx=a,
@@ -433,13 +455,15 @@ def main():
                                     degree=max(d, 2))
         vfilt.host_sync()
         e2e.append(time.perf_counter() - te)
-    e2e_s = statistics.median(e2e)
-    line["e2e"] = {"value": round(pix_per_step * world / e2e_s / 1e6, 1), "unit": "Mpixels/s",
+    e2e_s = max_over_ranks(statistics.median(e2e), dist, "cuda")
+    line["e2e"] = {"value": round(job_throughput(pix_per_step, 1, world, e2e_s * 1e3), 1),
+                   "unit": "Mpixels/s",
                    "h2d_bytes_per_step": len(launches) * H * W * 4,
                    "d2h_bytes_per_step": len(launches) * H * W * 4,
                    "call": "vf_filter_host_async per launch + vf_host_sync (pinned host "
                            "buffers, one step; median of 3 steps)",
-                   "sync_call_value": round(pix_per_step * world / e2e_sync_s / 1e6, 1),
+                   "sync_call_value": round(job_throughput(pix_per_step, 1, world,
+                                                           e2e_sync_s * 1e3), 1),
                    "sync_call": "vf_filter_host per launch (waits after each image)"}
 
     if not args.no_batch:

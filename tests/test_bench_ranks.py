@@ -1,0 +1,64 @@
+"""Host logic of the benchmark's multi-GPU form (replicas: every rank filters
+its own images, no data-path collective) on CPU with two gloo ranks: the
+timing reduction takes the slowest rank, the whole-job throughput counts the
+pixels of every rank, each rank's images come from their own seeds, and the
+reference arm runs on rank 0 only."""
+import contextlib
+import io
+import os
+import socket
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        slowest = bench.max_over_ranks(10.0 + 3.5 * rank, dist, "cpu")
+        seeds = [bench.rank_seed(s, rank) for s, _ in [(2, 0), (3, 0), (4, 0)]]
+        gathered = [None] * world
+        dist.all_gather_object(gathered, seeds)
+        q.put((rank, slowest, gathered))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    torch.multiprocessing.spawn(_worker, args=(2, _free_port(), q), nprocs=2, join=True)
+    results = sorted(q.get(timeout=60) for _ in range(2))
+    assert [r for r, _, _ in results] == [0, 1]
+    for _, slowest, gathered in results:
+        assert slowest == 13.5  # every rank reports the slowest rank's time
+        flat = [s for seeds in gathered for s in seeds]
+        assert len(set(flat)) == len(flat)  # no image is filtered by two ranks
+
+
+def test_single_process_helpers():
+    assert bench.max_over_ranks(7.25) == 7.25
+    assert bench.rank_seed(2, 0) == 2
+    # 176 Mpix per rank and step, 5 steps, 2 ranks, 2 s: 880 Mpix/s for the job
+    assert bench.job_throughput(176e6, 5, 2, 2000.0) == pytest.approx(880.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    args = types.SimpleNamespace(steps=1, warmup=0)
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        assert bench.reference_arm(args, 1, 2) == 0
+    assert out.getvalue() == ""
