@@ -3,7 +3,8 @@ the launch configuration the benchmark times, on sampled rows the FP64 oracle
 computes one by one (top and bottom borders, the middle):
 
 * one 4096 x 4096 image at 20 % impulses (seed 8), 5 x 5 and 7 x 7 windows:
-  FP32 criteria with the single-image bar, FP16x2 with its selection band;
+  FP32 criteria (with the library's own rationals) with the single-image
+  bar, FP16x2 and BF16x2 with their selection bands;
 * the 256-image batch (320x240 .. 1920x1080, seed 9, windows 3/5/7 and the
   five criteria round-robin), autotuned and replayed as a CUDA graph: a
   sample of images, three row bands each;
@@ -60,7 +61,8 @@ def big(vf):
 @pytest.mark.parametrize("crit,approx,deg", [("vmf", "exact", 4), ("bvdf", "exact", 4),
                                              ("bvdf", "poly", 4), ("amnfe", "rational", 4),
                                              ("amnfg", "poly", 4), ("evmf", "poly", 4),
-                                             ("evbdf", "poly", 4)])
+                                             ("evbdf", "poly", 4), ("amnfe", "rational_fit", 3),
+                                             ("evmf", "rational_fit", 4)])
 def test_4096_fp32_sampled(vf, big, crit, approx, deg, w):
     noisy, t = big
     out = vf.filter(t, criterion=crit, window=w, approx=approx, degree=deg)
@@ -68,17 +70,18 @@ def test_4096_fp32_sampled(vf, big, crit, approx, deg, w):
     check_rows(crit, noisy, F.Config(crit, w, approx, deg), out.cpu().numpy(), bands(4096))
 
 
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x2"])
 @pytest.mark.parametrize("w", [5, 7])
 @pytest.mark.parametrize("crit,approx", [("vmf", "exact"), ("bvdf", "poly"), ("evmf", "poly")])
-def test_4096_fp16x2_sampled(vf, big, crit, approx, w):
+def test_4096_packed_sampled(vf, big, crit, approx, w, prec):
     noisy, t = big
     out = vf.filter(t, criterion=crit, window=w, approx=approx, degree=4,
-                    precision="fp16x2").cpu().numpy()
+                    precision=prec).cpu().numpy()
     for r0, r1 in bands(4096):
         o, d = F.filter_image(noisy, F.Config(crit, w, approx, 4), rows=(r0, r1))
         sl = slice(r0, r1)
         diff = np.any(o[sl, :, :3] != out[sl, :, :3], axis=-1)
-        assert (diff & (d["gap"][sl] > BAND["fp16x2"])).sum() == 0
+        assert (diff & (d["gap"][sl] > BAND[prec])).sum() == 0
 
 
 BATCH_CRITS = ["vmf", "bvdf", "amnfe", "amnfg", "evmf"]
