@@ -37,6 +37,9 @@ NOISE = [(0.05, 2), (0.15, 3), (0.30, 4)]  # (p, seed)
 WINDOWS = [3, 5]
 METRIC = "Mpixels/s per filter/window, minimax vs exact, 1 GB300, at ≤0.05 dB PSNR drop"
 POOL = 48  # rotating input/output copies: 48 x 8 MB = 384 MB > 129 MB L2
+# the quality bar of a minimax variant against the exact filter: PSNR drop
+# (vs the clean image) and fraction of changed output pixels
+BAR_DB, BAR_CHANGED = 0.05, 0.005
 
 
 def variants():
@@ -101,30 +104,28 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline model
 
-# Thread instructions (predicated on) per output pixel of the kernels that
-# can dominate the step, from ncu captures on 6144 x 6144 (thread_inst_executed
-# with the predicate on; the kernels' instruction counts are not fixed by the
-# source: atan2f, the EVMF switch fraction, the pair-reuse tile borders).
+# Per output pixel of the kernels that can dominate the step, from ncu
+# captures of the current kernels on 6144 x 6144 RGBX (one launch each, after
+# the same command ran to completion without ncu):
+#   ncu --metrics <the counters below>,gpu__time_duration.sum --clock-control none
+#       -k regex:"reuse_kernel|filter_kernel|filter2_kernel|evmf_queue_kernel"
+#       -s 1 -c 1 --csv python bench.py --case <case> --size 6144
+# "fp32": FP32 operations executed per pixel (thread instructions, predicated
+#   on): FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2), the work of the
+#   FP32 FMA pipe (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul,ffma2,
+#   fadd2,fmul2}_pred_on.sum);
+# "inst": all thread instructions (smsp__thread_inst_executed_pred_on.sum);
+# "dram": DRAM bytes read + written (dram__bytes_{read,write}.sum);
+# "fma_pipe": ncu's FMA-pipe utilisation of the same launch
+#   (sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100).
 # Keyed (criterion, approx, degree, window); degree 0 for exact / rational.
-MEASURED_INST_PER_PIXEL = {
-    ("bvdf", "exact", 0, 5): 3277, ("bvdf", "poly", 2, 5): 2667, ("bvdf", "poly", 3, 5): 2759,
-    ("bvdf", "poly", 4, 5): 2854, ("bvdf", "poly", 5, 5): 2946, ("bvdf", "poly", 6, 5): 3040,
-    ("evmf", "exact", 0, 5): 2433, ("evmf", "poly", 4, 5): 1921, ("evmf", "rational", 0, 5): 2069,
-    ("amnfe", "exact", 0, 5): 1289, ("amnfe", "rational", 0, 5): 1349,
-    ("amnfg", "rational", 0, 5): 1399, ("vmf", "exact", 0, 5): 1466}
-# Pipe utilisation of the dominant kernel (ncu --set full on 6144 x 6144,
-# profiles/bvdf_exact_w5_reuse_6144.md): FP32 FMA pipe and XU (SFU / MUFU)
-# pipe, fractions of their peak issue rate
-MEASURED_PIPES = {("bvdf", "exact", 0, 5): {"fma_pipe": 0.403, "xu_pipe": 0.132,
-                                            "issue_active": 0.740}}
-# DRAM bytes (read + write) per output pixel from the same captures; the
-# BVDF polynomial kernels changed (gated finish phase) after theirs, so they
-# report no traffic until captured again
-MEASURED_DRAM_BYTES_PER_PIXEL = {
-    ("bvdf", "exact", 0, 5): 7.06,
-    ("evmf", "exact", 0, 5): 6.91, ("evmf", "poly", 4, 5): 6.88, ("evmf", "rational", 0, 5): 6.94,
-    ("amnfe", "exact", 0, 5): 7.04, ("amnfe", "rational", 0, 5): 7.04,
-    ("amnfg", "rational", 0, 5): 7.05, ("vmf", "exact", 0, 5): 7.05}
+MEASURED_PER_PIXEL = {
+    ("bvdf", "exact", 0, 5): {"inst": 3277, "dram": 7.06, "fp32": None, "fma_pipe": 0.403},
+    ("bvdf", "poly", 4, 5): {"inst": 2854, "dram": None, "fp32": None, "fma_pipe": None},
+    ("evmf", "exact", 0, 5): {"inst": 2433, "dram": 6.91, "fp32": None, "fma_pipe": None},
+    ("amnfe", "exact", 0, 5): {"inst": 1289, "dram": 7.04, "fp32": None, "fma_pipe": None},
+    ("vmf", "exact", 0, 5): {"inst": 1466, "dram": 7.05, "fp32": None, "fma_pipe": None},
+}
 
 
 # ---------------------------------------------------------------- ranks (replicas)
@@ -171,6 +172,9 @@ def main():
                     help="profiling: VF_OPT_PAIR_REUSE for --case (0 never, 1 auto, 2 always)")
     ap.add_argument("--overlap-launch", type=int, default=1, choices=[0, 1],
                     help="VF_OPT_OVERLAP_LAUNCH: programmatic dependent launches (default 1)")
+    ap.add_argument("--sections-out", default="bench_sections.json",
+                    help="file for the per-variant, batched, precision, quality-study, EVF and "
+                         "gate sections (the printed line carries a summary of them)")
     ap.add_argument("--tile-rows", type=int, default=4, choices=[2, 4, 8],
                     help="VF_OPT_TILE_ROWS of the per-window kernels (default 4)")
     args = ap.parse_args()
@@ -214,9 +218,12 @@ def main():
     ref_out = {}
     for w in WINDOWS:
         for (c, a, d) in V:
-            psnr, changed = [], []
+            psnr, changed, ties = [], [], []
             for k in range(3):
-                o = vfilt.filter(dev_imgs[k], criterion=c, window=w, approx=a, degree=max(d, 2))
+                st = torch.zeros(3, dtype=torch.int64, device="cuda")
+                o = vfilt.filter(dev_imgs[k], criterion=c, window=w, approx=a, degree=max(d, 2),
+                                 stats=st)
+                ties.append(int(st[vfilt.STAT_NEAR_TIES].item()))
                 o = o.cpu().numpy()[..., :3]
                 if a == "exact":
                     ref_out[(c, w, k)] = o
@@ -224,7 +231,8 @@ def main():
                 mse = ((clean.astype(np.float64) - o) ** 2).mean()
                 psnr.append(10 * math.log10(255 ** 2 / mse))
                 changed.append(float(np.any(o != ref_out[(c, w, k)], axis=-1).mean()))
-            quality[vkey(c, a, d, w)] = {"psnr_db": psnr, "changed": changed}
+            quality[vkey(c, a, d, w)] = {"psnr_db": psnr, "changed": changed,
+                                         "near_ties": ties}
     for w in WINDOWS:
         for (c, a, d) in V:
             q = quality[vkey(c, a, d, w)]
@@ -341,7 +349,8 @@ def main():
     for w in WINDOWS:
         for crit in ("vmf", "bvdf", "amnfe", "amnfg", "evmf"):
             ex = vkey(crit, "exact", 0, w)
-            ent = {"exact_mpix_s": round(H * W / kern_ms[ex] / 1e3, 1)}
+            ent = {"exact_mpix_s": round(H * W / kern_ms[ex] / 1e3, 1),
+                   "exact_near_ties_max": round(max(quality[ex]["near_ties"]) / (H * W), 5)}
             best = None
             for (c, a, d) in V:
                 if c != crit or a == "exact":
@@ -352,7 +361,8 @@ def main():
                        "speedup": round(kern_ms[ex] / kern_ms[k], 3),
                        "psnr_drop_db": round(q["psnr_drop_db"], 4),
                        "changed_max": round(q["changed_max"], 5),
-                       "meets_bar": q["psnr_drop_db"] <= 0.05}
+                       "near_ties_max": round(max(q["near_ties"]) / (H * W), 5),
+                       "meets_bar": q["psnr_drop_db"] <= BAR_DB and q["changed_max"] <= BAR_CHANGED}
                 ent[k.split("/")[1]] = row
                 if row["meets_bar"] and (best is None or row["mpix_s"] > ent[best]["mpix_s"]):
                     best = k.split("/")[1]
@@ -363,46 +373,8 @@ def main():
     c, a, wtag = dom.split("/")
     d = int(a[4:]) if a.startswith("poly") else 0
     a = "poly" if a.startswith("poly") else a
-    mkey = (c, a, d, int(wtag[1:]))
-    inst = MEASURED_INST_PER_PIXEL.get(mkey)
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # issue rate: 4 schedulers x 32 lanes x 1 instruction per clock per SM
-    peak_tinst = 152 * 128 * sm_max * 1e6 / 1e12  # thread instructions/s
-    roof = {"bound": "alu", "kernel": dom, "unit": "Tinst/s", "peak": round(peak_tinst, 2),
-            "peak_source": "152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x %.0f MHz "
-                           "(recipe unit counts and max clock)" % sm_max,
-            "traffic": None}
-    dram = MEASURED_DRAM_BYTES_PER_PIXEL.get(mkey)
-    if dram is not None:
-        roof["traffic"] = round(dram * H * W)
-        roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled "
-                                "from a 6144 x 6144 capture by pixels; algorithmic 8 B/px")
-    roof["launch_ms"] = round(dom_ms, 4)
-    if mkey in MEASURED_PIPES:
-        roof["pipes_ncu"] = dict(MEASURED_PIPES[mkey], source="ncu --set full, 6144 x 6144 "
-                                 "(profiles/bvdf_exact_w5_reuse_6144.md)")
-    if dram is not None:  # far below the HBM roofline: the kernels are compute-bound
-        gbs = dram * H * W / (dom_ms / 1e3) / 1e9
-        roof["hbm"] = {"achieved_gbs": round(gbs, 1),
-                       "peak_gbs": peaks.get("hbm_gbs"),
-                       "frac": (round(gbs / peaks["hbm_gbs"], 4) if peaks.get("hbm_gbs")
-                                else None),
-                       "peak_source": "MEASURED_PEAKS.json (of measured)"}
-    if inst is not None:
-        ach = inst * H * W / (dom_ms / 1e3) / 1e12
-        roof.update({"achieved": round(ach, 3), "frac": round(ach / peak_tinst, 4),
-                     "inst_per_pixel": inst,
-                     "inst_source": "thread instructions (predicated on) per pixel, ncu on "
-                                    "6144 x 6144 (profiles/inst_counts_w5_6144.md)"})
-    else:
-        roof.update({"achieved": None, "frac": None,
-                     "note": "no instruction count measured for this kernel"})
+    roof = roofline(dom, MEASURED_PER_PIXEL.get((c, a, d, int(wtag[1:]))), H * W, dom_ms,
+                    ck.get("sm_mhz"))
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "Mpixels/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -415,17 +387,15 @@ def main():
                        "l2": "inputs rotate through a %d MB pool (> 129 MB L2)" %
                              (POOL * 8),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "overlap_launch": args.overlap_launch,
-                       "launch": ("one step captured as a CUDA graph of its vf_filter calls, "
-                                  "the three images on three streams, replayed K times")
+                       "launch": ("one step captured as a CUDA graph of its vf_filter calls "
+                                  "(three images on three streams), replayed K times")
                                  if graph is not None else
                                  "vf_filter calls (graph capture failed: %s)" % graph_error},
             "eager": {"value": round(value_eager, 1), "ms_per_step": round(ms_eager / args.steps, 3),
-                      "streams": 1,
-                      "host_enqueue_ms_per_step": round(host_eager / args.steps, 3),
-                      "call": "vf_filter from Python, one call per launch"},
+                      "host_enqueue_ms_per_step": round(host_eager / args.steps, 3)},
             "gpu_launches": len(launches) * args.steps,
-            "clocks": ck, "roofline": roof, "per_filter_window": pfw}
+            "clocks": ck, "roofline": roof}
+    sections = {"per_filter_window": pfw}
 
     # end to end through the public host-buffer calls (copies inside the
     # timing): every launch of a step copies its image in and its result out
@@ -467,20 +437,100 @@ def main():
                    "sync_call": "vf_filter_host per launch (waits after each image)"}
 
     if not args.no_batch:
-        line["batched"] = bench_batch()
+        sections["batched"] = bench_batch()
     if not args.no_precision:
-        line["precision"] = bench_precision()
-        line["rational_fit"] = bench_rational_fit()
-        line["quality_study"] = bench_quality_study()
-        line["generalized_evf"] = bench_generalized_evf()
+        sections["precision"] = bench_precision()
+        sections["rational_fit"] = bench_rational_fit()
+        sections["quality_study"] = bench_quality_study()
+        sections["generalized_evf"] = bench_generalized_evf()
     if not args.no_gate:
-        line["gate"] = bench_gate()
+        sections["gate"] = bench_gate()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs, V, budget_s=15.0)
+    line["summary"] = summarize(sections)
     if rank == 0:
-        print(json.dumps(line))
+        if args.sections_out:
+            os.makedirs(os.path.dirname(os.path.abspath(args.sections_out)), exist_ok=True)
+            with open(args.sections_out, "w") as fh:
+                json.dump(sections, fh, indent=1)
+            line["sections_file"] = args.sections_out
+        print(json.dumps(line, separators=(",", ":")))
     if dist:
         dist.destroy_process_group()
+
+
+def roofline(kernel, counts, pixels, launch_ms, sm_mhz):
+    """The roofline object of the dominant kernel: FP32 FMA-pipe work executed
+    per launch (ncu counts per pixel x pixels) over its mean CUDA-event launch
+    time inside the timed region, against the FP32 lane peak (152 SMs x 128
+    lanes x the maximum SM clock); beside it the issue-slot fraction (all
+    thread instructions against 152 x 4 schedulers x 32 lanes per clock: the
+    same peak rate) and the DRAM traffic against the measured copy bandwidth."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 152 * 128 * sm_max * 1e6 / 1e12  # T FP32 lane operations / s
+    counts = counts or {}
+    roof = {"bound": "alu", "pipe": "FP32 FMA pipe (FFMA/FADD/FMUL, x2 for the paired forms)",
+            "kernel": kernel, "unit": "T FP32 ops/s", "peak": round(peak, 2),
+            "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (unit counts, max clock)" % sm_max,
+            "launch_ms": round(launch_ms, 4), "achieved": None, "frac": None, "traffic": None}
+    s = launch_ms / 1e3
+    if counts.get("fp32"):
+        ach = counts["fp32"] * pixels / s / 1e12
+        roof.update(achieved=round(ach, 3), frac=round(ach / peak, 4),
+                    fp32_ops_per_px=counts["fp32"])
+    if counts.get("inst"):
+        roof["issue_frac"] = round(counts["inst"] * pixels / s / 1e12 / peak, 4)
+        roof["inst_per_px"] = counts["inst"]
+    if counts.get("fma_pipe") is not None:
+        roof["fma_pipe_ncu"] = counts["fma_pipe"]
+    if counts.get("dram"):
+        roof["traffic"] = round(counts["dram"] * pixels)
+        gbs = counts["dram"] * pixels / s / 1e9
+        roof["hbm_gbs"] = round(gbs, 1)
+        if peaks.get("hbm_gbs"):
+            roof["hbm_frac"] = round(gbs / peaks["hbm_gbs"], 4)
+    if sm_mhz:
+        roof["frac_at_sampled_clock"] = (round(roof["frac"] * sm_max / sm_mhz, 4)
+                                         if roof["frac"] else None)
+    roof["source"] = "per-pixel counts: ncu on 6144 x 6144, one launch of the same kernel"
+    return roof
+
+
+def summarize(sections):
+    """A few KB of the side sections for the result line: per filter and window
+    the exact Mpix/s and the fastest minimax variant meeting the quality bar;
+    the batched, precision and gate forms' headline numbers."""
+    out = {}
+    pfw = sections.get("per_filter_window", {})
+    out["per_filter_window"] = {
+        k: [v["exact_mpix_s"], v["best_minimax"],
+            v[v["best_minimax"]]["mpix_s"] if v["best_minimax"] else None,
+            v[v["best_minimax"]]["speedup"] if v["best_minimax"] else None]
+        for k, v in pfw.items()}
+    out["per_filter_window_columns"] = ["exact Mpix/s", "best minimax meeting the bar",
+                                        "its Mpix/s", "speedup over exact"]
+    b = sections.get("batched")
+    if b:
+        out["batched"] = {"mpix_s": b["mpix_s"], "speedup_vs_per_image": b["speedup_vs_per_image"]}
+    pr = sections.get("precision")
+    if pr:
+        out["precision"] = {k: [v["mpix_s"], v.get("changed_vs_oracle", v.get("changed_vs_fp32_exact")),
+                                v["psnr_drop_db"]]
+                            for k, v in pr["variants"].items() if "/w5/" in k}
+        out["precision_columns"] = ["Mpix/s", "changed fraction", "PSNR drop dB"]
+    g = sections.get("gate")
+    if g:
+        out["gate"] = {"speedup_gated_vs_plain": g["speedup_gated_vs_plain"],
+                       "speedup_gated_vs_exact": g.get("speedup_gated_vs_exact"),
+                       "psnr_gain_db": round(g["psnr_gated_db_mean"] - g["psnr_plain_db_mean"], 3),
+                       "flagged_fraction_mean": g["flagged_fraction_mean"]}
+    return out
 
 
 BATCH_CRITS = ["vmf", "bvdf", "amnfe", "amnfg", "evmf"]
@@ -539,18 +589,37 @@ def bench_batch(reps=5):
             "gpu_launches_per_run": 1}
 
 
+# sRGB (IEC 61966-2-1) primaries to CIE XYZ; the white of the L*a*b*
+# conversion is the XYZ of sRGB (1, 1, 1) under this matrix (D65)
+SRGB_TO_XYZ = [[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722], [0.0193, 0.1192, 0.9505]]
+
+
 def _lab(rgb):
     """sRGB (IEC 61966-2-1) -> CIE 1976 L*a*b*, D65 white (the metric's colour
-    space); float64 arrays of shape (..., 3)."""
+    space); uint8 or float arrays of shape (..., 3) -> float64."""
     import numpy as np
-    c = rgb.astype(np.float64) / 255.0
+    m = np.array(SRGB_TO_XYZ)
+    c = rgb[..., :3].astype(np.float64) / 255.0
     c = np.where(c <= 0.04045, c / 12.92, ((c + 0.055) / 1.055) ** 2.4)
-    m = np.array([[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722], [0.0193, 0.1192, 0.9505]])
-    xyz = c @ m.T / np.array([0.95047, 1.0, 1.08883])
+    xyz = c @ m.T / m.sum(axis=1)
     d = 6.0 / 29.0
     f = np.where(xyz > d ** 3, np.cbrt(xyz), xyz / (3 * d * d) + 4.0 / 29.0)
     return np.stack([116 * f[..., 1] - 16, 500 * (f[..., 0] - f[..., 1]),
                      200 * (f[..., 1] - f[..., 2])], axis=-1)
+
+
+def _lab_torch(x):
+    """The same conversion on a torch tensor (any device), FP64: uint8
+    H x W x 3 (or 4) -> L*a*b*."""
+    import torch
+    m = torch.tensor(SRGB_TO_XYZ, dtype=torch.float64, device=x.device)
+    c = x[..., :3].double() / 255.0
+    c = torch.where(c <= 0.04045, c / 12.92, ((c + 0.055) / 1.055) ** 2.4)
+    xyz = (c @ m.T) / m.sum(dim=1)
+    d = 6.0 / 29.0
+    f = torch.where(xyz > d ** 3, xyz.clamp_min(0).pow(1.0 / 3.0), xyz / (3 * d * d) + 4.0 / 29.0)
+    return torch.stack([116 * f[..., 1] - 16, 500 * (f[..., 0] - f[..., 1]),
+                        200 * (f[..., 1] - f[..., 2])], -1)
 
 
 def _quality(clean, ref, out):
@@ -752,18 +821,7 @@ def bench_quality_study(count=64, size=512, reps=3):
     filters = [("bvdf", "poly"), ("amnfe", "rational"), ("evmf", "rational")]
     sets = [("uncorrelated", 0.10), ("correlated", 0.10), ("mixed", 0.10),
             ("correlated", 0.20), ("correlated", 0.30), ("correlated", 0.40)]
-    m = torch.tensor([[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722],
-                      [0.0193, 0.1192, 0.9505]], dtype=torch.float64, device="cuda")
-    white = torch.tensor([0.95047, 1.0, 1.08883], dtype=torch.float64, device="cuda")
-
-    def lab(x):  # uint8 H x W x 3 (or 4) -> FP64 L*a*b*
-        c = x[..., :3].double() / 255.0
-        c = torch.where(c <= 0.04045, c / 12.92, ((c + 0.055) / 1.055) ** 2.4)
-        xyz = (c @ m.T) / white
-        d = 6.0 / 29.0
-        f = torch.where(xyz > d ** 3, xyz.clamp_min(0).pow(1.0 / 3.0), xyz / (3 * d * d) + 4.0 / 29.0)
-        return torch.stack([116 * f[..., 1] - 16, 500 * (f[..., 0] - f[..., 1]),
-                            200 * (f[..., 1] - f[..., 2])], -1)
+    lab = _lab_torch
 
     def metrics(clean, lab_clean, y):
         d = clean[..., :3].double() - y[..., :3].double()

@@ -177,6 +177,33 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
                              double lo, double hi, double* num, int* num_len, double* den,
                              int* den_len, double* eps);
 
+/* Load the caller's own approximant of `fn` into the context (Sec. 2: any
+ * minimax polynomial or rational the caller fitted, e.g. the coefficients
+ * printed in Table 1 (VF_FN_ACOS_LO / VF_FN_ACOS_HI, degree 4) or Table 2
+ * (VF_FN_EXP, degrees 2..4)).
+ *   approx    VF_MINIMAX_POLY (degree 2..6): num[0..degree] in increasing
+ *             powers, den NULL and den_len 0; or VF_MINIMAX_RATIONAL_FIT
+ *             (degree 2..4): num[0..degree] / den[0..degree]
+ *   lo, hi    the interval the coefficients are meant for; the library
+ *             measures their maximum error against the function there (on
+ *             a 20,001-point grid) and reports it through vf_get_approximant
+ * From then on every call in this context that evaluates the degree-`degree`
+ * approximant of that kind for `fn` uses these coefficients (rounded to
+ * FP32 for the kernels) in place of the library's own fit, whatever the
+ * filter's interval or cut-off: vf_filter, vf_filter_host(_async),
+ * vf_filter_gated, vf_batch_create (a batch keeps the coefficients it was
+ * created with) and vf_batch_run_static.  vf_get_approximant returns them as
+ * given.  num = NULL, num_len = 0, den = NULL, den_len = 0 removes them (the
+ * library's fit is used again).  Host memory, read during the call;
+ * synchronous; no device work.
+ * Errors: VF_ERR_ARG (null context, bad enum, degree or interval, wrong
+ * coefficient counts, a non-finite coefficient, a denominator with a zero or
+ * a sign change on [lo, hi]), VF_ERR_UNSUPPORTED (VF_MINIMAX_RATIONAL: the
+ * paper's printed rationals are fixed). */
+vf_status vf_set_coefficients(vf_ctx* ctx, vf_function fn, vf_approx approx, int degree,
+                              const double* num, int num_len, const double* den, int den_len,
+                              double lo, double hi);
+
 /* Filter one image (Sec. 3): d_out(r,c) = F(W(r,c)) for every pixel.
  *   d_in, d_out   device pointers, height x width pixels of `channels`
  *                 (3 or 4) bytes, rows in_pitch / out_pitch bytes apart
@@ -320,9 +347,15 @@ void vf_batch_destroy(vf_batch* b);
  *   - No error text is recorded in the context (that could allocate).
  *   - The H2D copies of the descriptors come from the library's own static
  *     host buffer; the host side of the calls is serialised by a mutex.
- * Errors: VF_ERR_ARG (null pointers, count < 1, bad sizes or enums),
+ *     Because a replay of a recorded copy would read that buffer again after
+ *     later calls changed it, a call on a stream that is being captured is
+ *     refused with VF_ERR_UNSUPPORTED.
+ * Errors: VF_ERR_ARG (null pointers, count < 1, bad sizes or enums, an
+ * ENT cut-off outside (0, 1) for a fitted ENT approximant),
  * VF_ERR_UNSUPPORTED (count > VF_STATIC_MAX_IMAGES, a window other than
- * 3/5/7, an approximant not yet fitted), VF_ERR_ALIAS, VF_ERR_CUDA.
+ * 3/5/7, a precision other than FP32, an approximant not yet fitted, a
+ * capturing stream), VF_ERR_ALIAS, VF_ERR_CUDA (the runtime's last error is
+ * cleared before returning).
  * Asynchronous on `stream` apart from the pageable descriptor copies. */
 #define VF_STATIC_MAX_IMAGES 256
 vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count, void* stream);

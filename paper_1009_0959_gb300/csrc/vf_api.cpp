@@ -48,6 +48,10 @@ struct FitVal {
 
 struct vf_ctx {
   std::map<FitKey, FitVal> fits;
+  // vf_set_coefficients: the caller's approximants, keyed (kind: 0 polynomial,
+  // 1 rational; function; degree); they take the place of the library's fits
+  // on every interval
+  std::map<std::tuple<int, int, int>, FitVal> user;
   std::string last_error;
   int tile_rows = 4;  // TY of the per-window single-image launches
   int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF, EVBDF), 2 always
@@ -76,7 +80,13 @@ vf_status fail(vf_ctx* ctx, vf_status s, const std::string& msg) {
   return s;
 }
 
+const FitVal* user_fit(const vf_ctx* ctx, int kind, int fn, int degree) {
+  auto it = ctx->user.find(std::make_tuple(kind, fn, degree));
+  return it == ctx->user.end() ? nullptr : &it->second;
+}
+
 const FitVal* get_fit(vf_ctx* ctx, int fn, int degree, double lo, double hi) {
+  if (const FitVal* u = user_fit(ctx, 0, fn, degree)) return u;
   FitKey k{0, fn, degree, lo, hi};
   auto it = ctx->fits.find(k);
   if (it != ctx->fits.end()) return &it->second;
@@ -87,6 +97,7 @@ const FitVal* get_fit(vf_ctx* ctx, int fn, int degree, double lo, double hi) {
 
 // The library's own best (degree, degree) rational of function fn on [lo, hi].
 const FitVal* get_rational_fit(vf_ctx* ctx, int fn, int degree, double lo, double hi) {
+  if (const FitVal* u = user_fit(ctx, 1, fn, degree)) return u;
   FitKey k{1, fn, degree, lo, hi};
   auto it = ctx->fits.find(k);
   if (it != ctx->fits.end()) return &it->second;
@@ -204,6 +215,48 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
   *num_len = degree + 1;
   *den_len = 0;
   *eps = f->eps;
+  return VF_OK;
+}
+
+vf_status vf_set_coefficients(vf_ctx* ctx, vf_function fn, vf_approx approx, int degree,
+                              const double* num, int num_len, const double* den, int den_len,
+                              double lo, double hi) {
+  if (!ctx) return VF_ERR_ARG;
+  if ((int)fn < 0 || (int)fn > 3) return fail(ctx, VF_ERR_ARG, "bad function");
+  if (approx == VF_MINIMAX_RATIONAL)
+    return fail(ctx, VF_ERR_UNSUPPORTED,
+                "the paper's printed rationals are fixed; load a rational as "
+                "VF_MINIMAX_RATIONAL_FIT");
+  if (approx != VF_MINIMAX_POLY && approx != VF_MINIMAX_RATIONAL_FIT)
+    return fail(ctx, VF_ERR_ARG, "approx must be VF_MINIMAX_POLY or VF_MINIMAX_RATIONAL_FIT");
+  const int kind = approx == VF_MINIMAX_POLY ? 0 : 1;
+  if (kind == 0 && (degree < 2 || degree > 6)) return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
+  if (kind == 1 && (degree < 2 || degree > 4))
+    return fail(ctx, VF_ERR_ARG, "rational degree must be 2..4");
+  const auto key = std::make_tuple(kind, (int)fn, degree);
+  if (!num && num_len == 0 && !den && den_len == 0) {  // back to the library's own fit
+    ctx->user.erase(key);
+    return VF_OK;
+  }
+  if (!num || num_len != degree + 1)
+    return fail(ctx, VF_ERR_ARG, "num must hold degree + 1 coefficients");
+  if (kind == 0 && den_len != 0) return fail(ctx, VF_ERR_ARG, "a polynomial has no denominator");
+  if (kind == 1 && (!den || den_len != degree + 1))
+    return fail(ctx, VF_ERR_ARG, "den must hold degree + 1 coefficients");
+  if (!std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo))
+    return fail(ctx, VF_ERR_ARG, "bad interval");
+  FitVal v{};
+  for (int k = 0; k < num_len; ++k) {
+    if (!std::isfinite(num[k])) return fail(ctx, VF_ERR_ARG, "non-finite coefficient");
+    v.coef[k] = num[k];
+  }
+  for (int k = 0; k < den_len; ++k) {
+    if (!std::isfinite(den[k])) return fail(ctx, VF_ERR_ARG, "non-finite coefficient");
+    v.den[k] = den[k];
+  }
+  if (!approximant_error((int)fn, v.coef, num_len, v.den, den_len, lo, hi, &v.eps))
+    return fail(ctx, VF_ERR_ARG, "the denominator vanishes on the interval");
+  ctx->user[key] = v;
   return VF_OK;
 }
 
@@ -339,12 +392,18 @@ bool use_pair_reuse(const vf_ctx* ctx, int w, int crit) {
 }
 
 const double* cached_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi) {
+  if (const FitVal* u = user_fit(ctx, 0, fn, degree)) return u->coef;
   auto it = ctx->fits.find(FitKey{0, fn, degree, lo, hi});
   return it == ctx->fits.end() ? nullptr : it->second.coef;
 }
 
 bool cached_rational_fit(const vf_ctx* ctx, int fn, int degree, double lo, double hi,
                          const double** num, const double** den) {
+  if (const FitVal* u = user_fit(ctx, 1, fn, degree)) {
+    *num = u->coef;
+    *den = u->den;
+    return true;
+  }
   auto it = ctx->fits.find(FitKey{1, fn, degree, lo, hi});
   if (it == ctx->fits.end()) return false;
   *num = it->second.coef;

@@ -495,7 +495,10 @@ vf_status static_scratch(StaticLayout** out) {
   if (!g_static_dev[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr) return VF_ERR_CUDA;
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return VF_ERR_CUDA;
+    }
     g_static_dev[dev] = p;
   }
   *out = static_cast<StaticLayout*>(g_static_dev[dev]);
@@ -511,7 +514,8 @@ vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* 
   if (d.height < 1 || d.width < 1 || (d.channels != 3 && d.channels != 4)) return VF_ERR_ARG;
   const size_t row = (size_t)d.width * d.channels;
   if (d.in_pitch < row || d.out_pitch < row) return VF_ERR_ARG;
-  if ((int)p->criterion < 0 || (int)p->criterion > 5 || (int)p->approx < 0 || (int)p->approx > 3)
+  if ((int)p->criterion < 0 || (int)p->criterion > 5 || (int)p->approx < 0 || (int)p->approx > 3 ||
+      (int)p->precision < 0 || (int)p->precision > 2)
     return VF_ERR_ARG;
   if (p->criterion == VF_EVBDF) return VF_ERR_UNSUPPORTED;
   if (p->window < 1 || (p->window & 1) == 0 || p->window > 15) return VF_ERR_ARG;
@@ -561,6 +565,7 @@ vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* 
     if (!a) return VF_ERR_UNSUPPORTED;
     put(L.c.a, a, p->degree + 1);
   } else if (apx == kRational && rfit) {
+    if (crit == kEVMF && (!(L.ent_cutoff > 0.0f) || L.ent_cutoff >= 1.0f)) return VF_ERR_ARG;
     const double *num = nullptr, *den = nullptr;
     const bool ok = crit == kEVMF
                         ? cached_rational_fit(ctx, 3, p->degree, (double)L.ent_cutoff, 1.0, &num, &den)
@@ -591,6 +596,15 @@ extern "C" {
 vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count, void* stream) {
   if (!ctx || !descs || count < 1) return VF_ERR_ARG;
   if (count > kStaticMax) return VF_ERR_UNSUPPORTED;
+  // the descriptor copies read the library's one host staging buffer: a
+  // captured copy would read it again at every replay, after later calls had
+  // overwritten it, so a capturing stream is refused
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &capture) != cudaSuccess) {
+    cudaGetLastError();
+    return VF_ERR_CUDA;
+  }
+  if (capture != cudaStreamCaptureStatusNone) return VF_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_static_mutex);
   StaticLayout* dev = nullptr;
   vf_status st = static_scratch(&dev);
@@ -642,7 +656,10 @@ vf_status vf_batch_run_static(vf_ctx* ctx, const vf_image_desc* descs, int count
     e = cudaMemcpyAsync(dev->imgs, H.imgs, sizeof(BatchImage) * count, cudaMemcpyHostToDevice, s);
   // every call starts its tile counter at zero (the array keeps the last call's)
   if (e == cudaSuccess) e = cudaMemsetAsync(dev->counter, 0, sizeof(unsigned int), s);
-  if (e != cudaSuccess) return VF_ERR_CUDA;
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // leave no error behind for the caller's next CUDA call
+    return VF_ERR_CUDA;
+  }
   batch_kernel<<<sms * std::max(per_sm, 1), kTX * ty, smem, s>>>(dev->imgs, dev->begin, count,
                                                                  dev->counter);
   return cudaGetLastError() == cudaSuccess ? VF_OK : VF_ERR_CUDA;

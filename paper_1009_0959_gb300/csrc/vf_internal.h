@@ -186,4 +186,10 @@ bool remez_fit(int fn, int degree, double lo, double hi, double* coef, double* e
 bool remez_rational_fit(int fn, int m, int n, double lo, double hi, double* num, double* den,
                         double* eps);
 
+// Maximum error of p/q (q = 1 when den_len = 0) against function id fn on a
+// 20,001-point grid of [lo, hi]; false when the denominator changes sign or
+// vanishes on the grid.
+bool approximant_error(int fn, const double* num, int num_len, const double* den, int den_len,
+                       double lo, double hi, double* eps);
+
 }  // namespace vf

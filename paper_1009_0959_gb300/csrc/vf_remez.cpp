@@ -346,4 +346,25 @@ bool remez_rational_fit(int fn, int m, int n, double lo, double hi, double* num,
   return true;
 }
 
+bool approximant_error(int fn, const double* num, int num_len, const double* den, int den_len,
+                       double lo, double hi, double* eps) {
+  double e = 0.0;
+  int sign = 0;  // sign of the denominator at lo; it must keep it on [lo, hi]
+  for (int g = 0; g <= 20000; ++g) {
+    const double x = lo + (hi - lo) * g / 20000.0;
+    double pv = 0.0, qv = 1.0;
+    for (int k = num_len - 1; k >= 0; --k) pv = pv * x + num[k];
+    if (den_len > 0) {
+      qv = 0.0;
+      for (int k = den_len - 1; k >= 0; --k) qv = qv * x + den[k];
+      const int sg = qv > 0.0 ? 1 : (qv < 0.0 ? -1 : 0);
+      if (sg == 0 || (sign != 0 && sg != sign)) return false;  // a pole on the interval
+      sign = sg;
+    }
+    e = std::max(e, std::fabs(target(fn, x) - pv / qv));
+  }
+  *eps = e;
+  return std::isfinite(e);
+}
+
 }  // namespace vf

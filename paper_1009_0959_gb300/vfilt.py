@@ -77,6 +77,9 @@ def lib():
                                              ctypes.POINTER(I), P, ctypes.POINTER(I),
                                              ctypes.POINTER(ctypes.c_double)]
             L.vf_get_approximant.restype = I
+            L.vf_set_coefficients.argtypes = [P, I, I, I, P, I, P, I, ctypes.c_double,
+                                              ctypes.c_double]
+            L.vf_set_coefficients.restype = I
             L.vf_filter.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P, P]
             L.vf_filter.restype = I
             L.vf_filter_host.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P]
@@ -477,6 +480,23 @@ def get_approximant(fn: str, approx: str = "poly", degree: int = 4, lo: float = 
                                     float(hi), num, ctypes.byref(nl), den, ctypes.byref(dl),
                                     ctypes.byref(eps)), ctx)
     return list(num[: nl.value]), list(den[: dl.value]), eps.value
+
+
+def set_coefficients(fn: str, approx: str, degree: int, num=None, den=None, lo: float = 0.0,
+                     hi: float = 1.0):
+    """vf_set_coefficients: the caller's own approximant of `fn` (increasing
+    powers) for every later call of this thread's context; num=None restores
+    the library's fit."""
+    ctx = context()
+    if num is None:
+        st = lib().vf_set_coefficients(ctx, FUNCTIONS[fn], APPROX[approx], int(degree), None, 0,
+                                       None, 0, float(lo), float(hi))
+    else:
+        n = (ctypes.c_double * len(num))(*num)
+        d = (ctypes.c_double * len(den))(*den) if den else None
+        st = lib().vf_set_coefficients(ctx, FUNCTIONS[fn], APPROX[approx], int(degree), n,
+                                       len(num), d, len(den) if den else 0, float(lo), float(hi))
+    _check(st, ctx)
 
 
 def status_string(code: int) -> str:

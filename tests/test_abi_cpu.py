@@ -146,3 +146,66 @@ def test_evbdf_argument_checks(vf):
                          approx="rational") == 3
     assert vf.filter_ptr(base, base + 4096, 8, 8, 4, 32, 32, criterion="evbdf", approx="poly",
                          precision="fp16x2") == 3
+
+
+def test_set_coefficients_round_trip(vf, golden):
+    """vf_set_coefficients: the printed Table 1 / Table 2 rows and tab_exp_rat
+    (as a caller's rational) load into the context and come back from
+    vf_get_approximant as given, with their maximum error on the interval
+    measured by the library (the printed eps, to the printed precision); a
+    cleared entry gives the library's own fit back."""
+    import numpy as np
+    try:
+        for key, fn in [("table1_arcsin", "acos_hi"), ("table1_arccos", "acos_lo")]:
+            g = golden[key]
+            vf.set_coefficients(fn, "poly", 4, g["coef"], lo=g["interval"][0], hi=g["interval"][1])
+            num, den, eps = vf.get_approximant(fn, "poly", 4, *g["interval"])
+            assert num == g["coef"] and den == []
+            assert eps == pytest.approx(g["eps"], rel=3e-2)
+        for d, row in golden["table2_exp"]["rows"].items():
+            vf.set_coefficients("exp", "poly", int(d), row["coef"], lo=0.0, hi=10.0)
+            num, _, eps = vf.get_approximant("exp", "poly", int(d), 0.0, 10.0)
+            assert num == row["coef"]
+            assert eps == pytest.approx(row["eps"], rel=2e-3)
+        r = golden["exp_rational"]
+        vf.set_coefficients("exp", "rational_fit", 4, r["num"], r["den"], 0.0, 10.0)
+        num, den, eps = vf.get_approximant("exp", "rational_fit", 4, 0.0, 10.0)
+        assert num == r["num"] and den == r["den"]
+        assert 0.9 * r["eps"] <= eps <= 1.2 * r["eps"]
+    finally:
+        for fn in ("acos_hi", "acos_lo"):
+            vf.set_coefficients(fn, "poly", 4)
+        for d in (2, 3, 4):
+            vf.set_coefficients("exp", "poly", d)
+        vf.set_coefficients("exp", "rational_fit", 4)
+    num, _, _ = vf.get_approximant("acos_lo", "poly", 4, 0.0, 0.5)
+    # the library's own fit again: a_2 = -1.42988e-2 (the printed -1.429899e-2
+    # differs in the fifth digit)
+    assert num[2] == pytest.approx(-1.4298809e-2, rel=2e-6)
+    num, den, _ = vf.get_approximant("exp", "rational_fit", 4, 0.0, 10.0)
+    assert den[0] == 1.0 and np.isfinite(num).all()
+
+
+def test_set_coefficients_errors(vf):
+    E = vf.VFError
+    with pytest.raises(E) as e:
+        vf.set_coefficients("exp", "poly", 4, [1.0, 2.0, 3.0], lo=0.0, hi=10.0)  # too few
+    assert e.value.name == "VF_ERR_ARG"
+    with pytest.raises(E) as e:
+        vf.set_coefficients("exp", "poly", 7, [0.0] * 8, lo=0.0, hi=10.0)  # degree > 6
+    assert e.value.name == "VF_ERR_ARG"
+    with pytest.raises(E) as e:
+        vf.set_coefficients("exp", "rational", 4, [1.0] * 5, [1.0] * 5, 0.0, 10.0)
+    assert e.value.name == "VF_ERR_UNSUPPORTED"
+    with pytest.raises(E) as e:  # denominator 1 - z/5 vanishes at z = 5
+        vf.set_coefficients("exp", "rational_fit", 2, [1.0, 0.0, 0.0], [1.0, -0.2, 0.0], 0.0, 10.0)
+    assert e.value.name == "VF_ERR_ARG"
+    with pytest.raises(E) as e:
+        vf.set_coefficients("ent", "poly", 2, [0.0, float("nan"), 0.0], lo=0.05, hi=1.0)
+    assert e.value.name == "VF_ERR_ARG"
+    with pytest.raises(E) as e:
+        vf.set_coefficients("ent", "poly", 2, [0.0, 1.0, 0.0], lo=1.0, hi=0.05)
+    assert e.value.name == "VF_ERR_ARG"
+    # nothing was stored by the failed calls
+    num, _, _ = vf.get_approximant("exp", "poly", 4, 0.0, 10.0)
+    assert num[0] == pytest.approx(0.9666313, rel=1e-5)

@@ -62,3 +62,40 @@ def test_reference_arm_runs_on_rank_zero_only():
     with contextlib.redirect_stdout(out):
         assert bench.reference_arm(args, 1, 2) == 0
     assert out.getvalue() == ""
+
+
+def test_bench_lab_matches_oracle_metrics():
+    """The benchmark's quality study converts to L*a*b* with its own code
+    (numpy and torch forms); both agree with the oracle's pinned conversion
+    (oracle.metrics.srgb_to_lab: sRGB white -> (100, 0, 0)) on every 8-bit
+    grey level and on random colours, and so do the NCD figures built on it."""
+    import numpy as np
+    from oracle import metrics as M
+    rng = np.random.default_rng(3)
+    rgb = np.concatenate([np.repeat(np.arange(256, dtype=np.uint8)[:, None], 3, 1),
+                          rng.integers(0, 256, (4096, 3)).astype(np.uint8)])
+    ref = M.srgb_to_lab(rgb)
+    np.testing.assert_allclose(bench._lab(rgb), ref, rtol=0, atol=1e-10)
+    got = bench._lab_torch(torch.from_numpy(rgb)).numpy()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-9)
+    clean = rng.integers(0, 256, (40, 50, 3)).astype(np.uint8)
+    other = np.clip(clean.astype(int) + rng.integers(-9, 10, clean.shape), 0, 255).astype(np.uint8)
+    lc = bench._lab(clean)
+    ncd = np.linalg.norm(bench._lab(other) - lc, axis=-1).sum() / np.linalg.norm(lc, axis=-1).sum()
+    assert ncd == pytest.approx(M.ncd(clean, other), rel=1e-12)
+
+
+def test_roofline_object():
+    """The roofline's arithmetic: FP32 ops per pixel x pixels / launch time
+    against 152 x 128 lanes x the maximum clock; the issue fraction against
+    the same rate; traffic = DRAM bytes per pixel x pixels."""
+    r = bench.roofline("bvdf/exact/w5", {"fp32": 1000, "inst": 3000, "dram": 7.0,
+                                         "fma_pipe": 0.4}, 1 << 20, 0.1, None)
+    peak = r["peak"]
+    assert peak == pytest.approx(152 * 128 * 2070e6 / 1e12, rel=1e-3)
+    assert r["achieved"] == pytest.approx(1000 * (1 << 20) / 1e-4 / 1e12, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak, rel=1e-3)
+    assert r["issue_frac"] == pytest.approx(3 * r["frac"], rel=1e-3)
+    assert r["traffic"] == 7 * (1 << 20) and r["bound"] == "alu"
+    empty = bench.roofline("x", None, 100, 1.0, 2000.0)
+    assert empty["frac"] is None and empty["traffic"] is None

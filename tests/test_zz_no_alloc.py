@@ -91,3 +91,71 @@ def test_static_batch_rational_fits(vf):
     for (_, o, _), (_, r, _) in zip(outs, ref):
         assert torch.equal(o, r)
     b.close()
+
+
+def test_static_batch_bad_enums_and_cutoffs(vf):
+    """The same status codes as the ordinary calls for the same bad input: a
+    precision outside the enum is VF_ERR_ARG (1), an FP16x2 image
+    VF_ERR_UNSUPPORTED (3), an EVMF with a fitted ENT rational and a cut-off
+    outside (0, 1) VF_ERR_ARG."""
+    t = torch.zeros((8, 8, 4), dtype=torch.uint8, device="cuda")
+    o = torch.zeros_like(t)
+    assert vf.batch_run_static([(t, o, {"precision": 7})]) == 1
+    assert vf.batch_run_static([(t, o, {"criterion": "vmf", "precision": "fp16x2"})]) == 3
+    assert vf.batch_run_static([(t, o, dict(criterion="evmf", approx="rational_fit", degree=2,
+                                            ent_cutoff=1.5))]) == 1
+
+
+def test_static_batch_refuses_capture(vf):
+    """A call on a capturing stream is refused (VF_ERR_UNSUPPORTED) and leaves
+    the capture usable; the plain call afterwards still works."""
+    imgs = _images(6, 9)
+    ref = [(t, torch.zeros_like(t), p) for t, p in imgs]
+    b = vf.Batch(ref)
+    b.launch()
+    torch.cuda.synchronize()
+    outs = [(t, torch.zeros_like(t), p) for t, p in imgs]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    codes = []
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            codes.append(vf.batch_run_static(outs, stream=s))
+    torch.cuda.current_stream().wait_stream(s)
+    assert codes == [3]
+    assert vf.batch_run_static(outs) == 0
+    torch.cuda.synchronize()
+    for (_, o, _), (_, r, _) in zip(outs, ref):
+        assert torch.equal(o, r)
+    b.close()
+
+
+def test_static_batch_back_to_back_on_one_stream(vf):
+    """Two calls on the current stream with different image sets, windows and
+    criteria and no host wait between them: the second call's descriptor
+    copies must not disturb the first call's (each copy has read the host
+    staging before its call returns, and calls on one stream are ordered).
+    One synchronize, then both outputs byte for byte against the ordinary
+    batched call."""
+    a = _images(24, 11)
+    b_imgs = [(t, dict(p, window={3: 7, 5: 3, 7: 5}[p["window"]],
+                       criterion=CRITS[(CRITS.index(p["criterion"]) + 2) % 5]))
+              for t, p in _images(30, 12)]
+    for p in [p for _, p in b_imgs]:  # keep the minimax settings valid for the new criterion
+        p["approx"], p["degree"] = ("exact", 4) if p["approx"] == "exact" else MINIMAX[p["criterion"]]
+    refs = []
+    for imgs in (a, b_imgs):
+        r = [(t, torch.zeros_like(t), p) for t, p in imgs]
+        bb = vf.Batch(r)
+        bb.launch()
+        torch.cuda.synchronize()
+        bb.close()
+        refs.append(r)
+    outs = [[(t, torch.full_like(t, 3), p) for t, p in imgs] for imgs in (a, b_imgs)]
+    assert vf.batch_run_static(outs[0]) == 0
+    assert vf.batch_run_static(outs[1]) == 0
+    torch.cuda.synchronize()
+    for out, ref in zip(outs, refs):
+        for (_, o, _), (_, r, _) in zip(out, ref):
+            assert torch.equal(o, r)
