@@ -256,6 +256,35 @@ vf_status vf_filter_host_async(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out,
  * (its output is in host memory).  VF_ERR_CUDA if one of them failed. */
 vf_status vf_host_sync(vf_ctx* ctx);
 
+/* ---- row bands: one image split over several devices or calls --------------
+ * Every output pixel depends only on its own window (Sec. 3: y(r,c) =
+ * F(W(r,c))), so an image can be filtered in horizontal bands, each band a
+ * separate vf_filter call (on its own GPU, or one after another) on a copy of
+ * its rows plus (w - 1) / 2 halo rows above and below.  The band calls give
+ * the whole-image call's bytes when each band's first row lines up with the
+ * kernel's output tiles: vf_row_quantum gives that row quantum and
+ * vf_band_plan rounds the band's first input row down to it.
+ *
+ * vf_row_quantum: output rows per tile of the kernel vf_filter launches for
+ * `p` with this context's options (*rows).  Host only.
+ * Errors: VF_ERR_ARG (null pointers, bad enums), VF_ERR_UNSUPPORTED (window
+ * not 3/5/7). */
+vf_status vf_row_quantum(vf_ctx* ctx, const vf_params* p, int* rows);
+
+/* vf_band_plan: band `band` of `bands` (0-based) of an image `height` rows
+ * high, window `window`: the band's output rows are [*out_row0, *out_row0 +
+ * *out_rows) = [band * height / bands, (band + 1) * height / bands) (integer
+ * division); its input is the *in_rows image rows from *in_row0 on: the
+ * output rows, (window - 1) / 2 halo rows below (fewer at the image's bottom)
+ * and the halo above, extended up to a multiple of `quantum` (0 at the
+ * top).  vf_filter on those input rows (as an image of *in_rows rows) gives
+ * the band's output rows at rows *out_row0 - *in_row0 onwards of its output.
+ * Host arithmetic only; no context needed.
+ * Errors: VF_ERR_ARG (null pointers, height < 1, an even or non-positive
+ * window, quantum < 1, bands < 1 or > height, band outside [0, bands)). */
+vf_status vf_band_plan(int height, int window, int quantum, int bands, int band, int* in_row0,
+                       int* in_rows, int* out_row0, int* out_rows);
+
 /* ---- batched form: many images in one persistent launch ------------------ */
 
 /* One image of a batch: device buffers (caller-owned, as in vf_filter) and its

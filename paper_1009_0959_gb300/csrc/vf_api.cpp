@@ -1,5 +1,6 @@
 // vf_api.cpp -- the C ABI of include/vfilt.h: argument checks, the minimax
 // coefficient cache and kernel dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -257,6 +258,48 @@ vf_status vf_set_coefficients(vf_ctx* ctx, vf_function fn, vf_approx approx, int
   if (!approximant_error((int)fn, v.coef, num_len, v.den, den_len, lo, hi, &v.eps))
     return fail(ctx, VF_ERR_ARG, "the denominator vanishes on the interval");
   ctx->user[key] = v;
+  return VF_OK;
+}
+
+vf_status vf_row_quantum(vf_ctx* ctx, const vf_params* p, int* rows) {
+  if (!ctx) return VF_ERR_ARG;
+  if (!p || !rows) return fail(ctx, VF_ERR_ARG, "null pointer");
+  if ((int)p->criterion < 0 || (int)p->criterion > 5 || (int)p->precision < 0 ||
+      (int)p->precision > 2)
+    return fail(ctx, VF_ERR_ARG, "bad enum");
+  if (p->window != 3 && p->window != 5 && p->window != 7)
+    return fail(ctx, VF_ERR_UNSUPPORTED, "windows 3, 5 and 7 are built");
+  const int w = p->window, crit = (int)p->criterion;
+  if (p->precision != VF_FP32) {
+    *rows = ctx->tile_rows;  // packed tiles: 64 x TY outputs, one row per thread row
+  } else if (use_pair_reuse(ctx, w, crit)) {
+    *rows = reuse_tile_rows(w, crit);
+  } else if (crit == kEVMF && w == 5) {
+    *rows = evmf_queue_rows(w);  // the work-queue kernel's own tiles
+  } else {
+    *rows = ctx->tile_rows * outputs_per_thread(w, crit);
+  }
+  return VF_OK;
+}
+
+vf_status vf_band_plan(int height, int window, int quantum, int bands, int band, int* in_row0,
+                       int* in_rows, int* out_row0, int* out_rows) {
+  if (!in_row0 || !in_rows || !out_row0 || !out_rows) return VF_ERR_ARG;
+  if (height < 1 || window < 1 || (window & 1) == 0 || quantum < 1 || bands < 1 ||
+      bands > height || band < 0 || band >= bands)
+    return VF_ERR_ARG;
+  const int h = window / 2;
+  const long long r0 = (long long)band * height / bands;
+  const long long r1 = (long long)(band + 1) * height / bands;
+  // the halo rows above, with the band's first row rounded down to the tile
+  // quantum so that its tiles line up with the whole image's
+  long long a = r0 - h;
+  a = a <= 0 ? 0 : a / quantum * quantum;
+  const long long b = std::min<long long>(height, r1 + h);
+  *in_row0 = (int)a;
+  *in_rows = (int)(b - a);
+  *out_row0 = (int)r0;
+  *out_rows = (int)(r1 - r0);
   return VF_OK;
 }
 

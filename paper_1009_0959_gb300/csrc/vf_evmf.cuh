@@ -21,12 +21,9 @@
 
 namespace vf {
 
-// Tile rows of the queue kernel: 8 at 5 x 5 (less halo per output, fuller
-// batches; measured 4-13 % faster than 4; one CTA per SM of 16 rows / 128
-// registers or 24 rows / 80 registers measured 5-12 % slower than three of
-// 8 rows); 4 for larger windows, whose shared-memory aggregate slots and
-// larger queue entries would leave one CTA per SM.
-constexpr int evmf_queue_rows(int w) { return w <= 5 ? 8 : 4; }
+// Tile rows of the queue kernel: evmf_queue_rows (vf_internal.h); larger
+// windows take 4, whose shared-memory aggregate slots and larger queue
+// entries would leave one CTA per SM.
 
 // Queue of 2 * threads entries: fewer than `threads` wait after a batch, and
 // one tile adds at most `threads`.

@@ -80,6 +80,10 @@ def lib():
             L.vf_set_coefficients.argtypes = [P, I, I, I, P, I, P, I, ctypes.c_double,
                                               ctypes.c_double]
             L.vf_set_coefficients.restype = I
+            L.vf_row_quantum.argtypes = [P, ctypes.POINTER(Params), ctypes.POINTER(I)]
+            L.vf_row_quantum.restype = I
+            L.vf_band_plan.argtypes = [I, I, I, I, I] + [ctypes.POINTER(I)] * 4
+            L.vf_band_plan.restype = I
             L.vf_filter.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P, P]
             L.vf_filter.restype = I
             L.vf_filter_host.argtypes = [P, P, P, I, I, I, S, S, ctypes.POINTER(Params), P]
@@ -497,6 +501,48 @@ def set_coefficients(fn: str, approx: str, degree: int, num=None, den=None, lo: 
         st = lib().vf_set_coefficients(ctx, FUNCTIONS[fn], APPROX[approx], int(degree), n,
                                        len(num), d, len(den) if den else 0, float(lo), float(hi))
     _check(st, ctx)
+
+
+def row_quantum(**params) -> int:
+    """vf_row_quantum: output rows per tile of the kernel vf_filter runs for
+    these parameters (this thread's context options)."""
+    p = make_params(**params)
+    q = ctypes.c_int()
+    ctx = context()
+    _check(lib().vf_row_quantum(ctx, ctypes.byref(p), ctypes.byref(q)), ctx)
+    return q.value
+
+
+def band_plan(height: int, window: int, quantum: int, bands: int, band: int):
+    """vf_band_plan: (in_row0, in_rows, out_row0, out_rows) of one row band."""
+    v = [ctypes.c_int() for _ in range(4)]
+    st = lib().vf_band_plan(int(height), int(window), int(quantum), int(bands), int(band),
+                            *[ctypes.byref(x) for x in v])
+    if st != 0:
+        raise VFError(st, "vf_band_plan: bad arguments")
+    return tuple(x.value for x in v)
+
+
+def filter_band(host_img, band: int, bands: int, out=None, stream=None, **params):
+    """One row band of a host image (H x W x C uint8 tensor, pinned or not):
+    copies the band's input rows (with the halo) into device memory of the
+    current GPU, filters them there with vf_filter and copies the band's
+    output rows back into the rows [out_row0, out_row0 + out_rows) of the host
+    tensor `out` (allocated when None).  Returns (out, out_row0, out_rows).
+    Several processes, one per GPU, each filter their own band of an image
+    in shared host memory; no data moves between the GPUs."""
+    import torch
+    H = host_img.shape[0]
+    q = row_quantum(**params)
+    a, n, r0, m = band_plan(H, params.get("window", 3), q, bands, band)
+    if out is None:
+        out = torch.empty_like(host_img)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        d_in = host_img[a:a + n].to("cuda", non_blocking=True)
+        d_out = filter(d_in, stream=s, **params)
+        out[r0:r0 + m].copy_(d_out[r0 - a:r0 - a + m], non_blocking=False)
+    return out, r0, m
 
 
 def status_string(code: int) -> str:
