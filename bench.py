@@ -120,11 +120,11 @@ class Clocks:
 #   (sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100).
 # Keyed (criterion, approx, degree, window); degree 0 for exact / rational.
 MEASURED_PER_PIXEL = {
-    ("bvdf", "exact", 0, 5): {"inst": 3277, "dram": 7.06, "fp32": None, "fma_pipe": 0.403},
-    ("bvdf", "poly", 4, 5): {"inst": 2854, "dram": None, "fp32": None, "fma_pipe": None},
-    ("evmf", "exact", 0, 5): {"inst": 2433, "dram": 6.91, "fp32": None, "fma_pipe": None},
-    ("amnfe", "exact", 0, 5): {"inst": 1289, "dram": 7.04, "fp32": None, "fma_pipe": None},
-    ("vmf", "exact", 0, 5): {"inst": 1466, "dram": 7.05, "fp32": None, "fma_pipe": None},
+    ("bvdf", "exact", 0, 5): {"fp32": 1478.7, "inst": 3277.7, "dram": 7.045, "fma_pipe": 0.409},
+    ("bvdf", "poly", 4, 5): {"fp32": 1432.2, "inst": 2871.4, "dram": 7.030, "fma_pipe": 0.424},
+    ("evmf", "exact", 0, 5): {"fp32": 1083.8, "inst": 2432.6, "dram": 6.899, "fma_pipe": 0.378},
+    ("amnfe", "exact", 0, 5): {"fp32": 506.0, "inst": 1289.1, "dram": 7.040, "fma_pipe": 0.308},
+    ("vmf", "exact", 0, 5): {"fp32": 613.5, "inst": 1466.3, "dram": 7.063, "fma_pipe": 0.439},
 }
 
 
@@ -893,31 +893,44 @@ def bench_gate(frames=64, train_steps=800):
     import torch
 
     from paper_1009_0959_gb300 import synth, vfilt
+    kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
     t0 = time.perf_counter()
-    imgs, tgts = [], []
+    imgs, masks, gains = [], [], []
     for k in range(48):
         p = 0.05 + 0.25 * k / 47
         clean, noisy = synth.noisy(128, 128, p, 5000 + k)
-        imgs.append(synth.to_rgbx(noisy))
-        tgts.append(synth.impulse_mask(clean, noisy))
+        x = synth.to_rgbx(noisy)
+        imgs.append(x)
+        masks.append(synth.impulse_mask(clean, noisy))
+        # the plain filter's verdict: 1 where its output is closer to the
+        # clean pixel than the noisy pixel is (filtering this pixel pays)
+        y = vfilt.filter(torch.from_numpy(x).cuda(), **kw).cpu().numpy()[..., :3].astype(np.int32)
+        c, n = clean.astype(np.int32), noisy[..., :3].astype(np.int32)
+        gains.append((((y - c) ** 2).sum(-1) < ((n - c) ** 2).sum(-1)).astype(np.uint8))
     ti = torch.from_numpy(np.stack(imgs)).cuda()
-    tt = torch.from_numpy(np.stack(tgts)).cuda()
-    gate = vfilt.Gate(265)
-    loss = torch.zeros(1, device="cuda")
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    first = None
-    for s in range(train_steps):
-        k = (s * 8) % 48
-        gate.train_step(ti[k:k + 8], tt[k:k + 8], 1e-2, loss)
-        if s == 0:
-            torch.cuda.synchronize()
-            first = loss.item()
-    e1.record()
-    torch.cuda.synchronize()
-    train_ms = e0.elapsed_time(e1)
-    final = loss.item()
+
+    def train(targets, seed):
+        tt = torch.from_numpy(np.stack(targets)).cuda()
+        gate = vfilt.Gate(seed)
+        loss = torch.zeros(1, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        first = None
+        for s in range(train_steps):
+            k = (s * 8) % 48
+            gate.train_step(ti[k:k + 8], tt[k:k + 8], 1e-2, loss)
+            if s == 0:
+                torch.cuda.synchronize()
+                first = loss.item()
+        e1.record()
+        torch.cuda.synchronize()
+        return gate, e0.elapsed_time(e1), first, loss.item()
+
+    # targets: the generator's impulse masks, and the plain filter's outputs
+    # against the clean crops; the second gate is the one timed and reported
+    gate_mask, _, _, _ = train(masks, 265)
+    gate, train_ms, first, final = train(gains, 265)
 
     H, W = 2160, 3840
     noisy_d, clean_d = [], []
@@ -928,12 +941,16 @@ def bench_gate(frames=64, train_steps=800):
     out_plain = [torch.empty_like(noisy_d[0]) for _ in range(2)]
     out_gated = [torch.empty_like(noisy_d[0]) for _ in range(2)]
     flags = [torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in range(2)]
-    kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
+    kw_exact = dict(criterion="bvdf", window=5)
     stream = torch.cuda.current_stream()
 
     def plain():
         for f, x in enumerate(noisy_d):
             vfilt.filter(x, out_plain[f & 1], stream=stream, **kw)
+
+    def exact():
+        for f, x in enumerate(noisy_d):
+            vfilt.filter(x, out_plain[f & 1], stream=stream, **kw_exact)
 
     def gate_only():
         for f, x in enumerate(noisy_d):
@@ -955,24 +972,40 @@ def bench_gate(frames=64, train_steps=800):
         return a.elapsed_time(b)
 
     ms_plain, ms_gate, ms_gated = timed(plain), timed(gate_only), timed(gated)
+    ms_exact = timed(exact)
     # quality, untimed
-    ps_plain, ps_gated, differ, flagged = [], [], [], []
+    ps_plain, ps_gated, ps_mask, ps_noisy, differ, flagged = [], [], [], [], [], []
+
+    def psnr(o, c):
+        mse = ((o[..., :3].float() - c) ** 2).mean().item()
+        return 10 * math.log10(255 ** 2 / mse)
+
     for f, x in enumerate(noisy_d):
         op = vfilt.filter(x, **kw)
         fl = gate.infer(x, 0.5)
         og = vfilt.filter_gated(x, fl, **kw)
+        om = vfilt.filter_gated(x, gate_mask.infer(x, 0.5), **kw)
         c = clean_d[f].float()
-        for o, acc in ((op, ps_plain), (og, ps_gated)):
-            mse = ((o[..., :3].float() - c) ** 2).mean().item()
-            acc.append(10 * math.log10(255 ** 2 / mse))
+        ps_plain.append(psnr(op, c))
+        ps_gated.append(psnr(og, c))
+        ps_mask.append(psnr(om, c))
+        ps_noisy.append(psnr(x, c))
         differ.append((og[..., :3] != op[..., :3]).any(-1).float().mean().item())
         flagged.append(fl.float().mean().item())
     gate.close()
+    gate_mask.close()
     mpix = frames * H * W / 1e6
     return {"workload": "%d frames 3840x2160 panning scene (seed 265), impulses 5 -> 30 %%, "
                         "gate + 5x5 minimax BVDF (degree 4)" % frames,
             "train": {"steps": train_steps, "batch": "8 x 128x128", "ms": round(train_ms, 1),
-                      "loss_first": round(first, 4), "loss_last": round(final, 4)},
+                      "loss_first": round(first, 4), "loss_last": round(final, 4),
+                      "targets": "1 where the plain filter's output is closer to the clean "
+                                 "pixel than the noisy pixel (generator's clean crops + plain "
+                                 "filter outputs)"},
+            "exact_ms": round(ms_exact, 2), "exact_mpix_s": round(mpix / ms_exact * 1e3, 1),
+            "speedup_gated_vs_exact": round(ms_exact / ms_gated, 3),
+            "psnr_noisy_db_mean": round(float(np.mean(ps_noisy)), 3),
+            "psnr_gated_mask_targets_db_mean": round(float(np.mean(ps_mask)), 3),
             "plain_ms": round(ms_plain, 2), "plain_mpix_s": round(mpix / ms_plain * 1e3, 1),
             "gate_infer_ms": round(ms_gate, 2),
             "gate_infer_mpix_s": round(mpix / ms_gate * 1e3, 1),
