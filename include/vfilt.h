@@ -88,7 +88,10 @@ typedef enum {
   VF_FN_ACOS_LO = 0, /* arccos(z) on [0, 0.5]                    (Table 1, ARCCOS) */
   VF_FN_ACOS_HI = 1, /* 2 arcsin(tau / sqrt 2) on [0, 1/sqrt 2]   (Table 1, ARCSIN) */
   VF_FN_EXP = 2,     /* exp(-z) on [0, exp_cutoff]                (Table 2)         */
-  VF_FN_ENT = 3      /* z ln z on [ent_cutoff, 1]                 (tab_ent_rat)     */
+  VF_FN_ENT = 3,     /* z ln z on [ent_cutoff, 1]                 (tab_ent_rat)     */
+  VF_FN_HALF_ANGLE = 4 /* 2 atan(sqrt s) / sqrt s on [0, 1]: not in the paper; the
+                          exact angle A = u P(u^2), u = tan(A/2) = |a x b| /
+                          (|a||b| + a.b), with P of degree 7 (read-only)     */
 } vf_function;
 
 /* Filter parameters.  Fill with vf_default_params, then override. */
@@ -116,8 +119,10 @@ typedef struct {
 
 typedef struct vf_ctx vf_ctx;
 
-/* Create / destroy a context.  It holds the fitted coefficient cache, the
- * last error text and the device scratch of the batched calls. */
+/* Create / destroy a context.  It holds the fitted coefficient cache (the
+ * exact angle's arctangent polynomial is fitted on creation, a few
+ * milliseconds of host work), the last error text and the device scratch of
+ * the batched calls. */
 vf_status vf_create(vf_ctx** ctx);
 void vf_destroy(vf_ctx* ctx);
 
@@ -165,7 +170,9 @@ void vf_default_params(vf_params* p);
  * rational (VF_FN_EXP: tab_exp_rat on [0, 10]; VF_FN_ENT: tab_ent_rat on
  * [0.05, 1]; lo and hi are ignored); for VF_MINIMAX_RATIONAL_FIT the
  * library's own best (degree, degree) rational on [lo, hi] (degree 2..4,
- * denominator normalised to den[0] = 1).  num[0..*num_len), den[0..*den_len)
+ * denominator normalised to den[0] = 1).  Polynomial degrees 2..7 (the
+ * filters evaluate 2..6; VF_FN_HALF_ANGLE with degree 7 on [0, 1] is the
+ * polynomial of the exact angle, fitted when the context is created).  num[0..*num_len), den[0..*den_len)
  * receive coefficients in increasing powers (den_len = 0 for a polynomial;
  * arrays of 8 suffice), *eps the maximum error on [lo, hi] (fits) or on the
  * printed rational's interval (its printed value).  Fits are cached in the
@@ -196,8 +203,9 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
  * given.  num = NULL, num_len = 0, den = NULL, den_len = 0 removes them (the
  * library's fit is used again).  Host memory, read during the call;
  * synchronous; no device work.
- * Errors: VF_ERR_ARG (null context, bad enum, degree or interval, wrong
- * coefficient counts, a non-finite coefficient, a denominator with a zero or
+ * Errors: VF_ERR_ARG (null context, bad enum (VF_FN_HALF_ANGLE included: the
+ * exact angle's polynomial is fixed), degree or interval, wrong coefficient
+ * counts, a non-finite coefficient, a denominator with a zero or
  * a sign change on [lo, hi]), VF_ERR_UNSUPPORTED (VF_MINIMAX_RATIONAL: the
  * paper's printed rationals are fixed). */
 vf_status vf_set_coefficients(vf_ctx* ctx, vf_function fn, vf_approx approx, int degree,

@@ -120,7 +120,15 @@ extern "C" {
 vf_status vf_create(vf_ctx** ctx) {
   if (!ctx) return VF_ERR_ARG;
   *ctx = new (std::nothrow) vf_ctx();
-  return *ctx ? VF_OK : VF_ERR_OOM;
+  if (!*ctx) return VF_ERR_OOM;
+  // the exact angle's arctangent polynomial, fitted once per context so that
+  // every exact angle call (the allocation-free one included) finds it
+  if (!get_fit(*ctx, VF_FN_HALF_ANGLE, kHalfAngleDegree, 0.0, 1.0)) {
+    delete *ctx;
+    *ctx = nullptr;
+    return VF_ERR_ARG;
+  }
+  return VF_OK;
 }
 
 void vf_destroy(vf_ctx* ctx) {
@@ -198,7 +206,7 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
   }
   if (approx == VF_MINIMAX_RATIONAL_FIT) {
     if (degree < 2 || degree > 4) return fail(ctx, VF_ERR_ARG, "rational degree must be 2..4");
-    if ((int)fn < 0 || (int)fn > 3 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
+    if ((int)fn < 0 || (int)fn > 4 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
     const FitVal* f = get_rational_fit(ctx, (int)fn, degree, lo, hi);
     if (!f) return fail(ctx, VF_ERR_ARG, "rational minimax fit failed (pole on the interval)");
     for (int k = 0; k <= degree; ++k) num[k] = f->coef[k], den[k] = f->den[k];
@@ -208,8 +216,8 @@ vf_status vf_get_approximant(vf_ctx* ctx, vf_function fn, vf_approx approx, int 
     return VF_OK;
   }
   if (approx != VF_MINIMAX_POLY) return fail(ctx, VF_ERR_ARG, "approx must be poly or rational");
-  if (degree < 2 || degree > 6) return fail(ctx, VF_ERR_ARG, "degree must be 2..6");
-  if ((int)fn < 0 || (int)fn > 3 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
+  if (degree < 2 || degree > 7) return fail(ctx, VF_ERR_ARG, "degree must be 2..7");
+  if ((int)fn < 0 || (int)fn > 4 || !(hi > lo)) return fail(ctx, VF_ERR_ARG, "bad function/interval");
   const FitVal* f = get_fit(ctx, (int)fn, degree, lo, hi);
   if (!f) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
   for (int k = 0; k <= degree; ++k) num[k] = f->coef[k];
@@ -223,7 +231,8 @@ vf_status vf_set_coefficients(vf_ctx* ctx, vf_function fn, vf_approx approx, int
                               const double* num, int num_len, const double* den, int den_len,
                               double lo, double hi) {
   if (!ctx) return VF_ERR_ARG;
-  if ((int)fn < 0 || (int)fn > 3) return fail(ctx, VF_ERR_ARG, "bad function");
+  if ((int)fn < 0 || (int)fn > 3)
+    return fail(ctx, VF_ERR_ARG, "bad function (the exact angle's polynomial is fixed)");
   if (approx == VF_MINIMAX_RATIONAL)
     return fail(ctx, VF_ERR_UNSUPPORTED,
                 "the paper's printed rationals are fixed; load a rational as "
@@ -363,10 +372,16 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
   L.pdl = ctx->overlap;
 
   // coefficients of the approximant, rounded to FP32, zero above the degree
+  auto put = [](float* dst, const double* src, int len) {
+    for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
+  };
+  if (apx == kExact && (crit == kBVDF || crit == kEVBDF)) {
+    // the exact angle's arctangent polynomial (fitted when the context was made)
+    const FitVal* f = get_fit(ctx, VF_FN_HALF_ANGLE, kHalfAngleDegree, 0.0, 1.0);
+    if (!f) return fail(ctx, VF_ERR_ARG, "minimax fit failed");
+    put(L.c.a, f->coef, kHalfAngleDegree + 1);
+  }
   if (apx != kExact) {
-    auto put = [](float* dst, const double* src, int len) {
-      for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
-    };
     if (crit == kBVDF || crit == kEVBDF) {
       const FitVal* lo = get_fit(ctx, 0, p->degree, 0.0, 0.5);
       const FitVal* hi = get_fit(ctx, 1, p->degree, 0.0, 1.0 / std::sqrt(2.0));

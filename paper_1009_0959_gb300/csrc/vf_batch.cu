@@ -549,6 +549,11 @@ vf_status static_prepare(const vf_ctx* ctx, const vf_image_desc& d, BatchImage* 
   auto put = [](float* dst, const double* src, int len) {
     for (int k = 0; k < 8; ++k) dst[k] = k < len ? (float)src[k] : 0.0f;
   };
+  if (apx == kExact && crit == kBVDF) {  // fitted when the context was made
+    const double* a = cached_fit(ctx, VF_FN_HALF_ANGLE, kHalfAngleDegree, 0.0, 1.0);
+    if (!a) return VF_ERR_UNSUPPORTED;
+    put(L.c.a, a, kHalfAngleDegree + 1);
+  }
   if (apx == kPoly) {
     const double *a = nullptr, *b = nullptr;
     if (crit == kBVDF) {

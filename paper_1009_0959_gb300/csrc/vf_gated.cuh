@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) gated_kernel(const __grid_constant__ Laun
       ties += s.near_tie;
     } else if constexpr (APX == kExact) {
       Selection s =
-          window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleExact{}, sagg, stride, want_tie);
+          window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleExact(L.c.a), sagg, stride, want_tie);
       v = t.raw[(qy + s.best / W) * t.sw + qx + s.best % W];
       ties += s.near_tie;
     } else {

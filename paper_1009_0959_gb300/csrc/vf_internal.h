@@ -11,6 +11,9 @@
 namespace vf {
 
 constexpr int kTX = 32;  // output pixels per tile row (one warp)
+// Degree of the exact angle's arctangent polynomial (VF_FN_HALF_ANGLE): the
+// kernels evaluate its kHalfAngleDegree + 1 = 8 coefficients, in Coeffs::a.
+constexpr int kHalfAngleDegree = 7;
 
 enum { kVMF = 0, kBVDF = 1, kAMNFE = 2, kAMNFG = 3, kEVMF = 4, kEVBDF = 5 };
 enum { kExact = 0, kPoly = 1, kRational = 2 };

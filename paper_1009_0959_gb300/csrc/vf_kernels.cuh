@@ -147,17 +147,25 @@ __device__ __forceinline__ float cross2(float4 a, float4 b) {
 
 // Sec. 3.1, exact angle A = arccos(a.b / (|a||b|)).  Evaluated through the
 // half-angle identity tan(A/2) = |a x b| / (|a||b| + a.b): colour vectors
-// are non-negative, so a.b >= 0, A is in [0, pi/2] and the argument of the
-// arctangent is in [0, 1) -- the same angle without the loss of arccos near
-// 1, from the exact integer cross and dot products, and one arctangent
-// without quadrant cases (no divergent branches).  .w holds 1/|x| (0 for the
-// zero vector); a pair with a zero vector has angle pi/2.
+// are non-negative, so a.b >= 0, A is in [0, pi/2] and u = tan(A/2) is in
+// [0, 1) -- the same angle without the loss of arccos near 1, from the exact
+// integer cross and dot products.  A = 2 atan(u) = u P(u^2), P the library's
+// degree-7 minimax polynomial of 2 atan(sqrt s) / sqrt s on [0, 1] (Remez
+// exchange on the host, VF_FN_HALF_ANGLE; relative error 1.1e-7 before FP32
+// rounding, about that of a single-precision arctangent): no quadrant cases,
+// no divergent branches, FMA chains only.  c = its kHalfAngleCoeffs
+// coefficients.  .w holds 1/|x| (0 for the zero vector); a pair with a zero
+// vector has angle pi/2.
+constexpr int kHalfAngleCoeffs = 8;
 struct TermAngleExact {
+  const float* c;
+  __device__ __forceinline__ explicit TermAngleExact(const float* k) : c(k) {}
   __device__ __forceinline__ float operator()(float4 a, float4 b) const {
     const float dot = fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
     const float s = sqrt_approx(cross2(a, b));
     const float rr = a.w * b.w;  // 1 / (|a||b|)
-    const float ang = 2.0f * atanf(s * rr * rcp_approx(fmaf(dot, rr, 1.0f)));  // 1 + cos in [1, 2]
+    const float u = s * rr * rcp_approx(fmaf(dot, rr, 1.0f));  // 1 + cos in [1, 2]
+    const float ang = u * horner<kHalfAngleCoeffs>(c, u * u);
     return rr == 0.0f ? 1.57079632679f : ang;
   }
 };
@@ -773,7 +781,7 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
     if constexpr (CRIT == kVMF) {
       s = window_select<W, REG>(t.raw, t.sw, px, py, TermL2U8{}, sagg, stride, want_tie);
     } else if constexpr (APX == kExact) {
-      s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleExact{}, sagg, stride, want_tie);
+      s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleExact(L.c.a), sagg, stride, want_tie);
     } else {
       s = window_select<W, REG>(t.px, t.sw, px, py, TermAngleApprox<DEG>(L.c.a, L.c.b), sagg, stride,
                            want_tie);
@@ -808,7 +816,7 @@ __device__ __forceinline__ void process_tile(const Launch& L, int tile) {
       if constexpr (CRIT == kEVMF) {
         s = window_select<W, REG>(t.raw, t.sw, qx, qy, TermL2U8{}, sagg, stride, want_tie);
       } else if constexpr (APX == kExact) {  // EVBDF: the angle of Sec. 3.1
-        s = window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleExact{}, sagg, stride, want_tie);
+        s = window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleExact(L.c.a), sagg, stride, want_tie);
       } else {
         s = window_select<W, REG>(t.px, t.sw, qx, qy, TermAngleApprox<DEG>(L.c.a, L.c.b), sagg,
                                   stride, want_tie);

@@ -24,6 +24,11 @@ double target(int fn, double x) {
     case 1: return 2.0 * std::asin(x / std::sqrt(2.0));         // 2 arcsin(tau/sqrt2)
     case 2: return std::exp(-x);                                // exp(-z)
     case 3: return x > 0.0 ? x * std::log(x) : 0.0;             // z ln z
+    case 4: {  // 2 atan(sqrt s) / sqrt s: the exact angle's arctangent, A = u P(u^2)
+      if (x <= 0.0) return 2.0;
+      const double r = std::sqrt(x);
+      return 2.0 * std::atan(r) / r;
+    }
     default: return 0.0;
   }
 }

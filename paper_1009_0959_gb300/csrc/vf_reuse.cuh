@@ -24,6 +24,8 @@
 // another order (FP32, relative differences of a few 1e-7).
 #pragma once
 
+#include <type_traits>
+
 #include "vf_kernels.cuh"
 
 namespace vf {
@@ -42,6 +44,15 @@ struct ReuseGeom {
   static constexpr int THREADS = NT;         // threads of the CTA
   static constexpr int OUT = kRTX * RTY;      // outputs of the tile
 };
+
+// Calls f(std::integral_constant<int, k>{}) for k = A .. B in order.
+template <int A, int B, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (A <= B) {
+    f(std::integral_constant<int, A>{});
+    static_for<A + 1, B>(f);
+  }
+}
 
 inline size_t reuse_smem_bytes(int w, int rty = kRTY) {
   size_t rx = kRTX + w - 1, ry = rty + w - 1, nr = rx * ry, m = w - 1;
@@ -241,6 +252,28 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   //    dx > 0): (2w - 1) x region items of nearly equal cost, so the last
   //    round leaves few threads idle.
   auto row_terms = [&](const auto& term, const auto* src) {
+    if constexpr (NT >= NR) {
+      // one thread per region pixel: every offset is a compile-time constant
+      // and the pixel's own sample is loaded once.  A partner past the
+      // region's end reads the next shared array (its term is zeroed).
+      const int p = threadIdx.x;
+      if (p >= NR) return;
+      const int r = p / RX, c = p - r * RX;
+      const auto xp = load_sample(src + p);
+      auto one = [&](auto DX) {
+        constexpr int dx = decltype(DX)::value;
+        const bool col_in = c + dx >= 0 && c + dx < RX;
+#pragma unroll
+        for (int dy = 0; dy <= M; ++dy) {
+          if (dy == 0 && dx <= 0) continue;
+          float v = term(xp, load_sample(src + p + dy * RX + dx));
+          v = (col_in && r + dy < RY) ? v : 0.0f;
+          T[fwd_index<W>(dy, dx) * NR + p] = v;
+        }
+      };
+      static_for<-M, M>(one);
+      return;
+    }
     for (int item = threadIdx.x; item < (2 * M + 1) * NR; item += G::THREADS) {
       const int dxi = item / NR, p = item - dxi * NR;
       const int dx = dxi - M;
@@ -261,7 +294,7 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
     row_terms(TermL1{}, px);
   } else if constexpr (APX == kExact) {
-    row_terms(TermAngleExact{}, px);
+    row_terms(TermAngleExact(L.c.a), px);
   } else {
     row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b), px);
   }
@@ -398,7 +431,7 @@ __device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
     } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
       row_terms(TermL1{});
     } else if constexpr (APX == kExact) {
-      row_terms(TermAngleExact{});
+      row_terms(TermAngleExact(L.c.a));
     } else {
       row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b));
     }
@@ -519,7 +552,7 @@ __device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile
     } else if constexpr (CRIT == kAMNFE || CRIT == kAMNFG) {
       row_terms(TermL1{}, px);
     } else if constexpr (APX == kExact) {
-      row_terms(TermAngleExact{}, px);
+      row_terms(TermAngleExact(L.c.a), px);
     } else {
       row_terms(TermAngleApprox<DEG>(L.c.a, L.c.b), px);
     }

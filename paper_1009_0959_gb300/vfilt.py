@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libvfilt.so")
 CRITERIA = {"vmf": 0, "bvdf": 1, "amnfe": 2, "amnfg": 3, "evmf": 4, "evbdf": 5}
 APPROX = {"exact": 0, "poly": 1, "rational": 2, "rational_fit": 3}
 PRECISION = {"fp32": 0, "fp16x2": 1, "bf16x2": 2}
-FUNCTIONS = {"acos_lo": 0, "acos_hi": 1, "exp": 2, "ent": 3}
+FUNCTIONS = {"acos_lo": 0, "acos_hi": 1, "exp": 2, "ent": 3, "half_angle": 4}
 STATUS = {0: "VF_OK", 1: "VF_ERR_ARG", 2: "VF_ERR_ALIAS", 3: "VF_ERR_UNSUPPORTED",
           4: "VF_ERR_CUDA", 5: "VF_ERR_TIMEOUT", 6: "VF_ERR_OOM"}
 

@@ -209,3 +209,36 @@ def test_set_coefficients_errors(vf):
     # nothing was stored by the failed calls
     num, _, _ = vf.get_approximant("exp", "poly", 4, 0.0, 10.0)
     assert num[0] == pytest.approx(0.9666313, rel=1e-5)
+
+
+def test_half_angle_polynomial(vf):
+    """The exact angle's arctangent polynomial (VF_FN_HALF_ANGLE): the library's
+    degree-7 fit of 2 atan(sqrt s) / sqrt s on [0, 1], so that A = u P(u^2)
+    for u = tan(A/2) in [0, 1), reaches its minimax level (relative error
+    about 1.1e-7 of the angle) and agrees with the oracle's independent Remez
+    of the same function; the arctangent identity makes it exact on the
+    closed forms A(0) = 0, A(u = tan(pi/8)) = pi/4, A(u = 1) = pi/2."""
+    import math
+    import numpy as np
+    from oracle import remez as R
+    num, den, eps = vf.get_approximant("half_angle", "poly", 7, 0.0, 1.0)
+    assert den == [] and len(num) == 8
+    assert eps < 2e-7
+    P = np.polynomial.polynomial
+
+    def g(s):
+        s = np.asarray(s, dtype=np.float64)
+        r = np.sqrt(np.maximum(s, 1e-300))
+        return np.where(s > 0, 2 * np.arctan(r) / r, 2.0)
+
+    ref = R.remez(g, 0.0, 1.0, 7)
+    assert eps == pytest.approx(ref.eps, rel=1e-3)
+    u = np.linspace(0.0, 1.0, 100001)
+    ang = u * P.polyval(u * u, num)
+    exact = 2 * np.arctan(u)
+    rel = np.abs(ang - exact)[1:] / exact[1:]
+    assert rel.max() <= 1.2e-7
+    for uu, a in [(0.0, 0.0), (math.tan(math.pi / 8), math.pi / 4), (1.0, math.pi / 2)]:
+        assert uu * P.polyval(uu * uu, num) == pytest.approx(a, rel=1.2e-7, abs=1e-12)
+    with pytest.raises(vf.VFError):  # read-only
+        vf.set_coefficients("half_angle", "poly", 7, num, lo=0.0, hi=1.0)
