@@ -574,6 +574,17 @@ def bench_batch(reps=5):
 
     graph_ms = timed(lambda: b.graph_launch(stream))
     launch_ms = timed(lambda: b.launch(stream))
+    # both forms, whatever the autotuner kept
+    mode = tune["mode"]
+    forms = {}
+    for m in ("one_kernel", "class_kernels"):
+        if m == "one_kernel":
+            b.configure(tune["tile_rows"], tune["ctas_per_sm"],
+                        pixels_per_thread=tune["pixels_per_thread"])
+        else:
+            b.set_mode(m)
+        forms[m] = round(timed(lambda: b.graph_launch(stream)), 3)
+    b.set_mode(mode)
 
     def per_image():
         for inp, out, params in dev:
@@ -586,7 +597,8 @@ def bench_batch(reps=5):
             "mpix_s": round(mpix / graph_ms * 1e3, 1), "launch_ms": round(launch_ms, 3),
             "per_image_launches_ms": round(single_ms, 3),
             "speedup_vs_per_image": round(single_ms / graph_ms, 3), "autotune": tune,
-            "gpu_launches_per_run": 1}
+            "graph_ms_per_form": forms,
+            "gpu_launches_per_run": "1 graph (one kernel, or one kernel per image class)"}
 
 
 # sRGB (IEC 61966-2-1) primaries to CIE XYZ; the white of the L*a*b*

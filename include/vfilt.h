@@ -316,11 +316,13 @@ typedef struct vf_batch vf_batch;
  * Errors: those of vf_filter, VF_ERR_ARG for count < 1, VF_ERR_OOM. */
 vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf_batch** batch);
 
-/* Filter every image of the batch with ONE persistent kernel on `stream`:
- * SMs x CTAs-per-SM CTAs pull tiles from a device counter (reset by a memset
- * on the same stream) until the queue is empty.  Asynchronous; may be captured
- * into a CUDA graph by the caller.  Launches of one batch on different streams
- * must not overlap (they share the counter). */
+/* Filter every image of the batch on `stream`: with VF_BATCH_ONE_KERNEL (the
+ * default) ONE persistent kernel of SMs x CTAs-per-SM CTAs pulls tiles from a
+ * device counter (reset by a memset on the same stream) until the queue is
+ * empty; with VF_BATCH_CLASS_KERNELS one such kernel per image class on the
+ * batch's branch streams (see vf_batch_set_mode).  Asynchronous; may be
+ * captured into a CUDA graph by the caller.  Launches of one batch on
+ * different streams must not overlap (they share the counters). */
 vf_status vf_batch_launch(vf_batch* b, void* stream);
 
 /* The same launch as a CUDA graph (memset node + kernel node), instantiated
@@ -330,17 +332,18 @@ vf_status vf_batch_graph_launch(vf_batch* b, void* stream);
 
 /* Autotuner: times every tile shape (32 x TY thread rows, TY = 2, 4, 8) and
  * pixels-per-thread setting (see vf_batch_set_pixels_per_thread) with every
- * resident CTA count (1 .. occupancy maximum) on the batch itself (one
- * warm-up and three timed launches each, CUDA events on `stream`), keeps the
- * fastest and reports it (any out pointer may be NULL; the pixels per thread
- * through vf_batch_get_config).  Synchronous; writes the outputs (the same
- * values each time). */
+ * resident CTA count (1 .. occupancy maximum) on the batch itself, and the
+ * class-kernel form (vf_batch_set_mode) (one warm-up and three timed
+ * launches each, CUDA events on `stream`), keeps the fastest and reports it
+ * (any out pointer may be NULL; the pixels per thread through
+ * vf_batch_get_config, the form through vf_batch_get_mode).  Synchronous;
+ * writes the outputs (the same values each time). */
 vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas_per_sm,
                             float* best_ms);
 
-/* Set the configuration by hand: tile_rows 2, 4 or 8; ctas_per_sm 0 (the
- * occupancy maximum) up to that maximum.  Synchronous; not while a launch of
- * the batch is in flight. */
+/* Set the configuration of the one-kernel form by hand (and select that
+ * form): tile_rows 2, 4 or 8; ctas_per_sm 0 (the occupancy maximum) up to
+ * that maximum.  Synchronous; not while a launch of the batch is in flight. */
 vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm);
 
 /* Pixels per thread of the VMF and AMNF tiles with 3 x 3 and 5 x 5 windows:
@@ -348,9 +351,29 @@ vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm);
  * adjacent windows per thread sharing their common samples' pairs, 32 x 2TY
  * tiles), or 0 (the default: 2 for AMNF and 3 x 3 VMF, 1 for 5 x 5 VMF,
  * whose two-window body needs more registers than the shared kernel has).
- * Other images always take one window per thread.  Synchronous; not while a
- * launch of the batch is in flight. */
+ * Other images always take one window per thread.  Selects the one-kernel
+ * form.  Synchronous; not while a launch of the batch is in flight. */
 vf_status vf_batch_set_pixels_per_thread(vf_batch* b, int pixels_per_thread);
+
+/* Execution form of the batch:
+ *   VF_BATCH_ONE_KERNEL     one persistent kernel runs the tiles of every
+ *                           image (the default; configured by the calls above)
+ *   VF_BATCH_CLASS_KERNELS  one persistent kernel per image class (window x
+ *                           criterion x approximation), each with the tile
+ *                           shape, block size and shared memory of that
+ *                           class's single-image kernel (two windows per
+ *                           thread for VMF / AMNF, the tall pair-reuse tiles
+ *                           for BVDF, per-window tiles for EVMF); the class
+ *                           kernels run concurrently on the batch's own
+ *                           branch streams, forked from and joined to the
+ *                           caller's stream (one CUDA graph with
+ *                           vf_batch_graph_launch), costliest class first.
+ * vf_batch_autotune times both forms and keeps the faster.  Synchronous; not
+ * while a launch of the batch is in flight. */
+#define VF_BATCH_ONE_KERNEL 0
+#define VF_BATCH_CLASS_KERNELS 1
+vf_status vf_batch_set_mode(vf_batch* b, int mode);
+vf_status vf_batch_get_mode(const vf_batch* b, int* mode);
 
 /* The current configuration (any out pointer may be NULL). */
 vf_status vf_batch_get_config(const vf_batch* b, int* tile_rows, int* ctas_per_sm,

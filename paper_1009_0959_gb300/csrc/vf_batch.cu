@@ -18,6 +18,7 @@
 #include <new>
 #include <vector>
 
+#include "vf_batch_class.cuh"
 #include "vf_kernels.cuh"
 #include "vf_reuse.cuh"
 
@@ -36,12 +37,6 @@ __host__ __device__ constexpr int class_of(int w, int crit, int apx) {
   }
   return (w == 3 ? 0 : (w == 5 ? 1 : 2)) * kClassesPerWindow + k;
 }
-
-struct BatchImage {
-  Launch L;
-  int cls;
-  int two;  // 1: two windows per thread (tiles of 32 x 2TY outputs)
-};
 
 // Inside the batch kernel 3 x 3 keeps its aggregates in registers, and so
 // does the 5 x 5 AMNF (its integer city-block path needs about 64
@@ -174,8 +169,26 @@ static double pixel_cost(const LaunchClass& c) {
 
 using namespace vf;
 
+// One class of the class-kernel form: images [first, first + count) of the
+// class queue, its prefix array at begin_off, its counter, its tiles.
+struct BatchClass {
+  int w, crit, apx;
+  int first, count, begin_off, tiles;
+  double cost;  // estimated work (tiles x pixels x cost per pixel)
+};
+
+constexpr int kBatchBranches = 4;  // concurrent branches of the class-kernel form
+
 struct vf_batch {
   vf_ctx* ctx = nullptr;
+  int mode = VF_BATCH_ONE_KERNEL;
+  // class-kernel form: descriptors grouped by class, prefix arrays, counters
+  std::vector<BatchClass> classes;
+  BatchImage* d_cimgs = nullptr;
+  int* d_cbegin = nullptr;
+  unsigned int* d_ccounters = nullptr;
+  cudaStream_t branch[kBatchBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBatchBranches] = {};
   int device = 0, sms = 0;
   std::vector<BatchImage> host;  // queue order
   std::vector<double> cost;
@@ -257,7 +270,105 @@ int resident_ctas(const vf_batch* b, int ty) {
   return std::max(blocks, 1);
 }
 
+// Class-kernel form: group the images by class (window x criterion x
+// approximation), each class's images in the queue's cost order; tile counts
+// with the class's own tile rows.  Uploads the grouped descriptors and prefix
+// arrays (once, at creation).
+vf_status upload_classes(vf_batch* b) {
+  std::vector<int> order(b->count);
+  for (int i = 0; i < b->count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->host[x].cls < b->host[y].cls; });
+  std::vector<BatchImage> imgs;
+  std::vector<int> begin;
+  b->classes.clear();
+  for (int k = 0; k < b->count;) {
+    const int cls = b->host[order[k]].cls;
+    BatchClass c{};
+    c.w = class_window(cls);
+    c.crit = class_crit(cls);
+    const int kk = cls % kClassesPerWindow;
+    c.apx = c.crit == kVMF ? kExact
+            : c.crit == kBVDF ? (kk == 1 ? kExact : kPoly)
+                              : (kk - (c.crit == kAMNFE ? 3 : (c.crit == kAMNFG ? 6 : 9)));
+    c.first = (int)imgs.size();
+    c.begin_off = (int)begin.size();
+    const int rows = class_rows(c.w, c.crit);
+    long long tiles = 0;
+    double px = 0.0;
+    for (; k < b->count && b->host[order[k]].cls == cls; ++k) {
+      BatchImage im = b->host[order[k]];
+      im.L.tiles_x = (im.L.width + kTX - 1) / kTX;
+      begin.push_back((int)tiles);
+      tiles += (long long)im.L.tiles_x * ((im.L.height + rows - 1) / rows);
+      if (tiles > 0x7fffffffLL) return set_error(b->ctx, VF_ERR_UNSUPPORTED, "batch too large");
+      px += (double)im.L.width * im.L.height;
+      imgs.push_back(im);
+    }
+    begin.push_back((int)tiles);
+    c.count = (int)imgs.size() - c.first;
+    c.tiles = (int)tiles;
+    LaunchClass lc{c.crit, c.w, c.apx, 0, 0};
+    c.cost = px * pixel_cost(lc);
+    b->classes.push_back(c);
+  }
+  // costliest classes first: their kernels start first, the cheap ones fill
+  // the tail
+  std::stable_sort(b->classes.begin(), b->classes.end(),
+                   [](const BatchClass& x, const BatchClass& y) { return x.cost > y.cost; });
+  cudaError_t e = cudaMalloc(&b->d_cimgs, sizeof(BatchImage) * imgs.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_cbegin, sizeof(int) * begin.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ccounters, sizeof(unsigned int) * b->classes.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_cimgs, imgs.data(), sizeof(BatchImage) * imgs.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_cbegin, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < kBatchBranches && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(b->ctx, e == cudaErrorMemoryAllocation ? VF_ERR_OOM : VF_ERR_CUDA,
+                     cudaGetErrorString(e));
+  }
+  return VF_OK;
+}
+
+// Class-kernel form: reset the counters on s, fork the branches from s, the
+// class kernels on the branches (class i on branch i mod kBatchBranches, in
+// cost order), join them back into s.
+vf_status enqueue_classes(vf_batch* b, cudaStream_t s) {
+  const int nb = std::min<int>(kBatchBranches, (int)b->classes.size());
+  cudaError_t e =
+      cudaMemsetAsync(b->d_ccounters, 0, sizeof(unsigned int) * b->classes.size(), s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, s);
+  for (int i = 0; i < nb && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+  for (size_t i = 0; i < b->classes.size() && e == cudaSuccess; ++i) {
+    const BatchClass& c = b->classes[i];
+    cudaStream_t bs = b->branch[i % nb];
+    const BatchImage* imgs = b->d_cimgs + c.first;
+    const int* begin = b->d_cbegin + c.begin_off;
+    unsigned int* counter = b->d_ccounters + i;
+    e = c.w == 3   ? launch_class_w3(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs)
+        : c.w == 5 ? launch_class_w5(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs)
+                   : launch_class_w7(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs);
+  }
+  for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(b->join[i], b->branch[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(b->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return VF_OK;
+}
+
 vf_status enqueue(vf_batch* b, cudaStream_t s) {
+  if (b->mode == VF_BATCH_CLASS_KERNELS) return enqueue_classes(b, s);
   const int threads = kTX * b->ty;
   int per_sm = b->ctas_per_sm > 0 ? b->ctas_per_sm : resident_ctas(b, b->ty);
   const int grid = b->sms * per_sm;
@@ -319,6 +430,7 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
                      cudaGetErrorString(e));
   }
   vf_status st = upload(b, 4);
+  if (st == VF_OK) st = upload_classes(b);
   if (st != VF_OK) {
     vf_batch_destroy(b);
     return st;
@@ -400,12 +512,34 @@ vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas
       }
     }
   }
+  // the class-kernel form (no configuration of its own)
+  int best_mode = VF_BATCH_ONE_KERNEL;
+  if (st == VF_OK) {
+    b->mode = VF_BATCH_CLASS_KERNELS;
+    st = enqueue(b, s);  // warm-up
+    float ms_min = 1e30f;
+    for (int r = 0; r < 3 && st == VF_OK; ++r) {
+      cudaEventRecord(e0, s);
+      st = enqueue(b, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = set_error(b->ctx, VF_ERR_CUDA, "sync");
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_min = std::min(ms_min, ms);
+    }
+    if (st == VF_OK && ms_min < best) {
+      best = ms_min;
+      best_mode = VF_BATCH_CLASS_KERNELS;
+    }
+    b->mode = VF_BATCH_ONE_KERNEL;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->ppt = best_ppt;
   if (st != VF_OK) return st;
   st = upload(b, best_ty);
   b->ctas_per_sm = best_ctas;
+  b->mode = best_mode;
   drop_graph(b);
   if (tile_rows) *tile_rows = best_ty;
   if (ctas_per_sm) *ctas_per_sm = best_ctas;
@@ -421,6 +555,7 @@ vf_status vf_batch_configure(vf_batch* b, int tile_rows, int ctas_per_sm) {
     return set_error(b->ctx, VF_ERR_ARG, "more CTAs per SM than can be resident");
   vf_status st = upload(b, tile_rows);
   b->ctas_per_sm = ctas_per_sm;
+  b->mode = VF_BATCH_ONE_KERNEL;  // a configuration of the one-kernel form selects it
   drop_graph(b);
   return st;
 }
@@ -431,8 +566,24 @@ vf_status vf_batch_set_pixels_per_thread(vf_batch* b, int pixels_per_thread) {
     return set_error(b->ctx, VF_ERR_ARG, "pixels per thread must be 0, 1 or 2");
   b->ppt = pixels_per_thread;
   vf_status st = upload(b, b->ty);
+  b->mode = VF_BATCH_ONE_KERNEL;
   drop_graph(b);
   return st;
+}
+
+vf_status vf_batch_set_mode(vf_batch* b, int mode) {
+  if (!b) return VF_ERR_ARG;
+  if (mode != VF_BATCH_ONE_KERNEL && mode != VF_BATCH_CLASS_KERNELS)
+    return set_error(b->ctx, VF_ERR_ARG, "mode must be VF_BATCH_ONE_KERNEL or VF_BATCH_CLASS_KERNELS");
+  b->mode = mode;
+  drop_graph(b);
+  return VF_OK;
+}
+
+vf_status vf_batch_get_mode(const vf_batch* b, int* mode) {
+  if (!b || !mode) return VF_ERR_ARG;
+  *mode = b->mode;
+  return VF_OK;
 }
 
 vf_status vf_batch_get_config(const vf_batch* b, int* tile_rows, int* ctas_per_sm,
@@ -451,6 +602,17 @@ void vf_batch_destroy(vf_batch* b) {
   if (b->d_imgs) cudaFree(b->d_imgs);
   if (b->d_begin) cudaFree(b->d_begin);
   if (b->d_counter) cudaFree(b->d_counter);
+  for (int i = 0; i < kBatchBranches; ++i) {
+    if (b->branch[i]) {
+      cudaStreamSynchronize(b->branch[i]);
+      cudaStreamDestroy(b->branch[i]);
+    }
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->d_cimgs) cudaFree(b->d_cimgs);
+  if (b->d_cbegin) cudaFree(b->d_cbegin);
+  if (b->d_ccounters) cudaFree(b->d_ccounters);
   delete b;
 }
 

@@ -108,6 +108,10 @@ def lib():
             L.vf_batch_get_config.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I),
                                               ctypes.POINTER(I)]
             L.vf_batch_get_config.restype = I
+            L.vf_batch_set_mode.argtypes = [P, I]
+            L.vf_batch_set_mode.restype = I
+            L.vf_batch_get_mode.argtypes = [P, ctypes.POINTER(I)]
+            L.vf_batch_get_mode.restype = I
             L.vf_batch_destroy.argtypes = [P]
             L.vf_batch_destroy.restype = None
             L.vf_batch_run_static.argtypes = [P, P, I, P]
@@ -312,12 +316,23 @@ class Batch:
                    self.ctx)
         _check(lib().vf_batch_configure(self.handle, int(tile_rows), int(ctas_per_sm)), self.ctx)
 
+    MODES = {"one_kernel": 0, "class_kernels": 1}
+
+    def set_mode(self, mode):
+        """vf_batch_set_mode: "one_kernel" (one persistent kernel for every
+        class) or "class_kernels" (one persistent kernel per class, run
+        concurrently)."""
+        _check(lib().vf_batch_set_mode(self.handle, self.MODES[mode]), self.ctx)
+
     def config(self):
-        """tile_rows, ctas_per_sm (0: occupancy maximum) and pixels_per_thread."""
-        ty, ctas, ppt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        """mode, tile_rows, ctas_per_sm (0: occupancy maximum) and
+        pixels_per_thread (the last three apply to the one-kernel form)."""
+        ty, ctas, ppt, mode = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().vf_batch_get_config(self.handle, ctypes.byref(ty), ctypes.byref(ctas),
                                          ctypes.byref(ppt)), self.ctx)
-        return {"tile_rows": ty.value, "ctas_per_sm": ctas.value,
+        _check(lib().vf_batch_get_mode(self.handle, ctypes.byref(mode)), self.ctx)
+        names = {v: k for k, v in self.MODES.items()}
+        return {"mode": names[mode.value], "tile_rows": ty.value, "ctas_per_sm": ctas.value,
                 "pixels_per_thread": ppt.value}
 
     def close(self):

@@ -89,11 +89,13 @@ def test_batch_graph_autotune_identical(vf):
     cfg = b.autotune()
     assert cfg["tile_rows"] in (2, 4, 8) and cfg["ctas_per_sm"] >= 1 and cfg["ms"] > 0
     assert cfg["pixels_per_thread"] in (0, 1, 2)
+    assert cfg["mode"] in ("one_kernel", "class_kernels")
     run_and_check()
     for ty in (2, 8):
         for ppt in (0, 1, 2):
             b.configure(ty, 1, pixels_per_thread=ppt)
-            assert b.config() == {"tile_rows": ty, "ctas_per_sm": 1, "pixels_per_thread": ppt}
+            assert b.config() == {"mode": "one_kernel", "tile_rows": ty, "ctas_per_sm": 1,
+                                  "pixels_per_thread": ppt}
             run_and_check()
     with pytest.raises(vf.VFError):
         b.configure(4, 0, pixels_per_thread=3)
@@ -131,3 +133,49 @@ def test_batch_errors(vf):
     with pytest.raises(vf.VFError):
         b.configure(3, 1)
     b.close()
+
+
+def test_batch_class_kernels(vf):
+    """The class-kernel form (one persistent kernel per class, concurrent
+    branches): every image meets the oracle parity bar; plain and graph
+    launches give the same bytes; VMF, AMNF and BVDF images (the single-image
+    kernels' bodies and tile shapes) equal the single-image call byte for
+    byte."""
+    items = make_batch(40, 4, lo=(1, 1), hi=(150, 230))
+    dev = to_dev(items)
+    b = vf.Batch(dev)
+    b.set_mode("class_kernels")
+    assert b.config()["mode"] == "class_kernels"
+    b.launch()
+    torch.cuda.synchronize()
+    first = [o.clone() for _, o, _ in dev]
+    for _, o, _ in dev:
+        o.zero_()
+    b.graph_launch()
+    b.graph_launch()
+    torch.cuda.synchronize()
+    for (noisy, p), (inp, o, _), f in zip(items, dev, first):
+        assert torch.equal(f, o)
+        ro, rd = F.filter_image(noisy, F.Config(p["criterion"], p["window"], p["approx"],
+                                                p["degree"]))
+        check(p["criterion"], ro, rd, o.cpu().numpy())
+        if p["criterion"] != "evmf":
+            single = vf.filter(inp, **p)
+            torch.cuda.synchronize()
+            assert torch.equal(single, o), p
+    b.set_mode("one_kernel")
+    b.launch()
+    torch.cuda.synchronize()
+    for (noisy, p), (_, o, _) in zip(items, dev):
+        ro, rd = F.filter_image(noisy, F.Config(p["criterion"], p["window"], p["approx"],
+                                                p["degree"]))
+        check(p["criterion"], ro, rd, o.cpu().numpy())
+    with pytest.raises(vf.VFError):
+        lib_set_mode(vf, b, 7)  # no such form
+    b.close()
+
+
+def lib_set_mode(vf, b, mode):
+    st = vf.lib().vf_batch_set_mode(b.handle, mode)
+    if st != 0:
+        raise vf.VFError(st, "bad mode")

@@ -51,15 +51,22 @@ def image():
 
 
 def _oracle_rows(noisy, cfg, rows):
+    """The oracle on the sampled rows: each band of six rows is filtered as a
+    crop holding the band and the window's halo rows (the crop's own border
+    rows coincide with the image's at the top and bottom bands), with all
+    host threads."""
     out = np.zeros((len(rows), N, 3), np.uint8)
     gap = np.zeros((len(rows), N))
     k = 0
+    h = cfg.window // 2
     for r0 in (0, 1360, 2730, N - 6):
-        o, d = F.filter_image(noisy, cfg, threads=os.cpu_count() or 1, rows=(r0, r0 + 6))
-        out[k:k + 6] = o[r0:r0 + 6, :, :3]
-        g = d["gap"][r0:r0 + 6]
+        a, b = max(0, r0 - h), min(N, r0 + 6 + h)
+        o, d = F.filter_image(noisy[a:b], cfg, threads=os.cpu_count() or 1)
+        sl = slice(r0 - a, r0 - a + 6)
+        out[k:k + 6] = o[sl, :, :3]
+        g = d["gap"][sl]
         if cfg.criterion in ("amnfe", "amnfg"):
-            y = d["yreal"][r0:r0 + 6]
+            y = d["yreal"][sl]
             g = np.abs(y - np.floor(y) - 0.5).min(-1)  # distance to a rounding boundary
         gap[k:k + 6] = g
         k += 6
