@@ -14,6 +14,7 @@
 // class overlaps the next.
 #pragma once
 
+#include "vf_evmf.cuh"
 #include "vf_kernels.cuh"
 #include "vf_reuse.cuh"
 
@@ -26,24 +27,138 @@ struct BatchImage {
 };
 
 // Body of a class: 0 two windows per thread (VMF, AMNFE, AMNFG), 1 the tall
-// pair-reuse tiles (BVDF), 2 per-window tiles with compaction (EVMF).
-constexpr int class_body(int crit) { return crit == kBVDF ? 1 : (crit == kEVMF ? 2 : 0); }
+// pair-reuse tiles (BVDF), 2 per-window tiles with compaction (EVMF 3 x 3
+// and 7 x 7), 3 the EVMF work queue (EVMF 5 x 5), as the single-image
+// launches choose them.
+constexpr int class_body(int w, int crit) {
+  return crit == kBVDF ? 1 : (crit == kEVMF ? (w == 5 ? 3 : 2) : 0);
+}
 // Thread rows of the two-window and per-window bodies (32 x 4 threads).
 constexpr int kClassTY = 4;
 // Output rows of one tile of a class.
 constexpr int class_rows(int w, int crit) {
-  return class_body(crit) == 1 ? reuse_tile_rows(w, kBVDF)
-                               : (class_body(crit) == 0 ? 2 * kClassTY : kClassTY);
+  return class_body(w, crit) == 1   ? reuse_tile_rows(w, kBVDF)
+         : class_body(w, crit) == 0 ? 2 * kClassTY
+         : class_body(w, crit) == 3 ? evmf_queue_rows(w)
+                                    : kClassTY;
 }
 constexpr int class_threads(int w, int crit) {
-  return class_body(crit) == 1 ? reuse_threads(w, reuse_tile_rows(w, kBVDF)) : kTX * kClassTY;
+  return class_body(w, crit) == 1   ? reuse_threads(w, reuse_tile_rows(w, kBVDF))
+         : class_body(w, crit) == 3 ? kTX * evmf_queue_rows(w)
+                                    : kTX * kClassTY;
 }
 inline size_t class_kernel_smem(int w, int crit) {
-  switch (class_body(crit)) {
+  switch (class_body(w, crit)) {
     case 0: return smem_bytes(w, crit, 2 * kClassTY);
     case 1: return reuse_any_smem_bytes(w, reuse_tile_rows(w, kBVDF));
+    case 3: return evmf_queue_smem_bytes(w, evmf_queue_rows(w));
     default: return smem_bytes(w, crit, kClassTY);
   }
+}
+
+// Output pixel reference of a queued window: its byte address with the store
+// form in bits 62-63 (0 one 32-bit store, 1 three bytes, 2 four bytes), so
+// that a queue entry outlives the tile (and the image) it came from.
+__device__ __forceinline__ unsigned long long out_ref(const Launch& L, int gx, int gy) {
+  const uint8_t* p = L.out + (long long)gy * L.out_pitch + (long long)gx * L.channels;
+  const unsigned long long form = L.vec4_out ? 0ull : (L.channels == 4 ? 2ull : 1ull);
+  return reinterpret_cast<unsigned long long>(p) | (form << 62);
+}
+__device__ __forceinline__ void store_ref(unsigned long long r, uint32_t v) {
+  uint8_t* p = reinterpret_cast<uint8_t*>(r & ((1ull << 62) - 1ull));
+  const unsigned form = (unsigned)(r >> 62);
+  if (form == 0) {
+    *reinterpret_cast<uint32_t*>(p) = v;
+    return;
+  }
+  p[0] = (uint8_t)v;
+  p[1] = (uint8_t)(v >> 8);
+  p[2] = (uint8_t)(v >> 16);
+  if (form == 2) p[3] = (uint8_t)(v >> 24);
+}
+
+// The EVMF work queue (evmf_queue_kernel, vf_evmf.cuh) over the tiles of
+// every image of the class: each tile comes from the class counter (its
+// image's descriptor staged in shared memory), and a queued window carries
+// its output address instead of coordinates, so windows of different images
+// share the queue and its full-warp batches.
+template <int W, int APX, int DEG, bool REG = uses_reg_path(W, kEVMF)>
+__global__ void __launch_bounds__(256, 3)
+    evmf_class_kernel(const BatchImage* __restrict__ imgs, const int* __restrict__ begin,
+                      int count, unsigned int* counter) {
+  constexpr int N = W * W, R = W / 2;
+  const int T = blockDim.x, TY = T / kTX, CAP = 2 * T;
+  const TileSmem t = carve(W, REG, TY, T);
+  unsigned long long* qdst = reinterpret_cast<unsigned long long*>(t.list);  // CAP outputs
+  uint32_t* qwin = reinterpret_cast<uint32_t*>(qdst + CAP);                  // CAP x N pixels
+  __shared__ int s_tail, s_item;
+  __shared__ Launch s_L;
+  if (threadIdx.x == 0) s_tail = 0;
+  const int lane = threadIdx.x & 31;
+  const int px = threadIdx.x % kTX, py = threadIdx.x / kTX;
+  float* sagg = t.agg + threadIdx.x;
+  const int total = begin[count];
+  int head = 0;  // same value in every thread
+
+  auto median = [&](int e) {
+    const int slot = e % CAP;
+    const uint32_t* win = qwin + (size_t)slot * N;
+    const Selection s = window_select<W, REG>(win, W, 0, 0, TermL2U8{}, sagg, T, false);
+    store_ref(qdst[slot], win[s.best]);
+  };
+
+  for (;;) {
+    __syncthreads();  // staged pixels, s_L and s_item of the previous tile are done
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    int lo = 0, hi = count - 1;  // largest i with begin[i] <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (begin[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const int tile = item - begin[lo];
+    if (threadIdx.x < 32) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&imgs[lo].L);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_L);
+      for (int k = threadIdx.x; k < (int)(sizeof(Launch) / 4); k += 32) dst[k] = src[k];
+    }
+    __syncthreads();
+    const Launch& L = s_L;
+    const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+    const int x0 = txi * kTX, y0 = tyi * TY;
+    stage_tile<kEVMF>(L, t, x0, y0, R);
+    __syncthreads();
+    const int gx = x0 + px, gy = y0 + py;
+    const bool valid = gx < L.width && gy < L.height;
+    bool tie = false;
+    const bool sw = valid && evmf_switch<W, APX, DEG>(L, t, px, py, tie);
+    if (valid && !sw) store_px(L, gx, gy, t.raw[(py + R) * t.sw + px + R]);
+    // warp-aggregated append: consecutive slots for a warp's switched pixels
+    const unsigned m = __ballot_sync(0xffffffffu, sw);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(&s_tail, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (sw) {
+      const int slot = (base + __popc(m & ((1u << lane) - 1u))) % CAP;
+      uint32_t* dst = qwin + (size_t)slot * N;
+#pragma unroll
+      for (int a = 0; a < W; ++a)
+#pragma unroll
+        for (int i = 0; i < W; ++i) dst[a * W + i] = t.raw[(py + a) * t.sw + px + i];
+      qdst[slot] = out_ref(L, gx, gy);
+    }
+    __syncthreads();
+    const int tail = s_tail;
+    if (tail - head >= T) {  // uniform: every thread read the same tail
+      median(head + (int)threadIdx.x);
+      head += T;
+    }
+  }
+  __syncthreads();
+  const int tail = s_tail;
+  if ((int)threadIdx.x < tail - head) median(head + (int)threadIdx.x);
 }
 
 // begin[i] = first tile of the class's image i, begin[count] = its tiles.
@@ -73,9 +188,9 @@ __global__ void __launch_bounds__(class_threads(W, CRIT))
       for (int k = threadIdx.x; k < (int)(sizeof(Launch) / 4); k += 32) dst[k] = src[k];
     }
     __syncthreads();
-    if constexpr (class_body(CRIT) == 0) {
+    if constexpr (class_body(W, CRIT) == 0) {
       process_tile2<W, CRIT, APX, DEG>(s_L, tile);
-    } else if constexpr (class_body(CRIT) == 1) {
+    } else if constexpr (class_body(W, CRIT) == 1) {
       constexpr int RTY = reuse_tile_rows(W, kBVDF);
       reuse_any_tile<W, kBVDF, APX, DEG, RTY, reuse_threads(W, RTY)>(s_L, tile);
     } else {
@@ -90,7 +205,9 @@ __global__ void __launch_bounds__(class_threads(W, CRIT))
 template <int W, int CRIT, int APX, int DEG>
 cudaError_t launch_class_one(const BatchImage* imgs, const int* begin, int count,
                              unsigned int* counter, int tiles, cudaStream_t s) {
-  auto kern = class_kernel<W, CRIT, APX, DEG>;
+  void (*kern)(const BatchImage*, const int*, int, unsigned int*);
+  if constexpr (class_body(W, CRIT) == 3) kern = evmf_class_kernel<W, APX, DEG>;
+  else kern = class_kernel<W, CRIT, APX, DEG>;
   const size_t smem = class_kernel_smem(W, CRIT);
   const int threads = class_threads(W, CRIT);
   cudaError_t e = cudaSuccess;
