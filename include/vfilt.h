@@ -363,13 +363,17 @@ vf_status vf_batch_set_pixels_per_thread(vf_batch* b, int pixels_per_thread);
  *                           shape, block size and shared memory of that
  *                           class's single-image kernel (two windows per
  *                           thread for VMF / AMNF, the tall pair-reuse tiles
- *                           for BVDF, per-window tiles for EVMF); the class
- *                           kernels run concurrently on the batch's own
+ *                           for BVDF, the work queue for EVMF 5 x 5 and
+ *                           per-window tiles for the other EVMF windows), or,
+ *                           for a class where that is faster, one
+ *                           single-image launch per image (BVDF by default);
+ *                           the classes run concurrently on the batch's own
  *                           branch streams, forked from and joined to the
  *                           caller's stream (one CUDA graph with
  *                           vf_batch_graph_launch), costliest class first.
- * vf_batch_autotune times both forms and keeps the faster.  Synchronous; not
- * while a launch of the batch is in flight. */
+ * vf_batch_autotune times, per class, its class kernel against its
+ * single-image launches and keeps the faster, then times both forms and keeps
+ * the faster.  Synchronous; not while a launch of the batch is in flight. */
 #define VF_BATCH_ONE_KERNEL 0
 #define VF_BATCH_CLASS_KERNELS 1
 vf_status vf_batch_set_mode(vf_batch* b, int mode);

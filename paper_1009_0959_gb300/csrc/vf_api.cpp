@@ -486,7 +486,15 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
   vf_status st = prepare_launch(ctx, d_in, d_out, height, width, channels, in_pitch, out_pitch, p,
                                 d_stats, &L, &cls);
   if (st != VF_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+  return launch_single(ctx, L, cls, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace vf {
+
+vf_status launch_single(vf_ctx* ctx, Launch L, const LaunchClass& cls, cudaStream_t s) {
+  const int height = L.height, width = L.width;
   if (cls.precision == VF_FP32 && use_pair_reuse(ctx, cls.w, cls.crit)) {
     L.tiles_x = (width + kTX - 1) / kTX;
     const int rows = reuse_tile_rows(cls.w, cls.crit);
@@ -510,6 +518,10 @@ vf_status vf_filter(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height
   if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
   return VF_OK;
 }
+
+}  // namespace vf
+
+extern "C" {
 
 vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height, int width,
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,

@@ -174,7 +174,8 @@ using namespace vf;
 struct BatchClass {
   int w, crit, apx;
   int first, count, begin_off, tiles;
-  double cost;  // estimated work (tiles x pixels x cost per pixel)
+  double cost;    // estimated work (tiles x pixels x cost per pixel)
+  int per_image;  // 1: the class's images go as single-image launches instead
 };
 
 constexpr int kBatchBranches = 4;  // concurrent branches of the class-kernel form
@@ -191,6 +192,8 @@ struct vf_batch {
   cudaEvent_t fork = nullptr, join[kBatchBranches] = {};
   int device = 0, sms = 0;
   std::vector<BatchImage> host;  // queue order
+  std::vector<LaunchClass> host_cls;  // the images' kernel classes, queue order
+  std::vector<int> cls_img;           // class-kernel form: host index of each grouped image
   std::vector<double> cost;
   BatchImage* d_imgs = nullptr;
   int* d_begin = nullptr;
@@ -277,6 +280,7 @@ int resident_ctas(const vf_batch* b, int ty) {
 vf_status upload_classes(vf_batch* b) {
   std::vector<int> order(b->count);
   for (int i = 0; i < b->count; ++i) order[i] = i;
+  b->cls_img.clear();
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return b->host[x].cls < b->host[y].cls; });
   std::vector<BatchImage> imgs;
@@ -298,6 +302,7 @@ vf_status upload_classes(vf_batch* b) {
     double px = 0.0;
     for (; k < b->count && b->host[order[k]].cls == cls; ++k) {
       BatchImage im = b->host[order[k]];
+      b->cls_img.push_back(order[k]);
       im.L.tiles_x = (im.L.width + kTX - 1) / kTX;
       begin.push_back((int)tiles);
       tiles += (long long)im.L.tiles_x * ((im.L.height + rows - 1) / rows);
@@ -310,6 +315,11 @@ vf_status upload_classes(vf_batch* b) {
     c.tiles = (int)tiles;
     LaunchClass lc{c.crit, c.w, c.apx, 0, 0};
     c.cost = px * pixel_cost(lc);
+    // BVDF keeps one launch per image by default: its tall tiles take a whole
+    // SM each, and the single-image kernel reads the approximant as
+    // constant-bank operands where the class kernel reads the staged
+    // descriptor (vf_batch_autotune decides per class by timing)
+    c.per_image = c.crit == kBVDF;
     b->classes.push_back(c);
   }
   // costliest classes first: their kernels start first, the cheap ones fill
@@ -340,22 +350,34 @@ vf_status upload_classes(vf_batch* b) {
 // Class-kernel form: reset the counters on s, fork the branches from s, the
 // class kernels on the branches (class i on branch i mod kBatchBranches, in
 // cost order), join them back into s.
+// One class on stream bs: its class kernel (its counter reset first), or one
+// single-image launch per image.
+cudaError_t enqueue_one_class(vf_batch* b, size_t i, cudaStream_t bs) {
+  const BatchClass& c = b->classes[i];
+  if (c.per_image) {
+    for (int k = 0; k < c.count; ++k) {
+      const int h = b->cls_img[c.first + k];
+      if (launch_single(b->ctx, b->host[h].L, b->host_cls[h], bs) != VF_OK)
+        return cudaErrorLaunchFailure;
+    }
+    return cudaSuccess;
+  }
+  const BatchImage* imgs = b->d_cimgs + c.first;
+  const int* begin = b->d_cbegin + c.begin_off;
+  unsigned int* counter = b->d_ccounters + i;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), bs);
+  if (e != cudaSuccess) return e;
+  return c.w == 3   ? launch_class_w3(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs)
+         : c.w == 5 ? launch_class_w5(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs)
+                    : launch_class_w7(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs);
+}
+
 vf_status enqueue_classes(vf_batch* b, cudaStream_t s) {
   const int nb = std::min<int>(kBatchBranches, (int)b->classes.size());
-  cudaError_t e =
-      cudaMemsetAsync(b->d_ccounters, 0, sizeof(unsigned int) * b->classes.size(), s);
-  if (e == cudaSuccess) e = cudaEventRecord(b->fork, s);
+  cudaError_t e = cudaEventRecord(b->fork, s);
   for (int i = 0; i < nb && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-  for (size_t i = 0; i < b->classes.size() && e == cudaSuccess; ++i) {
-    const BatchClass& c = b->classes[i];
-    cudaStream_t bs = b->branch[i % nb];
-    const BatchImage* imgs = b->d_cimgs + c.first;
-    const int* begin = b->d_cbegin + c.begin_off;
-    unsigned int* counter = b->d_ccounters + i;
-    e = c.w == 3   ? launch_class_w3(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs)
-        : c.w == 5 ? launch_class_w5(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs)
-                   : launch_class_w7(c.crit, c.apx, imgs, begin, c.count, counter, c.tiles, bs);
-  }
+  for (size_t i = 0; i < b->classes.size() && e == cudaSuccess; ++i)
+    e = enqueue_one_class(b, i, b->branch[i % nb]);
   for (int i = 0; i < nb && e == cudaSuccess; ++i) {
     e = cudaEventRecord(b->join[i], b->branch[i]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
@@ -399,6 +421,7 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
   b->count = count;
   std::vector<std::pair<double, int>> order;
   std::vector<BatchImage> imgs(count);
+  std::vector<LaunchClass> lcls(count);
   for (int i = 0; i < count; ++i) {
     const vf_image_desc& d = descs[i];
     LaunchClass c;
@@ -413,10 +436,14 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
       return st;
     }
     imgs[i].cls = class_of(c.w, c.crit, c.apx);
+    lcls[i] = c;
     order.push_back({-pixel_cost(c), i});
   }
   std::stable_sort(order.begin(), order.end());
-  for (auto& o : order) b->host.push_back(imgs[o.second]);
+  for (auto& o : order) {
+    b->host.push_back(imgs[o.second]);
+    b->host_cls.push_back(lcls[o.second]);
+  }
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -512,8 +539,26 @@ vf_status vf_batch_autotune(vf_batch* b, void* stream, int* tile_rows, int* ctas
       }
     }
   }
-  // the class-kernel form (no configuration of its own)
+  // the class-kernel form: per class, its class kernel or one launch per
+  // image, whichever is faster alone; then the whole form
   int best_mode = VF_BATCH_ONE_KERNEL;
+  for (size_t i = 0; i < b->classes.size() && st == VF_OK; ++i) {
+    float t[2] = {1e30f, 1e30f};
+    for (int form = 0; form < 2 && st == VF_OK; ++form) {
+      b->classes[i].per_image = form;
+      if (enqueue_one_class(b, i, s) != cudaSuccess) st = set_error(b->ctx, VF_ERR_CUDA, "launch");
+      for (int r = 0; r < 3 && st == VF_OK; ++r) {
+        cudaEventRecord(e0, s);
+        if (enqueue_one_class(b, i, s) != cudaSuccess) st = set_error(b->ctx, VF_ERR_CUDA, "launch");
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = set_error(b->ctx, VF_ERR_CUDA, "sync");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t[form] = std::min(t[form], ms);
+      }
+    }
+    b->classes[i].per_image = t[1] < t[0];
+  }
   if (st == VF_OK) {
     b->mode = VF_BATCH_CLASS_KERNELS;
     st = enqueue(b, s);  // warm-up

@@ -162,6 +162,10 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
                          unsigned long long* d_stats, Launch* out, LaunchClass* cls);
 
+// The launch of vf_filter for a prepared image: the pair-reuse, per-window or
+// packed kernel the context's options select, on stream s.
+vf_status launch_single(vf_ctx* ctx, Launch L, const LaunchClass& cls, cudaStream_t s);
+
 // Whether the gate inference runs on the tensor cores (context option).
 bool gate_tensor_cores(const vf_ctx* ctx);
 
