@@ -141,10 +141,14 @@ const char* vf_last_error(const vf_ctx* ctx);
  *                      (default) or 8 (32 x TY outputs; 32 x 2TY for VMF
  *                      and AMNF with w <= 5, whose threads filter two
  *                      windows; the EVMF work-queue kernel picks its own).
- *   VF_OPT_GATE_TENSOR_CORES  1 (default): vf_gate_infer runs the three
- *                      convolutions on the tensor cores (mma, BF16 operands:
- *                      activations rounded to BF16 between layers, FP32
- *                      accumulation); 0: CUDA cores with FP32 activations.
+ *   VF_OPT_GATE_TENSOR_CORES  the engine of vf_gate_infer: 1 (default) the
+ *                      three convolutions on the 5th-generation tensor cores
+ *                      (tcgen05 MMAs with TMEM accumulators, one per 3 x 3
+ *                      tap over rows of 128 cells); 2 the warp-level mma
+ *                      instructions of earlier tensor cores; both with BF16
+ *                      operands (activations rounded to BF16 between layers)
+ *                      and FP32 accumulation; 0: CUDA cores with FP32
+ *                      activations.
  *   VF_OPT_OVERLAP_LAUNCH  1 (default): vf_filter's kernels are launched as
  *                      programmatic dependents of the previous kernel in the
  *                      stream: their CTAs may be scheduled while that kernel
@@ -493,6 +497,12 @@ vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int 
 vf_status vf_gate_save(vf_gate* g, const char* path);
 vf_status vf_gate_load(vf_gate* g, const char* path);
 unsigned long long vf_gate_step_count(const vf_gate* g);
+/* Whether every tensor-core inference since the last check completed: the
+ * tcgen05 engine waits for its MMAs with a bounded wait (about a second);
+ * if one gave up, that launch skipped its remaining tiles and set a flag in
+ * the gate.  Waits for the device (synchronous), returns VF_ERR_TIMEOUT (and
+ * clears the flag) if a wait gave up, else VF_OK. */
+vf_status vf_gate_check(vf_gate* g);
 void vf_gate_destroy(vf_gate* g);
 
 #ifdef __cplusplus

@@ -56,7 +56,7 @@ struct vf_ctx {
   std::string last_error;
   int tile_rows = 4;  // TY of the per-window single-image launches
   int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF, EVBDF), 2 always
-  int gate_tc = 1;     // gate inference on the tensor cores (BF16 activations)
+  int gate_tc = 1;     // gate inference: 0 CUDA cores, 1 tcgen05, 2 warp-level mma
   int overlap = 1;     // programmatic dependent launches for vf_filter
   // device staging of vf_filter_host (grown on demand, freed by vf_destroy)
   uint8_t* d_stage = nullptr;
@@ -167,7 +167,10 @@ vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value) {
       if (value < 0 || value > 2) return fail(ctx, VF_ERR_ARG, "pair reuse 0, 1 or 2");
       ctx->pair_reuse = value;
       return VF_OK;
-    case VF_OPT_GATE_TENSOR_CORES: ctx->gate_tc = value != 0; return VF_OK;
+    case VF_OPT_GATE_TENSOR_CORES:
+      if (value < 0 || value > 2) return fail(ctx, VF_ERR_ARG, "gate tensor cores 0, 1 or 2");
+      ctx->gate_tc = value;
+      return VF_OK;
     case VF_OPT_OVERLAP_LAUNCH: ctx->overlap = value != 0; return VF_OK;
     case VF_OPT_TILE_ROWS:
       if (value != 2 && value != 4 && value != 8) return fail(ctx, VF_ERR_ARG, "tile rows 2, 4 or 8");
@@ -442,7 +445,7 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
 
 vf_status set_error(vf_ctx* ctx, vf_status s, const char* msg) { return fail(ctx, s, msg); }
 
-bool gate_tensor_cores(const vf_ctx* ctx) { return ctx->gate_tc != 0; }
+int gate_tensor_cores(const vf_ctx* ctx) { return ctx->gate_tc; }
 
 bool use_pair_reuse(const vf_ctx* ctx, int w, int crit) {
   return ctx->pair_reuse == 2 ? has_reuse_kernel(w, crit)

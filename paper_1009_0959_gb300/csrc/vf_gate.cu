@@ -13,6 +13,7 @@
 // point atomics), so training is bit-reproducible and resumable.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -585,6 +586,290 @@ __global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv
   }
 }
 
+// ---- fused inference on the 5th-generation tensor cores (tcgen05): every
+// layer is an implicit GEMM over rows of 128 cells, M = 128 cells x N = 16
+// output channels x K = 16, one MMA per 3 x 3 tap (layer 1: per pair of tap
+// rows), accumulating in tensor memory (TMEM); BF16 operands staged in shared
+// memory in the K-major, unswizzled core-matrix layout, FP32 accumulation.
+// A tap's shifted rows are the same planar activations read from a start
+// address 16 bytes per cell further on, so no operand is ever gathered:
+//   x0  [row][130 cells][8 channels: R, G, B, 0 ...]          (16 B per cell)
+//   a1, a2  two such planes per layer (channels 0-7, 8-15)
+// and the A descriptor of a tap is its start cell, with the next K half one
+// plane further on (layer 1: one row further on, so that one MMA covers two
+// tap rows; the third tap row is paired with a zero weight row).  One thread
+// issues the MMAs of a layer and commits them to an mbarrier; after the
+// (bounded) wait, all eight warps read the accumulators back with tcgen05.ld
+// (warp w: TMEM lanes 32 (w mod 4) .. + 31, every other layer row), add the
+// bias, apply ReLU, round to BF16 and write the next layer's planes, or, for
+// layer 3, the logit's flag and probability.  Outputs per CTA tile: 124 x 6
+// (the 128-cell rows shrink by 2 cells per 3 x 3 layer); two CTAs per SM,
+// persistent over the tiles.  Numerics as gate_infer_tc: BF16 input and
+// activations between layers, BF16 weights, FP32 accumulation and biases.
+constexpr int G5_X = 124, G5_Y = 6;                    // outputs per tile
+constexpr int G5_CW = 130;                             // cells per staged row
+constexpr int G5_RP = G5_CW * 16;                      // bytes per staged row
+constexpr int G5_R0 = G5_Y + 7, G5_R1 = G5_Y + 4, G5_R2 = G5_Y + 2;  // rows of x0, a1, a2
+constexpr int G5_A1P = G5_R1 * G5_RP, G5_A2P = G5_R2 * G5_RP;      // plane bytes
+constexpr int G5_BM = 512;                             // one 16 x 16 BF16 B operand
+constexpr int G5_OFF_B = 0;                            // 6 + 9 + 9 B operands
+constexpr int G5_OFF_BIAS = G5_OFF_B + 24 * G5_BM;
+constexpr int G5_OFF_X0 = G5_OFF_BIAS + 256;           // x0, later a2 (x0 is dead by then)
+constexpr int G5_OFF_A1 = G5_OFF_X0 + 2 * G5_A2P;
+constexpr int G5_SMEM = G5_OFF_A1 + 2 * G5_A1P;
+constexpr int G5_THREADS = 256;
+constexpr int G5_TMEM_COLS = 256;                      // >= 16 columns x 10 layer-1 rows
+static_assert(G5_R0 * G5_RP <= 2 * G5_A2P, "x0 fits in the a2 planes it shares");
+static_assert(G5_SMEM <= 113 * 1024, "two CTAs per SM");
+static_assert(16 * G5_R1 <= G5_TMEM_COLS, "a layer's accumulators fit the TMEM allocation");
+// instruction descriptor (kind::f16): FP32 D, BF16 A and B, both K-major,
+// N = 16 (bits 17-22: N / 8), M = 128 (bits 24-28: M / 16)
+constexpr uint32_t G5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (2u << 17) | (8u << 24);
+
+__device__ __forceinline__ uint32_t g5_smem(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+// Shared-memory matrix descriptor: start address, leading (K-direction)
+// byte offset, stride (M/N-direction, next 8 rows) byte offset, descriptor
+// version 1, no swizzle.
+__device__ __forceinline__ uint64_t g5_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void g5_mma(uint32_t d_tmem, uint64_t a, uint64_t b, bool acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(G5_IDESC), "r"((int)acc));
+}
+// Bounded wait for the mbarrier phase `parity` (about a second at most);
+// false if it gave up.
+__device__ __forceinline__ bool g5_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < (1ll << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void g5_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ float g5_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(r) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void g5_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void g5_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void g5_proxy_fence() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(G5_THREADS, 2)
+    gate_infer_tc5(Images I, const __nv_bfloat16* wb, float logit_threshold, uint8_t* flags,
+                   long long flag_pitch, float* prob, int tiles_x, int ntiles, int* status) {
+  extern __shared__ __align__(128) unsigned char g5[];
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, row parity
+  const int cell = 32 * q + lane;         // the cell (TMEM lane) this thread reads back
+  const uint32_t bar = g5_smem(&s_bar);
+  float* bias = reinterpret_cast<float*>(g5 + G5_OFF_BIAS);
+
+  // B operands (16 output channels x 16 K, [K half][n][8]) and biases, once
+  auto put_b = [&](int mat, int n, int k, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(g5 + G5_OFF_B + mat * G5_BM + (k >> 3) * 256 + n * 16 +
+                                      (k & 7) * 2) = __float2bfloat16_rn(v);
+  };
+  for (int e = tid; e < 24 * 256; e += G5_THREADS) {
+    const int mat = e >> 8, n = (e >> 4) & 15, k = e & 15;
+    float v = 0.0f;
+    if (mat < 6) {  // layer 1, tap rows (2p, 2p + 1), tap column v: K = (row, channel)
+      const int p = mat / 3, tv = mat % 3, u = 2 * p + (k >> 3), c = k & 7;
+      if (u <= 2 && c < 3) v = __bfloat162float(wb[OFF_W1 + ((n * 3 + c) * 3 + u) * 3 + tv]);
+    } else if (mat < 15) {  // layer 2, tap (u, v): K = input channel
+      const int t = mat - 6;
+      v = __bfloat162float(wb[OFF_W2 + (n * kC + k) * 9 + t]);
+    } else {  // layer 3 (one output channel, N padded to 16 with zeros)
+      const int t = mat - 15;
+      if (n == 0) v = __bfloat162float(wb[OFF_W3 + k * 9 + t]);
+    }
+    put_b(mat, n, k, v);
+  }
+  if (tid < kC) bias[tid] = __bfloat162float(wb[OFF_B1 + tid]);
+  else if (tid < 2 * kC) bias[tid] = __bfloat162float(wb[OFF_B2 + tid - kC]);
+  else if (tid == 2 * kC) bias[tid] = __bfloat162float(wb[OFF_B3]);
+  // the two padding cells of every a1 row (read only by discarded cells)
+  for (int e = tid; e < 2 * G5_R1 * 2; e += G5_THREADS) {
+    const int plane = e / (2 * G5_R1), r = (e / 2) % G5_R1, c = 128 + (e & 1);
+    *reinterpret_cast<uint4*>(g5 + G5_OFF_A1 + plane * G5_A1P + r * G5_RP + c * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     g5_smem(&s_taddr)),
+                 "r"(G5_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    g5_fence_before();
+  }
+  __syncthreads();
+  g5_fence_after();
+  const uint32_t tmem = s_taddr;
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+  uint32_t parity = 0;
+  const bool word = I.channels == 4 && (reinterpret_cast<uintptr_t>(I.img) & 3) == 0 &&
+                    (I.pitch & 3) == 0;
+  const uint32_t sb = g5_smem(g5 + G5_OFF_B), sx0 = g5_smem(g5 + G5_OFF_X0),
+                 sa1 = g5_smem(g5 + G5_OFF_A1), sa2 = sx0;
+
+  // one layer: thread 0 issues its MMAs and commits them; every thread waits
+  // (thread 0 on the mbarrier, the others at the barrier after it)
+  auto run_layer = [&](auto issue) -> bool {
+    g5_proxy_fence();  // the generic-proxy writes of the operands, for the tensor cores
+    __syncthreads();
+    if (tid == 0) {
+      g5_fence_after();
+      issue();
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              bar));
+      s_ok = g5_wait(bar, parity) ? 1 : 0;
+    }
+    __syncthreads();
+    parity ^= 1u;
+    g5_fence_after();
+    return s_ok != 0;
+  };
+
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int xs = (tile % tiles_x) * G5_X, ys = (tile / tiles_x) * G5_Y;
+    // x0 rows ys - 3 .. ys + G5_Y + 3, cells xs - 3 .. xs + 126 (zero outside
+    // the image, and the extra row below that pairs with the third tap row)
+    for (int e = tid; e < G5_R0 * G5_CW; e += G5_THREADS) {
+      const int r = e / G5_CW, c = e - r * G5_CW;
+      const int gy = ys - 3 + r, gx = xs - 3 + c;
+      uint32_t w01 = 0u, w23 = 0u;
+      if (r < G5_Y + 6 && gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) {
+        const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
+        uint32_t px;
+        if (word) px = *reinterpret_cast<const uint32_t*>(src);
+        else px = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
+        const float cr = (float)(px & 255u) * (1.0f / 255.0f) - 0.5f;
+        const float cg = (float)((px >> 8) & 255u) * (1.0f / 255.0f) - 0.5f;
+        const float cb = (float)((px >> 16) & 255u) * (1.0f / 255.0f) - 0.5f;
+        w01 = pack_bf16(cr, cg);
+        w23 = pack_bf16(cb, 0.0f);
+      }
+      *reinterpret_cast<uint4*>(g5 + G5_OFF_X0 + r * G5_RP + c * 16) = make_uint4(w01, w23, 0u, 0u);
+    }
+    // layer 1: rows y = 0 .. G5_R1 - 1 of 128 cells, tap rows (0, 1) and (2, 3)
+    ok = run_layer([&] {
+      for (int y = 0; y < G5_R1; ++y)
+        for (int p = 0; p < 2; ++p)
+          for (int v = 0; v < 3; ++v)
+            g5_mma(tmem + 16 * y,
+                   g5_desc(sx0 + ((y + 2 * p) * G5_CW + v) * 16, G5_RP, 128),
+                   g5_desc(sb + (p * 3 + v) * G5_BM, 256, 128), p + v > 0);
+    });
+    if (!ok) break;
+    for (int y = h; y < G5_R1; y += 2) {
+      float z[16];
+      g5_ld16(lane_addr + 16 * y, z);
+      const int gy = ys - 2 + y, gx = xs - 2 + cell;
+      const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+      uint32_t w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        w[k] = in ? pack_bf16(fmaxf(z[2 * k] + bias[2 * k], 0.0f),
+                              fmaxf(z[2 * k + 1] + bias[2 * k + 1], 0.0f))
+                  : 0u;
+      unsigned char* dst = g5 + G5_OFF_A1 + y * G5_RP + cell * 16;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(dst + G5_A1P) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    g5_fence_before();
+    // layer 2: rows y = 0 .. G5_R2 - 1, 9 taps
+    ok = run_layer([&] {
+      for (int y = 0; y < G5_R2; ++y)
+        for (int t = 0; t < 9; ++t)
+          g5_mma(tmem + 16 * y,
+                 g5_desc(sa1 + ((y + t / 3) * G5_CW + t % 3) * 16, G5_A1P, 128),
+                 g5_desc(sb + (6 + t) * G5_BM, 256, 128), t > 0);
+    });
+    if (!ok) break;
+    for (int y = h; y < G5_R2; y += 2) {
+      float z[16];
+      g5_ld16(lane_addr + 16 * y, z);
+      const int gy = ys - 1 + y, gx = xs - 1 + cell;
+      const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+      uint32_t w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        w[k] = in ? pack_bf16(fmaxf(z[2 * k] + bias[kC + 2 * k], 0.0f),
+                              fmaxf(z[2 * k + 1] + bias[kC + 2 * k + 1], 0.0f))
+                  : 0u;
+      unsigned char* dst = g5 + G5_OFF_X0 + y * G5_RP + cell * 16;  // a2 over x0
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(dst + G5_A2P) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    g5_fence_before();
+    // layer 3: rows y = 0 .. G5_Y - 1, 9 taps, output channel 0
+    ok = run_layer([&] {
+      for (int y = 0; y < G5_Y; ++y)
+        for (int t = 0; t < 9; ++t)
+          g5_mma(tmem + 16 * y,
+                 g5_desc(sa2 + ((y + t / 3) * G5_CW + t % 3) * 16, G5_A2P, 128),
+                 g5_desc(sb + (15 + t) * G5_BM, 256, 128), t > 0);
+    });
+    if (!ok) break;
+    for (int y = h; y < G5_Y; y += 2) {
+      const float z = g5_ld1(lane_addr + 16 * y) + bias[2 * kC];
+      const int gy = ys + y, gx = xs + cell;
+      if (cell < G5_X && gy < I.H && gx < I.W) {
+        if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
+        if (prob) prob[(long long)gy * I.W + gx] = 1.0f / (1.0f + expf(-z));
+      }
+    }
+    g5_fence_before();
+    __syncthreads();  // the tile's reads of TMEM and of the x0 / a2 planes are done
+  }
+  if (!ok && tid == 0) atomicExch(status, 1);
+  g5_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    g5_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(G5_TMEM_COLS));
+  }
+}
+
 uint32_t crc32(const unsigned char* p, size_t n, uint32_t crc = 0) {
   // CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bitwise
   crc = ~crc;
@@ -616,6 +901,8 @@ struct vf_gate {
   float* part = nullptr;
   float* loss_part = nullptr;
   long long cap_pixels = 0;
+  int* d_status = nullptr;  // 1 after a bounded device-side wait gave up
+  int sms = 0;
 };
 
 namespace {
@@ -710,6 +997,11 @@ vf_status vf_gate_create(vf_ctx* ctx, unsigned long long seed, vf_gate** out) {
   if (e == cudaSuccess) e = cudaMalloc(&g->grad, NPARAM * 4);
   if (e == cudaSuccess) e = cudaMalloc(&g->wb, NPARAM * 2);
   if (e == cudaSuccess) e = cudaMalloc(&g->part, sizeof(float) * (size_t)kWgradBlocks * NPARAM);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) {
     cudaGetLastError();
     vf_gate_destroy(g);
@@ -819,7 +1111,21 @@ vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, 
   if (st != VF_OK) return st;
   const float thr = std::log(threshold / (1.0f - threshold));
   cudaError_t e = cudaSuccess;
-  if (gate_tensor_cores(g->ctx)) {
+  const int engine = gate_tensor_cores(g->ctx);
+  if (engine == 1) {
+    const int tiles_x = (width + G5_X - 1) / G5_X, tiles_y = (height + G5_Y - 1) / G5_Y;
+    const long long ntiles = (long long)tiles_x * tiles_y;
+    if (ntiles > 0x7fffffffLL) return set_error(g->ctx, VF_ERR_UNSUPPORTED, "image too large");
+    const int grid = (int)std::min<long long>(ntiles, 2LL * std::max(g->sms, 1));
+    e = cudaFuncSetAttribute(gate_infer_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G5_SMEM);
+    if (e == cudaSuccess) {
+      gate_infer_tc5<<<grid, G5_THREADS, G5_SMEM, (cudaStream_t)stream>>>(
+          I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x, (int)ntiles,
+          g->d_status);
+      e = cudaGetLastError();
+    }
+  } else if (engine == 2) {
     const int tiles_x = (width + TX - 1) / TX, tiles_y = (height + TY - 1) / TY;
     e = cudaFuncSetAttribute(gate_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TC_SMEM);
@@ -955,11 +1261,21 @@ vf_status vf_gate_load(vf_gate* g, const char* path) {
 
 unsigned long long vf_gate_step_count(const vf_gate* g) { return g ? g->step : 0; }
 
+vf_status vf_gate_check(vf_gate* g) {
+  if (!g) return VF_ERR_ARG;
+  int st = 0;
+  cudaError_t e = cudaMemcpy(&st, g->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st != 0) e = cudaMemset(g->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return set_error(g->ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return st ? set_error(g->ctx, VF_ERR_TIMEOUT, "a tensor-core wait of the gate inference gave up")
+            : VF_OK;
+}
+
 void vf_gate_destroy(vf_gate* g) {
   if (!g) return;
   free_scratch(g);
   for (void* p : {(void*)g->theta, (void*)g->m, (void*)g->v, (void*)g->grad, (void*)g->wb,
-                  (void*)g->part})
+                  (void*)g->part, (void*)g->d_status})
     if (p) cudaFree(p);
   delete g;
 }

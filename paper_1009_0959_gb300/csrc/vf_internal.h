@@ -166,8 +166,8 @@ vf_status prepare_launch(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int h
 // packed kernel the context's options select, on stream s.
 vf_status launch_single(vf_ctx* ctx, Launch L, const LaunchClass& cls, cudaStream_t s);
 
-// Whether the gate inference runs on the tensor cores (context option).
-bool gate_tensor_cores(const vf_ctx* ctx);
+// Gate inference engine (context option): 0 CUDA cores, 1 tcgen05, 2 mma.sync.
+int gate_tensor_cores(const vf_ctx* ctx);
 
 // Whether an FP32 call of window w and criterion crit runs the pair-reuse
 // kernels under the context's VF_OPT_PAIR_REUSE setting.

@@ -137,6 +137,8 @@ def lib():
             L.vf_gate_load.restype = I
             L.vf_gate_step_count.argtypes = [P]
             L.vf_gate_step_count.restype = ctypes.c_ulonglong
+            L.vf_gate_check.argtypes = [P]
+            L.vf_gate_check.restype = I
             L.vf_gate_destroy.argtypes = [P]
             L.vf_gate_destroy.restype = None
             _lib = L
@@ -421,6 +423,11 @@ class Gate:
         _check(lib().vf_gate_load(self.handle, str(path).encode()), self.ctx)
 
     @property
+    def check(self):
+        """vf_gate_check: raises VFError (VF_ERR_TIMEOUT) if a tensor-core wait
+        of an inference since the last check gave up."""
+        _check(lib().vf_gate_check(self.handle), self.ctx)
+
     def step(self):
         return lib().vf_gate_step_count(self.handle)
 

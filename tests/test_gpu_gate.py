@@ -67,27 +67,38 @@ def test_gradient_and_forward_match_oracle(vf):
     gate.close()
 
 
-def test_tensor_core_inference_matches_bf16_oracle(vf):
-    """The tensor-core inference rounds activations to BF16 between layers;
-    against the oracle taking the same reading the remaining differences are
-    FP32 accumulation order and the occasional BF16 rounding flip of an
-    activation: probabilities within 2e-3, flags equal away from the
-    threshold.  Images span several 32 x 8 tiles with ragged edges."""
-    imgs, tgts = batch(3, 37, 70, 4)
+@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("shape", [(37, 70), (40, 300), (13, 125), (1, 1), (7, 1), (1, 260)])
+def test_tensor_core_inference_matches_bf16_oracle(vf, engine, shape):
+    """Both tensor-core engines (1: tcgen05 MMAs into TMEM over rows of 128
+    cells, 124 x 6 outputs per tile; 2: warp-level mma, 32 x 16 tiles) round
+    activations to BF16 between layers; against the oracle taking the same
+    reading the remaining differences are FP32 accumulation order and the
+    occasional BF16 rounding flip of an activation: probabilities within
+    2e-3, flags equal away from the threshold.  The shapes span several tiles
+    of either engine with ragged edges, and images smaller than one tile."""
+    H, W = shape
+    imgs, tgts = batch(2, H, W, 4)
     theta = G.init(5)
     theta[G.NPARAM - 17:] += 0.03
     gate = vf.Gate()
     gate.set_params(theta.astype(np.float32))
     wq = G.bf16_round(theta.astype(np.float32).astype(np.float64))
-    for k in range(3):
-        ref = G.forward(imgs[k], wq, act_bf16=True)["p"]
-        t = torch.from_numpy(imgs[k]).cuda()
-        fl, pr = gate.infer(t, 0.5, flags=torch.empty((37, 70), dtype=torch.uint8, device="cuda"),
-                            prob=torch.empty((37, 70), device="cuda"))
-        torch.cuda.synchronize()
-        np.testing.assert_allclose(pr.cpu().numpy(), ref, atol=2e-3)
-        sure = np.abs(ref - 0.5) > 5e-3
-        np.testing.assert_array_equal(fl.cpu().numpy()[sure], (ref > 0.5)[sure])
+    try:
+        vf.set_option("gate_tensor_cores", engine)
+        for k in range(2):
+            ref = G.forward(imgs[k], wq, act_bf16=True)["p"]
+            t = torch.from_numpy(imgs[k]).cuda()
+            fl, pr = gate.infer(t, 0.5,
+                                flags=torch.empty((H, W), dtype=torch.uint8, device="cuda"),
+                                prob=torch.empty((H, W), device="cuda"))
+            torch.cuda.synchronize()
+            np.testing.assert_allclose(pr.cpu().numpy(), ref, atol=2e-3)
+            sure = np.abs(ref - 0.5) > 5e-3
+            np.testing.assert_array_equal(fl.cpu().numpy()[sure], (ref > 0.5)[sure])
+        gate.check()  # no device-side wait gave up
+    finally:
+        vf.set_option("gate_tensor_cores", 1)
     gate.close()
 
 
