@@ -422,12 +422,12 @@ class Gate:
     def load(self, path):
         _check(lib().vf_gate_load(self.handle, str(path).encode()), self.ctx)
 
-    @property
     def check(self):
         """vf_gate_check: raises VFError (VF_ERR_TIMEOUT) if a tensor-core wait
         of an inference since the last check gave up."""
         _check(lib().vf_gate_check(self.handle), self.ctx)
 
+    @property
     def step(self):
         return lib().vf_gate_step_count(self.handle)
 
