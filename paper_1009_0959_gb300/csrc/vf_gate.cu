@@ -656,8 +656,7 @@ __device__ __forceinline__ bool g5_wait(uint32_t bar, uint32_t parity) {
   }
   return false;
 }
-__device__ __forceinline__ void g5_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+__device__ __forceinline__ void g5_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
       "%14,%15}, [%16];\n"
@@ -665,9 +664,9 @@ __device__ __forceinline__ void g5_ld16(uint32_t taddr, float (&v)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+__device__ __forceinline__ void g5_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 __device__ __forceinline__ float g5_ld1(uint32_t taddr) {
   uint32_t r;
@@ -745,8 +744,34 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   uint32_t parity = 0;
   const bool word = I.channels == 4 && (reinterpret_cast<uintptr_t>(I.img) & 3) == 0 &&
                     (I.pitch & 3) == 0;
-  const uint32_t sb = g5_smem(g5 + G5_OFF_B), sx0 = g5_smem(g5 + G5_OFF_X0),
-                 sa1 = g5_smem(g5 + G5_OFF_A1), sa2 = sx0;
+  // descriptors of the operand bases; a start address further on by d bytes
+  // (a multiple of 16) is the same descriptor plus d / 16 (the 14-bit address
+  // field cannot carry: every address is below 256 KB)
+  const uint64_t dx0 = g5_desc(g5_smem(g5 + G5_OFF_X0), G5_RP, 128);
+  const uint64_t da1 = g5_desc(g5_smem(g5 + G5_OFF_A1), G5_A1P, 128);
+  const uint64_t da2 = g5_desc(g5_smem(g5 + G5_OFF_X0), G5_A2P, 128);
+  const uint64_t dbm = g5_desc(g5_smem(g5 + G5_OFF_B), 256, 128);
+  constexpr uint64_t kCellD = 1, kRowD = G5_RP / 16, kMatD = G5_BM / 16;
+  // the next tile's input pixels, loaded while the tile's last layer runs
+  constexpr int kPre = (G5_R0 * G5_CW + G5_THREADS - 1) / G5_THREADS;
+  uint32_t pre[kPre];
+  auto fetch = [&](int t) {
+    const int xs = (t % tiles_x) * G5_X, ys = (t / tiles_x) * G5_Y;
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+      const int e = tid + j * G5_THREADS;
+      const int r = e / G5_CW, c = e - r * G5_CW;
+      const int gy = ys - 3 + r, gx = xs - 3 + c;
+      uint32_t px = 0xffffffffu;  // marks a cell outside the image (zero input)
+      if (e < G5_R0 * G5_CW && r < G5_Y + 6 && t < ntiles && gy >= 0 && gy < I.H && gx >= 0 &&
+          gx < I.W) {
+        const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
+        if (word) px = *reinterpret_cast<const uint32_t*>(src) & 0x00ffffffu;
+        else px = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
+      }
+      pre[j] = px;
+    }
+  };
 
   // one layer: thread 0 issues its MMAs and commits them; every thread waits
   // (thread 0 on the mbarrier, the others at the barrier after it)
@@ -768,19 +793,20 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   };
 
   bool ok = true;
+  fetch(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int xs = (tile % tiles_x) * G5_X, ys = (tile / tiles_x) * G5_Y;
     // x0 rows ys - 3 .. ys + G5_Y + 3, cells xs - 3 .. xs + 126 (zero outside
-    // the image, and the extra row below that pairs with the third tap row)
-    for (int e = tid; e < G5_R0 * G5_CW; e += G5_THREADS) {
+    // the image, and the extra row below that pairs with the third tap row),
+    // from the pixels fetched during the previous tile
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+      const int e = tid + j * G5_THREADS;
+      if (e >= G5_R0 * G5_CW) break;
       const int r = e / G5_CW, c = e - r * G5_CW;
-      const int gy = ys - 3 + r, gx = xs - 3 + c;
+      const uint32_t px = pre[j];
       uint32_t w01 = 0u, w23 = 0u;
-      if (r < G5_Y + 6 && gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) {
-        const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
-        uint32_t px;
-        if (word) px = *reinterpret_cast<const uint32_t*>(src);
-        else px = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
+      if (px != 0xffffffffu) {
         const float cr = (float)(px & 255u) * (1.0f / 255.0f) - 0.5f;
         const float cg = (float)((px >> 8) & 255u) * (1.0f / 255.0f) - 0.5f;
         const float cb = (float)((px >> 16) & 255u) * (1.0f / 255.0f) - 0.5f;
@@ -794,59 +820,58 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       for (int y = 0; y < G5_R1; ++y)
         for (int p = 0; p < 2; ++p)
           for (int v = 0; v < 3; ++v)
-            g5_mma(tmem + 16 * y,
-                   g5_desc(sx0 + ((y + 2 * p) * G5_CW + v) * 16, G5_RP, 128),
-                   g5_desc(sb + (p * 3 + v) * G5_BM, 256, 128), p + v > 0);
+            g5_mma(tmem + 16 * y, dx0 + (y + 2 * p) * kRowD + v * kCellD,
+                   dbm + (p * 3 + v) * kMatD, p + v > 0);
     });
     if (!ok) break;
-    for (int y = h; y < G5_R1; y += 2) {
-      float z[16];
-      g5_ld16(lane_addr + 16 * y, z);
-      const int gy = ys - 2 + y, gx = xs - 2 + cell;
-      const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
-      uint32_t w[8];
+    // this thread's rows y (every other one) of a layer, two tcgen05.ld per
+    // wait: z + bias, ReLU, BF16, into the next layer's two planes (0 outside
+    // the image)
+    auto act_rows = [&](int rows, int gy0, int gx0, const float* b, unsigned char* planes,
+                        int plane_bytes) {
+      for (int y = h; y < rows; y += 4) {
+        uint32_t z[2][16];
+        const bool two = y + 2 < rows;
+        g5_ld16(lane_addr + 16 * y, z[0]);
+        if (two) g5_ld16(lane_addr + 16 * (y + 2), z[1]);
+        g5_wait_ld();
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        w[k] = in ? pack_bf16(fmaxf(z[2 * k] + bias[2 * k], 0.0f),
-                              fmaxf(z[2 * k + 1] + bias[2 * k + 1], 0.0f))
-                  : 0u;
-      unsigned char* dst = g5 + G5_OFF_A1 + y * G5_RP + cell * 16;
-      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-      *reinterpret_cast<uint4*>(dst + G5_A1P) = make_uint4(w[4], w[5], w[6], w[7]);
-    }
+        for (int i = 0; i < 2; ++i) {
+          if (i == 1 && !two) break;
+          const int yy = y + 2 * i, gy = gy0 + yy, gx = gx0 + cell;
+          const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+          uint32_t w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            w[k] = in ? pack_bf16(fmaxf(__uint_as_float(z[i][2 * k]) + b[2 * k], 0.0f),
+                                  fmaxf(__uint_as_float(z[i][2 * k + 1]) + b[2 * k + 1], 0.0f))
+                      : 0u;
+          unsigned char* dst = planes + yy * G5_RP + cell * 16;
+          *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4*>(dst + plane_bytes) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+      }
+    };
+    act_rows(G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
     g5_fence_before();
     // layer 2: rows y = 0 .. G5_R2 - 1, 9 taps
     ok = run_layer([&] {
       for (int y = 0; y < G5_R2; ++y)
         for (int t = 0; t < 9; ++t)
-          g5_mma(tmem + 16 * y,
-                 g5_desc(sa1 + ((y + t / 3) * G5_CW + t % 3) * 16, G5_A1P, 128),
-                 g5_desc(sb + (6 + t) * G5_BM, 256, 128), t > 0);
+          g5_mma(tmem + 16 * y, da1 + (y + t / 3) * kRowD + (t % 3) * kCellD,
+                 dbm + (6 + t) * kMatD, t > 0);
     });
     if (!ok) break;
-    for (int y = h; y < G5_R2; y += 2) {
-      float z[16];
-      g5_ld16(lane_addr + 16 * y, z);
-      const int gy = ys - 1 + y, gx = xs - 1 + cell;
-      const bool in = gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
-      uint32_t w[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        w[k] = in ? pack_bf16(fmaxf(z[2 * k] + bias[kC + 2 * k], 0.0f),
-                              fmaxf(z[2 * k + 1] + bias[kC + 2 * k + 1], 0.0f))
-                  : 0u;
-      unsigned char* dst = g5 + G5_OFF_X0 + y * G5_RP + cell * 16;  // a2 over x0
-      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-      *reinterpret_cast<uint4*>(dst + G5_A2P) = make_uint4(w[4], w[5], w[6], w[7]);
-    }
+    act_rows(G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);  // a2 over x0
     g5_fence_before();
-    // layer 3: rows y = 0 .. G5_Y - 1, 9 taps, output channel 0
+    // layer 3: rows y = 0 .. G5_Y - 1, 9 taps, output channel 0; the next
+    // tile's pixels are fetched while its MMAs run
+    fetch(tile + gridDim.x);
     ok = run_layer([&] {
       for (int y = 0; y < G5_Y; ++y)
         for (int t = 0; t < 9; ++t)
-          g5_mma(tmem + 16 * y,
-                 g5_desc(sa2 + ((y + t / 3) * G5_CW + t % 3) * 16, G5_A2P, 128),
-                 g5_desc(sb + (15 + t) * G5_BM, 256, 128), t > 0);
+          g5_mma(tmem + 16 * y, da2 + (y + t / 3) * kRowD + (t % 3) * kCellD,
+                 dbm + (15 + t) * kMatD, t > 0);
     });
     if (!ok) break;
     for (int y = h; y < G5_Y; y += 2) {
