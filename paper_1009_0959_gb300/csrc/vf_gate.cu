@@ -602,7 +602,11 @@ __global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv
 // (bounded) wait, all eight warps read the accumulators back with tcgen05.ld
 // (warp w: TMEM lanes 32 (w mod 4) .. + 31, every other layer row), add the
 // bias, apply ReLU, round to BF16 and write the next layer's planes, or, for
-// layer 3, the logit's flag and probability.  Outputs per CTA tile: 124 x 6
+// layer 3 (whose three tap rows are the N columns of one accumulator per a2
+// row: 24 MMAs per tile instead of 54), the logit's flag and probability.
+// The MMAs of a layer are issued by two threads (rows alternating); at
+// N = 16 an MMA costs about as much as one of N = 64, so the tensor core's
+// issue time per tile, not its FLOP rate, bounds this kernel.  Outputs per CTA tile: 124 x 6
 // (the 128-cell rows shrink by 2 cells per 3 x 3 layer); two CTAs per SM,
 // persistent over the tiles.  Numerics as gate_infer_tc: BF16 input and
 // activations between layers, BF16 weights, FP32 accumulation and biases.
@@ -612,8 +616,10 @@ constexpr int G5_RP = G5_CW * 16;                      // bytes per staged row
 constexpr int G5_R0 = G5_Y + 7, G5_R1 = G5_Y + 4, G5_R2 = G5_Y + 2;  // rows of x0, a1, a2
 constexpr int G5_A1P = G5_R1 * G5_RP, G5_A2P = G5_R2 * G5_RP;      // plane bytes
 constexpr int G5_BM = 512;                             // one 16 x 16 BF16 B operand
-constexpr int G5_OFF_B = 0;                            // 6 + 9 + 9 B operands
-constexpr int G5_OFF_BIAS = G5_OFF_B + 24 * G5_BM;
+constexpr int G5_NB = 6 + 9 + 3;                       // B operands of layers 1, 2, 3
+constexpr int G5_OFF_B = 0;
+constexpr int G5_OFF_BIAS = G5_OFF_B + G5_NB * G5_BM;
+constexpr int G5_ISSUERS = 2;                          // threads issuing a layer's MMAs
 constexpr int G5_OFF_X0 = G5_OFF_BIAS + 256;           // x0, later a2 (x0 is dead by then)
 constexpr int G5_OFF_A1 = G5_OFF_X0 + 2 * G5_A2P;
 constexpr int G5_SMEM = G5_OFF_A1 + 2 * G5_A1P;
@@ -668,12 +674,6 @@ __device__ __forceinline__ void g5_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 __device__ __forceinline__ void g5_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
-__device__ __forceinline__ float g5_ld1(uint32_t taddr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(r) : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-  return __uint_as_float(r);
-}
 __device__ __forceinline__ void g5_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     *reinterpret_cast<__nv_bfloat16*>(g5 + G5_OFF_B + mat * G5_BM + (k >> 3) * 256 + n * 16 +
                                       (k & 7) * 2) = __float2bfloat16_rn(v);
   };
-  for (int e = tid; e < 24 * 256; e += G5_THREADS) {
+  for (int e = tid; e < G5_NB * 256; e += G5_THREADS) {
     const int mat = e >> 8, n = (e >> 4) & 15, k = e & 15;
     float v = 0.0f;
     if (mat < 6) {  // layer 1, tap rows (2p, 2p + 1), tap column v: K = (row, channel)
@@ -711,9 +711,9 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     } else if (mat < 15) {  // layer 2, tap (u, v): K = input channel
       const int t = mat - 6;
       v = __bfloat162float(wb[OFF_W2 + (n * kC + k) * 9 + t]);
-    } else {  // layer 3 (one output channel, N padded to 16 with zeros)
-      const int t = mat - 15;
-      if (n == 0) v = __bfloat162float(wb[OFF_W3 + k * 9 + t]);
+    } else {  // layer 3, tap column v: N = tap row u (one output channel; u < 3)
+      const int tv = mat - 15;
+      if (n < 3) v = __bfloat162float(wb[OFF_W3 + k * 9 + n * 3 + tv]);
     }
     put_b(mat, n, k, v);
   }
@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
         make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(G5_ISSUERS));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -773,18 +773,20 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     }
   };
 
-  // one layer: thread 0 issues its MMAs and commits them; every thread waits
-  // (thread 0 on the mbarrier, the others at the barrier after it)
+  // one layer: lane 0 of warps 0 .. G5_ISSUERS - 1 each issue the MMAs of
+  // every G5_ISSUERS-th row and commit them (the mbarrier counts one arrival
+  // per issuer); thread 0 waits on the mbarrier, the others at the barrier
+  // after it
   auto run_layer = [&](auto issue) -> bool {
     g5_proxy_fence();  // the generic-proxy writes of the operands, for the tensor cores
     __syncthreads();
-    if (tid == 0) {
+    if (lane == 0 && warp < G5_ISSUERS) {
       g5_fence_after();
-      issue();
+      issue(warp);
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               bar));
-      s_ok = g5_wait(bar, parity) ? 1 : 0;
+      if (tid == 0) s_ok = g5_wait(bar, parity) ? 1 : 0;
     }
     __syncthreads();
     parity ^= 1u;
@@ -816,8 +818,8 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       *reinterpret_cast<uint4*>(g5 + G5_OFF_X0 + r * G5_RP + c * 16) = make_uint4(w01, w23, 0u, 0u);
     }
     // layer 1: rows y = 0 .. G5_R1 - 1 of 128 cells, tap rows (0, 1) and (2, 3)
-    ok = run_layer([&] {
-      for (int y = 0; y < G5_R1; ++y)
+    ok = run_layer([&](int first) {
+      for (int y = first; y < G5_R1; y += G5_ISSUERS)
         for (int p = 0; p < 2; ++p)
           for (int v = 0; v < 3; ++v)
             g5_mma(tmem + 16 * y, dx0 + (y + 2 * p) * kRowD + v * kCellD,
@@ -855,8 +857,8 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     act_rows(G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
     g5_fence_before();
     // layer 2: rows y = 0 .. G5_R2 - 1, 9 taps
-    ok = run_layer([&] {
-      for (int y = 0; y < G5_R2; ++y)
+    ok = run_layer([&](int first) {
+      for (int y = first; y < G5_R2; y += G5_ISSUERS)
         for (int t = 0; t < 9; ++t)
           g5_mma(tmem + 16 * y, da1 + (y + t / 3) * kRowD + (t % 3) * kCellD,
                  dbm + (6 + t) * kMatD, t > 0);
@@ -864,18 +866,29 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     if (!ok) break;
     act_rows(G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);  // a2 over x0
     g5_fence_before();
-    // layer 3: rows y = 0 .. G5_Y - 1, 9 taps, output channel 0; the next
-    // tile's pixels are fetched while its MMAs run
+    // layer 3 (one output channel): the tap rows go to N instead of to nine
+    // MMAs: for every a2 row y', three MMAs (tap columns v, A shifted by v
+    // cells) give D_y'[cell][u] = sum_v sum_c a2[y'][cell + v][c] W3[c][u][v];
+    // output row y is D_y[.][0] + D_(y+1)[.][1] + D_(y+2)[.][2].  The next
+    // tile's pixels are fetched while the MMAs run.
     fetch(tile + gridDim.x);
-    ok = run_layer([&] {
-      for (int y = 0; y < G5_Y; ++y)
-        for (int t = 0; t < 9; ++t)
-          g5_mma(tmem + 16 * y, da2 + (y + t / 3) * kRowD + (t % 3) * kCellD,
-                 dbm + (15 + t) * kMatD, t > 0);
+    ok = run_layer([&](int first) {
+      for (int y = first; y < G5_R2; y += G5_ISSUERS)
+        for (int v = 0; v < 3; ++v)
+          g5_mma(tmem + 16 * y, da2 + y * kRowD + v * kCellD, dbm + (15 + v) * kMatD, v > 0);
     });
     if (!ok) break;
     for (int y = h; y < G5_Y; y += 2) {
-      const float z = g5_ld1(lane_addr + 16 * y) + bias[2 * kC];
+      uint32_t r0, r1, r2;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
+                   : "=r"(r0) : "r"(lane_addr + 16 * y));
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
+                   : "=r"(r1) : "r"(lane_addr + 16 * (y + 1) + 1));
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
+                   : "=r"(r2) : "r"(lane_addr + 16 * (y + 2) + 2));
+      g5_wait_ld();
+      const float z =
+          (__uint_as_float(r0) + __uint_as_float(r1)) + __uint_as_float(r2) + bias[2 * kC];
       const int gy = ys + y, gx = xs + cell;
       if (cell < G5_X && gy < I.H && gx < I.W) {
         if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
