@@ -505,6 +505,19 @@ unsigned long long vf_gate_step_count(const vf_gate* g);
 vf_status vf_gate_check(vf_gate* g);
 void vf_gate_destroy(vf_gate* g);
 
+/* ---- failure injection (tests) ------------------------------------------- */
+
+/* Makes an allocation of this library fail on purpose, so that the error
+ * paths can be exercised without exhausting memory: after `after` further
+ * allocations succeed, the next one fails as if the memory were exhausted
+ * (VF_ERR_OOM from the call that made it) and the hook disarms itself;
+ * after < 0 disarms it at once.  Counted allocations: the handles of
+ * vf_create, vf_batch_create and vf_gate_create, and every device buffer the
+ * library allocates (host staging, batch descriptors, gate weights and
+ * training scratch).  A failed call releases what it had allocated and
+ * leaves the context usable.  Process-wide; returns the previous setting. */
+int vf_debug_fail_alloc(int after);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // vf_api.cpp -- the C ABI of include/vfilt.h: argument checks, the minimax
 // coefficient cache and kernel dispatch.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -119,7 +120,7 @@ extern "C" {
 
 vf_status vf_create(vf_ctx** ctx) {
   if (!ctx) return VF_ERR_ARG;
-  *ctx = new (std::nothrow) vf_ctx();
+  *ctx = alloc_refused() ? nullptr : new (std::nothrow) vf_ctx();
   if (!*ctx) return VF_ERR_OOM;
   // the exact angle's arctangent polynomial, fitted once per context so that
   // every exact angle call (the allocation-free one included) finds it
@@ -522,9 +523,24 @@ vf_status launch_single(vf_ctx* ctx, Launch L, const LaunchClass& cls, cudaStrea
   return VF_OK;
 }
 
+namespace {
+// allocations left before the injected failure; < 0: disarmed
+std::atomic<int> g_fail_after{-1};
+}  // namespace
+
+bool alloc_refused() {
+  int k = g_fail_after.load();
+  while (k >= 0) {
+    if (g_fail_after.compare_exchange_weak(k, k - 1)) return k == 0;
+  }
+  return false;
+}
+
 }  // namespace vf
 
 extern "C" {
+
+int vf_debug_fail_alloc(int after) { return g_fail_after.exchange(after < 0 ? -1 : after); }
 
 vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int height, int width,
                          int channels, size_t in_pitch, size_t out_pitch, const vf_params* p,
@@ -544,7 +560,7 @@ vf_status vf_filter_host(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out, int h
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     ctx->d_stage = nullptr;
     ctx->stage_bytes = 0;
-    if (cudaMalloc(&ctx->d_stage, need) != cudaSuccess) {
+    if (device_alloc(&ctx->d_stage, need) != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, VF_ERR_OOM, "device staging allocation failed");
     }
@@ -599,7 +615,7 @@ vf_status vf_filter_host_async(vf_ctx* ctx, const uint8_t* h_in, uint8_t* h_out,
     if (sl.d_buf) cudaFree(sl.d_buf);
     sl.d_buf = nullptr;
     sl.bytes = 0;
-    if (cudaMalloc(&sl.d_buf, need) != cudaSuccess) {
+    if (device_alloc(&sl.d_buf, need) != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, VF_ERR_OOM, "device staging allocation failed");
     }

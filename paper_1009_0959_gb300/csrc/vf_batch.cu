@@ -326,9 +326,10 @@ vf_status upload_classes(vf_batch* b) {
   // the tail
   std::stable_sort(b->classes.begin(), b->classes.end(),
                    [](const BatchClass& x, const BatchClass& y) { return x.cost > y.cost; });
-  cudaError_t e = cudaMalloc(&b->d_cimgs, sizeof(BatchImage) * imgs.size());
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_cbegin, sizeof(int) * begin.size());
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_ccounters, sizeof(unsigned int) * b->classes.size());
+  cudaError_t e = device_alloc(&b->d_cimgs, sizeof(BatchImage) * imgs.size());
+  if (e == cudaSuccess) e = device_alloc(&b->d_cbegin, sizeof(int) * begin.size());
+  if (e == cudaSuccess)
+    e = device_alloc(&b->d_ccounters, sizeof(unsigned int) * b->classes.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_cimgs, imgs.data(), sizeof(BatchImage) * imgs.size(),
                    cudaMemcpyHostToDevice);
@@ -415,7 +416,7 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
   if (!ctx) return VF_ERR_ARG;
   if (!descs || !out || count < 1) return set_error(ctx, VF_ERR_ARG, "empty batch");
   *out = nullptr;
-  vf_batch* b = new (std::nothrow) vf_batch();
+  vf_batch* b = alloc_refused() ? nullptr : new (std::nothrow) vf_batch();
   if (!b) return VF_ERR_OOM;
   b->ctx = ctx;
   b->count = count;
@@ -447,9 +448,9 @@ vf_status vf_batch_create(vf_ctx* ctx, const vf_image_desc* descs, int count, vf
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_imgs, sizeof(BatchImage) * count);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_begin, sizeof(int) * (count + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned int));
+  if (e == cudaSuccess) e = device_alloc(&b->d_imgs, sizeof(BatchImage) * count);
+  if (e == cudaSuccess) e = device_alloc(&b->d_begin, sizeof(int) * (count + 1));
+  if (e == cudaSuccess) e = device_alloc(&b->d_counter, sizeof(unsigned int));
   if (e != cudaSuccess) {
     vf_batch_destroy(b);
     cudaGetLastError();

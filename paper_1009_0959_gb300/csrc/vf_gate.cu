@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv
   uint32_t* s2 = reinterpret_cast<uint32_t*>(tc_smem + TC_OFF_S2);  // a2
   float* bias = reinterpret_cast<float*>(tc_smem + TC_OFF_BIAS);
   {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(wb);  // cudaMalloc'd: aligned
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(wb);  // device_alloc'd: aligned
     uint32_t* dst = reinterpret_cast<uint32_t*>(sw);
     for (int k = threadIdx.x; k < NPARAM / 2; k += blockDim.x) dst[k] = src[k];
     if ((NPARAM & 1) && threadIdx.x == 0) sw[NPARAM - 1] = wb[NPARAM - 1];
@@ -958,12 +958,12 @@ vf_status ensure_scratch(vf_gate* g, long long pixels) {
   free_scratch(g);
   const size_t P = (size_t)pixels;
   const long long blocks = (pixels + kThreads - 1) / kThreads;
-  cudaError_t e = cudaMalloc(&g->z1, P * kC * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->z2, P * kC * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->z3, P * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->dz1, P * kC * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->dz2, P * kC * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->loss_part, (size_t)blocks * 4);
+  cudaError_t e = device_alloc(&g->z1, P * kC * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->z2, P * kC * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->z3, P * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->dz1, P * kC * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->dz2, P * kC * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->loss_part, (size_t)blocks * 4);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_scratch(g);
@@ -1025,17 +1025,17 @@ extern "C" {
 vf_status vf_gate_create(vf_ctx* ctx, unsigned long long seed, vf_gate** out) {
   if (!ctx || !out) return VF_ERR_ARG;
   *out = nullptr;
-  vf_gate* g = new (std::nothrow) vf_gate();
+  vf_gate* g = alloc_refused() ? nullptr : new (std::nothrow) vf_gate();
   if (!g) return VF_ERR_OOM;
   g->ctx = ctx;
   g->seed = seed;
-  cudaError_t e = cudaMalloc(&g->theta, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->m, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->v, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->grad, NPARAM * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&g->wb, NPARAM * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&g->part, sizeof(float) * (size_t)kWgradBlocks * NPARAM);
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(int));
+  cudaError_t e = device_alloc(&g->theta, NPARAM * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->m, NPARAM * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->v, NPARAM * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->grad, NPARAM * 4);
+  if (e == cudaSuccess) e = device_alloc(&g->wb, NPARAM * 2);
+  if (e == cudaSuccess) e = device_alloc(&g->part, sizeof(float) * (size_t)kWgradBlocks * NPARAM);
+  if (e == cudaSuccess) e = device_alloc(&g->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(int));
   int dev = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);

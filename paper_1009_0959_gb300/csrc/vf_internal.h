@@ -204,4 +204,15 @@ bool remez_rational_fit(int fn, int m, int n, double lo, double hi, double* num,
 bool approximant_error(int fn, const double* num, int num_len, const double* den, int den_len,
                        double lo, double hi, double* eps);
 
+// Failure injection (vf_debug_fail_alloc): true when the armed countdown
+// reaches this allocation, which the caller then treats as out of memory.
+bool alloc_refused();
+
+// cudaMalloc through the failure-injection countdown.
+template <class T>
+cudaError_t device_alloc(T** p, size_t bytes) {
+  if (alloc_refused()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
 }  // namespace vf

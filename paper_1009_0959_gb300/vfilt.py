@@ -141,6 +141,8 @@ def lib():
             L.vf_gate_check.restype = I
             L.vf_gate_destroy.argtypes = [P]
             L.vf_gate_destroy.restype = None
+            L.vf_debug_fail_alloc.argtypes = [I]
+            L.vf_debug_fail_alloc.restype = I
             _lib = L
         return _lib
 
@@ -565,6 +567,12 @@ def filter_band(host_img, band: int, bands: int, out=None, stream=None, **params
         d_out = filter(d_in, stream=s, **params)
         out[r0:r0 + m].copy_(d_out[r0 - a:r0 - a + m], non_blocking=False)
     return out, r0, m
+
+
+def debug_fail_alloc(after: int) -> int:
+    """vf_debug_fail_alloc: fail the library's allocation after the next
+    `after` ones (< 0 disarms); returns the previous setting."""
+    return lib().vf_debug_fail_alloc(int(after))
 
 
 def status_string(code: int) -> str:

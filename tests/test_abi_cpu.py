@@ -242,3 +242,24 @@ def test_half_angle_polynomial(vf):
         assert uu * P.polyval(uu * uu, num) == pytest.approx(a, rel=1.2e-7, abs=1e-12)
     with pytest.raises(vf.VFError):  # read-only
         vf.set_coefficients("half_angle", "poly", 7, num, lo=0.0, hi=1.0)
+
+
+def test_alloc_failure_hook_without_gpu(vf):
+    """vf_debug_fail_alloc: the countdown skips `after` allocations, fails the
+    next one with VF_ERR_OOM (6) and disarms itself; a negative value
+    disarms it.  vf_create's handle is a counted allocation."""
+    L = vf.lib()
+    ctx = ctypes.c_void_p()
+    assert vf.debug_fail_alloc(0) == -1
+    assert L.vf_create(ctypes.byref(ctx)) == 6 and not ctx.value
+    assert vf.debug_fail_alloc(-1) == -1                   # it disarmed itself
+    assert vf.debug_fail_alloc(1) == -1
+    assert L.vf_create(ctypes.byref(ctx)) == 0 and ctx.value
+    L.vf_destroy(ctx)
+    ctx = ctypes.c_void_p()
+    assert L.vf_create(ctypes.byref(ctx)) == 6 and not ctx.value
+    assert vf.debug_fail_alloc(5) == -1
+    assert vf.debug_fail_alloc(-7) == 5                    # disarmed before it fired
+    assert L.vf_create(ctypes.byref(ctx)) == 0
+    L.vf_destroy(ctx)
+    assert vf.debug_fail_alloc(-1) == -1
