@@ -587,50 +587,70 @@ __global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv
 }
 
 // ---- fused inference on the 5th-generation tensor cores (tcgen05): every
-// layer is an implicit GEMM over rows of 128 cells, M = 128 cells x N = 16
-// output channels x K = 16, one MMA per 3 x 3 tap (layer 1: per pair of tap
-// rows), accumulating in tensor memory (TMEM); BF16 operands staged in shared
-// memory in the K-major, unswizzled core-matrix layout, FP32 accumulation.
-// A tap's shifted rows are the same planar activations read from a start
-// address 16 bytes per cell further on, so no operand is ever gathered:
+// layer is an implicit GEMM over rows of 128 cells (M = 128 cells, K = 16
+// input channels), BF16 operands staged in shared memory in the K-major,
+// unswizzled core-matrix layout, FP32 accumulators in tensor memory (TMEM):
 //   x0  [row][130 cells][8 channels: R, G, B, 0 ...]          (16 B per cell)
 //   a1, a2  two such planes per layer (channels 0-7, 8-15)
-// and the A descriptor of a tap is its start cell, with the next K half one
-// plane further on (layer 1: one row further on, so that one MMA covers two
-// tap rows; the third tap row is paired with a zero weight row).  One thread
-// issues the MMAs of a layer and commits them to an mbarrier; after the
-// (bounded) wait, all eight warps read the accumulators back with tcgen05.ld
-// (warp w: TMEM lanes 32 (w mod 4) .. + 31, every other layer row), add the
-// bias, apply ReLU, round to BF16 and write the next layer's planes, or, for
-// layer 3 (whose three tap rows are the N columns of one accumulator per a2
-// row: 24 MMAs per tile instead of 54), the logit's flag and probability.
-// The MMAs of a layer are issued by two threads (rows alternating); at
-// N = 16 an MMA costs about as much as one of N = 64, so the tensor core's
-// issue time per tile, not its FLOP rate, bounds this kernel.  Outputs per CTA tile: 124 x 6
-// (the 128-cell rows shrink by 2 cells per 3 x 3 layer); two CTAs per SM,
-// persistent over the tiles.  Numerics as gate_infer_tc: BF16 input and
+// A tap's shifted cells are the same planar activations read from a start
+// address 16 bytes per cell further on, so no operand is ever gathered.
+//
+// The three tap rows of a 3 x 3 layer go to the MMA's N dimension instead of
+// to separate MMAs.  TMEM columns are blocks of 16, block b the accumulator
+// of output row b - 2.  One MMA takes one input row r (one tap column: A
+// shifted by 0, 1 or 2 cells) against the weights of all three tap rows laid
+// side by side along N in reverse order, and writes blocks r .. r + 2: block
+// r + g receives tap row 2 - g, which is exactly input row r's share of
+// output row r - 2 + g.  Every MMA accumulates onto its blocks, so the sum
+// over tap rows builds up in TMEM as the input rows stream past (a sliding
+// accumulator; the blocks are cleared beforehand with tcgen05.st):
+//   layer 1 (3 -> 16): K = 8 channels of row r and 8 of row r + 1 (the next
+//            K half one row further on), N = 64 (output rows r - 2 .. r + 1):
+//            6 row pairs x 3 tap columns = 18 MMAs per tile;
+//   layer 2 (16 -> 16): N = 48, 10 rows x 3 tap columns = 30 MMAs;
+//   layer 3 (16 -> 1): N = 48 with the tap columns in the first three
+//            columns of each block (the others zero weights), the cell
+//            shift applied afterwards (the output of cell x adds column v of
+//            cell x + v: warp shuffles, and shared memory across the lane
+//            quarters): 8 MMAs.
+// 56 MMAs per tile instead of 162 with one MMA of N = 16 per tap: at these
+// widths an MMA costs the tensor core nearly the same time whatever its N
+// (measured: 61 cycles back to back from one thread for N = 16 .. 64, 66 at
+// 128), so the count is what bounds the kernel.  One thread issues a layer's
+// MMAs (in order: they accumulate onto shared blocks) and commits them to an
+// mbarrier; after the (bounded) wait all eight warps read the accumulators
+// back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4) .. + 31, the blocks
+// of one parity), add the bias, apply ReLU, round to BF16 and write the next
+// layer's planes, then clear the blocks they own.  Outputs per CTA tile:
+// 124 x 6 (the 128-cell rows shrink by two cells per layer); two CTAs per
+// SM, persistent over the tiles.  Numerics as gate_infer_tc: BF16 input and
 // activations between layers, BF16 weights, FP32 accumulation and biases.
 constexpr int G5_X = 124, G5_Y = 6;                    // outputs per tile
 constexpr int G5_CW = 130;                             // cells per staged row
 constexpr int G5_RP = G5_CW * 16;                      // bytes per staged row
-constexpr int G5_R0 = G5_Y + 7, G5_R1 = G5_Y + 4, G5_R2 = G5_Y + 2;  // rows of x0, a1, a2
+constexpr int G5_R0 = G5_Y + 6, G5_R1 = G5_Y + 4, G5_R2 = G5_Y + 2;  // rows of x0, a1, a2
 constexpr int G5_A1P = G5_R1 * G5_RP, G5_A2P = G5_R2 * G5_RP;      // plane bytes
-constexpr int G5_BM = 512;                             // one 16 x 16 BF16 B operand
-constexpr int G5_NB = 6 + 9 + 3;                       // B operands of layers 1, 2, 3
-constexpr int G5_OFF_B = 0;
-constexpr int G5_OFF_BIAS = G5_OFF_B + G5_NB * G5_BM;
-constexpr int G5_ISSUERS = 2;                          // threads issuing a layer's MMAs
+constexpr int G5_N1 = 64, G5_N2 = 48, G5_N3 = 48;      // MMA widths of the layers
+constexpr int G5_B1 = 2 * G5_N1 * 16, G5_B2 = 2 * G5_N2 * 16;  // bytes of one B operand
+constexpr int G5_OFF_B1 = 0;                           // 3 tap columns each
+constexpr int G5_OFF_B2 = G5_OFF_B1 + 3 * G5_B1;
+constexpr int G5_OFF_B3 = G5_OFF_B2 + 3 * G5_B2;
+constexpr int G5_OFF_BIAS = G5_OFF_B3 + 2 * G5_N3 * 16;
 constexpr int G5_OFF_X0 = G5_OFF_BIAS + 256;           // x0, later a2 (x0 is dead by then)
 constexpr int G5_OFF_A1 = G5_OFF_X0 + 2 * G5_A2P;
 constexpr int G5_SMEM = G5_OFF_A1 + 2 * G5_A1P;
 constexpr int G5_THREADS = 256;
-constexpr int G5_TMEM_COLS = 256;                      // >= 16 columns x 10 layer-1 rows
+constexpr int G5_BLOCKS = G5_R0 + 2;                   // TMEM blocks (output rows -2 .. R0 - 1)
+constexpr int G5_TMEM_COLS = 256;
 static_assert(G5_R0 * G5_RP <= 2 * G5_A2P, "x0 fits in the a2 planes it shares");
 static_assert(G5_SMEM <= 113 * 1024, "two CTAs per SM");
-static_assert(16 * G5_R1 <= G5_TMEM_COLS, "a layer's accumulators fit the TMEM allocation");
+static_assert(16 * G5_BLOCKS <= G5_TMEM_COLS, "the accumulator blocks fit the TMEM allocation");
+static_assert(G5_R0 % 2 == 0, "layer 1 takes the x0 rows in pairs");
 // instruction descriptor (kind::f16): FP32 D, BF16 A and B, both K-major,
-// N = 16 (bits 17-22: N / 8), M = 128 (bits 24-28: M / 16)
-constexpr uint32_t G5_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (2u << 17) | (8u << 24);
+// N / 8 at bits 17-22, M / 16 = 8 (M = 128) at bits 24-28
+__host__ __device__ constexpr uint32_t g5_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | (8u << 24);
+}
 
 __device__ __forceinline__ uint32_t g5_smem(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -642,11 +662,13 @@ __device__ __forceinline__ uint64_t g5_desc(uint32_t addr, uint32_t lbo, uint32_
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void g5_mma(uint32_t d_tmem, uint64_t a, uint64_t b, bool acc) {
+// D[tmem] += A * B^T (every MMA accumulates: the blocks are cleared first)
+template <int N>
+__device__ __forceinline__ void g5_mma(uint32_t d_tmem, uint64_t a, uint64_t b) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(G5_IDESC), "r"((int)acc));
+      "l"(a), "l"(b), "r"(g5_idesc(N)), "r"(1));
 }
 // Bounded wait for the mbarrier phase `parity` (about a second at most);
 // false if it gave up.
@@ -671,8 +693,24 @@ __device__ __forceinline__ void g5_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+__device__ __forceinline__ uint32_t g5_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(r) : "r"(taddr));
+  return r;
+}
 __device__ __forceinline__ void g5_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+// Clears this warp's accumulator blocks (its 32 lanes, blocks b = h, h + 2,
+// ...) and waits for the stores.
+__device__ __forceinline__ void g5_clear(uint32_t lane_addr, int h) {
+  const uint32_t z = 0u;
+  for (int b = h; b < G5_BLOCKS; b += 2)
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1,%1};\n" ::"r"(lane_addr + 16 * b),
+        "r"(z));
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 __device__ __forceinline__ void g5_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -691,31 +729,45 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   __shared__ uint32_t s_taddr;
   __shared__ __align__(8) unsigned long long s_bar;
   __shared__ int s_ok;
+  __shared__ float s_edge[G5_Y][4][3];  // layer 3: lanes 0, 1 of each quarter, for lanes 30, 31
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, row parity
+  const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, block parity
   const int cell = 32 * q + lane;         // the cell (TMEM lane) this thread reads back
   const uint32_t bar = g5_smem(&s_bar);
   float* bias = reinterpret_cast<float*>(g5 + G5_OFF_BIAS);
 
-  // B operands (16 output channels x 16 K, [K half][n][8]) and biases, once
-  auto put_b = [&](int mat, int n, int k, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(g5 + G5_OFF_B + mat * G5_BM + (k >> 3) * 256 + n * 16 +
-                                      (k & 7) * 2) = __float2bfloat16_rn(v);
-  };
-  for (int e = tid; e < G5_NB * 256; e += G5_THREADS) {
-    const int mat = e >> 8, n = (e >> 4) & 15, k = e & 15;
+  // B operands ([K half][n][8 k], 16 bytes per n) and biases, once.  Column
+  // group g of an operand (n = 16 g + o) holds tap row 2 - g (layer 1's
+  // second K half, the next input row: tap row 3 - g).
+  for (int e = tid; e < 3 * G5_N1 * 16 + 3 * G5_N2 * 16 + G5_N3 * 16; e += G5_THREADS) {
+    int off, nn, idx;
     float v = 0.0f;
-    if (mat < 6) {  // layer 1, tap rows (2p, 2p + 1), tap column v: K = (row, channel)
-      const int p = mat / 3, tv = mat % 3, u = 2 * p + (k >> 3), c = k & 7;
-      if (u <= 2 && c < 3) v = __bfloat162float(wb[OFF_W1 + ((n * 3 + c) * 3 + u) * 3 + tv]);
-    } else if (mat < 15) {  // layer 2, tap (u, v): K = input channel
-      const int t = mat - 6;
-      v = __bfloat162float(wb[OFF_W2 + (n * kC + k) * 9 + t]);
-    } else {  // layer 3, tap column v: N = tap row u (one output channel; u < 3)
-      const int tv = mat - 15;
-      if (n < 3) v = __bfloat162float(wb[OFF_W3 + k * 9 + n * 3 + tv]);
+    if (e < 3 * G5_N1 * 16) {  // layer 1, tap column tv: K = (row half, channel)
+      const int tv = e / (G5_N1 * 16);
+      idx = e % (G5_N1 * 16);
+      nn = G5_N1;
+      off = G5_OFF_B1 + tv * G5_B1;
+      const int n = idx >> 4, k = idx & 15, g = n >> 4, o = n & 15, c = k & 7;
+      const int u = 2 - g + (k >> 3);
+      if (u >= 0 && u <= 2 && c < 3)
+        v = __bfloat162float(wb[OFF_W1 + ((o * 3 + c) * 3 + u) * 3 + tv]);
+    } else if (e < 3 * G5_N1 * 16 + 3 * G5_N2 * 16) {  // layer 2: K = input channel
+      const int e2 = e - 3 * G5_N1 * 16, tv = e2 / (G5_N2 * 16);
+      idx = e2 % (G5_N2 * 16);
+      nn = G5_N2;
+      off = G5_OFF_B2 + tv * G5_B2;
+      const int n = idx >> 4, k = idx & 15, g = n >> 4, o = n & 15;
+      v = __bfloat162float(wb[OFF_W2 + (o * kC + k) * 9 + (2 - g) * 3 + tv]);
+    } else {  // layer 3: column 16 g + tv of block g is tap (2 - g, tv)
+      idx = e - 3 * G5_N1 * 16 - 3 * G5_N2 * 16;
+      nn = G5_N3;
+      off = G5_OFF_B3;
+      const int n = idx >> 4, k = idx & 15, g = n >> 4, tv = n & 15;
+      if (tv < 3) v = __bfloat162float(wb[OFF_W3 + k * 9 + (2 - g) * 3 + tv]);
     }
-    put_b(mat, n, k, v);
+    const int n = idx >> 4, k = idx & 15;
+    *reinterpret_cast<__nv_bfloat16*>(g5 + off + (k >> 3) * (nn * 16) + n * 16 + (k & 7) * 2) =
+        __float2bfloat16_rn(v);
   }
   if (tid < kC) bias[tid] = __bfloat162float(wb[OFF_B1 + tid]);
   else if (tid < 2 * kC) bias[tid] = __bfloat162float(wb[OFF_B2 + tid - kC]);
@@ -727,7 +779,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
         make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(G5_ISSUERS));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -741,6 +793,8 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   g5_fence_after();
   const uint32_t tmem = s_taddr;
   const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+  g5_clear(lane_addr, h);  // the first tile's accumulators
+  g5_fence_before();
   uint32_t parity = 0;
   const bool word = I.channels == 4 && (reinterpret_cast<uintptr_t>(I.img) & 3) == 0 &&
                     (I.pitch & 3) == 0;
@@ -750,8 +804,10 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   const uint64_t dx0 = g5_desc(g5_smem(g5 + G5_OFF_X0), G5_RP, 128);
   const uint64_t da1 = g5_desc(g5_smem(g5 + G5_OFF_A1), G5_A1P, 128);
   const uint64_t da2 = g5_desc(g5_smem(g5 + G5_OFF_X0), G5_A2P, 128);
-  const uint64_t dbm = g5_desc(g5_smem(g5 + G5_OFF_B), 256, 128);
-  constexpr uint64_t kCellD = 1, kRowD = G5_RP / 16, kMatD = G5_BM / 16;
+  const uint64_t db1 = g5_desc(g5_smem(g5 + G5_OFF_B1), G5_N1 * 16, 128);
+  const uint64_t db2 = g5_desc(g5_smem(g5 + G5_OFF_B2), G5_N2 * 16, 128);
+  const uint64_t db3 = g5_desc(g5_smem(g5 + G5_OFF_B3), G5_N3 * 16, 128);
+  constexpr uint64_t kCellD = 1, kRowD = G5_RP / 16, kB1D = G5_B1 / 16, kB2D = G5_B2 / 16;
   // the next tile's input pixels, loaded while the tile's last layer runs
   constexpr int kPre = (G5_R0 * G5_CW + G5_THREADS - 1) / G5_THREADS;
   uint32_t pre[kPre];
@@ -763,8 +819,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       const int r = e / G5_CW, c = e - r * G5_CW;
       const int gy = ys - 3 + r, gx = xs - 3 + c;
       uint32_t px = 0xffffffffu;  // marks a cell outside the image (zero input)
-      if (e < G5_R0 * G5_CW && r < G5_Y + 6 && t < ntiles && gy >= 0 && gy < I.H && gx >= 0 &&
-          gx < I.W) {
+      if (e < G5_R0 * G5_CW && t < ntiles && gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) {
         const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
         if (word) px = *reinterpret_cast<const uint32_t*>(src) & 0x00ffffffu;
         else px = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
@@ -773,20 +828,18 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     }
   };
 
-  // one layer: lane 0 of warps 0 .. G5_ISSUERS - 1 each issue the MMAs of
-  // every G5_ISSUERS-th row and commit them (the mbarrier counts one arrival
-  // per issuer); thread 0 waits on the mbarrier, the others at the barrier
-  // after it
+  // one layer: thread 0 issues its MMAs (in order) and commits them to the
+  // mbarrier, then waits on it; the others wait at the barrier after it
   auto run_layer = [&](auto issue) -> bool {
     g5_proxy_fence();  // the generic-proxy writes of the operands, for the tensor cores
     __syncthreads();
-    if (lane == 0 && warp < G5_ISSUERS) {
+    if (tid == 0) {
       g5_fence_after();
-      issue(warp);
+      issue();
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               bar));
-      if (tid == 0) s_ok = g5_wait(bar, parity) ? 1 : 0;
+      s_ok = g5_wait(bar, parity) ? 1 : 0;
     }
     __syncthreads();
     parity ^= 1u;
@@ -798,9 +851,8 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   fetch(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int xs = (tile % tiles_x) * G5_X, ys = (tile / tiles_x) * G5_Y;
-    // x0 rows ys - 3 .. ys + G5_Y + 3, cells xs - 3 .. xs + 126 (zero outside
-    // the image, and the extra row below that pairs with the third tap row),
-    // from the pixels fetched during the previous tile
+    // x0 rows ys - 3 .. ys + G5_Y + 2, cells xs - 3 .. xs + 126 (zero outside
+    // the image), from the pixels fetched during the previous tile
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
       const int e = tid + j * G5_THREADS;
@@ -817,25 +869,23 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       }
       *reinterpret_cast<uint4*>(g5 + G5_OFF_X0 + r * G5_RP + c * 16) = make_uint4(w01, w23, 0u, 0u);
     }
-    // layer 1: rows y = 0 .. G5_R1 - 1 of 128 cells, tap rows (0, 1) and (2, 3)
-    ok = run_layer([&](int first) {
-      for (int y = first; y < G5_R1; y += G5_ISSUERS)
-        for (int p = 0; p < 2; ++p)
-          for (int v = 0; v < 3; ++v)
-            g5_mma(tmem + 16 * y, dx0 + (y + 2 * p) * kRowD + v * kCellD,
-                   dbm + (p * 3 + v) * kMatD, p + v > 0);
+    // layer 1: x0 row pairs (r, r + 1), r even, into blocks r .. r + 3
+    ok = run_layer([&] {
+      for (int r = 0; r < G5_R0; r += 2)
+        for (int v = 0; v < 3; ++v)
+          g5_mma<G5_N1>(tmem + 16 * r, dx0 + r * kRowD + v * kCellD, db1 + v * kB1D);
     });
     if (!ok) break;
-    // this thread's rows y (every other one) of a layer, two tcgen05.ld per
-    // wait: z + bias, ReLU, BF16, into the next layer's two planes (0 outside
-    // the image)
+    // this thread's output rows (block parity h), two tcgen05.ld per wait:
+    // z + bias, ReLU, BF16, into the next layer's two planes (0 outside the
+    // image); then its blocks are cleared for the next layer
     auto act_rows = [&](int rows, int gy0, int gx0, const float* b, unsigned char* planes,
                         int plane_bytes) {
       for (int y = h; y < rows; y += 4) {
         uint32_t z[2][16];
         const bool two = y + 2 < rows;
-        g5_ld16(lane_addr + 16 * y, z[0]);
-        if (two) g5_ld16(lane_addr + 16 * (y + 2), z[1]);
+        g5_ld16(lane_addr + 16 * (y + 2), z[0]);
+        if (two) g5_ld16(lane_addr + 16 * (y + 4), z[1]);
         g5_wait_ld();
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -853,50 +903,71 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
           *reinterpret_cast<uint4*>(dst + plane_bytes) = make_uint4(w[4], w[5], w[6], w[7]);
         }
       }
+      g5_clear(lane_addr, h);
+      g5_fence_before();
     };
     act_rows(G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
-    g5_fence_before();
-    // layer 2: rows y = 0 .. G5_R2 - 1, 9 taps
-    ok = run_layer([&](int first) {
-      for (int y = first; y < G5_R2; y += G5_ISSUERS)
-        for (int t = 0; t < 9; ++t)
-          g5_mma(tmem + 16 * y, da1 + (y + t / 3) * kRowD + (t % 3) * kCellD,
-                 dbm + (6 + t) * kMatD, t > 0);
+    // layer 2: a1 rows r, shifted by tap column v, into blocks r .. r + 2
+    ok = run_layer([&] {
+      for (int r = 0; r < G5_R1; ++r)
+        for (int v = 0; v < 3; ++v)
+          g5_mma<G5_N2>(tmem + 16 * r, da1 + r * kRowD + v * kCellD, db2 + v * kB2D);
     });
     if (!ok) break;
     act_rows(G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);  // a2 over x0
-    g5_fence_before();
-    // layer 3 (one output channel): the tap rows go to N instead of to nine
-    // MMAs: for every a2 row y', three MMAs (tap columns v, A shifted by v
-    // cells) give D_y'[cell][u] = sum_v sum_c a2[y'][cell + v][c] W3[c][u][v];
-    // output row y is D_y[.][0] + D_(y+1)[.][1] + D_(y+2)[.][2].  The next
-    // tile's pixels are fetched while the MMAs run.
+    // layer 3 (one output channel): a2 rows r, unshifted, into blocks r ..
+    // r + 2; column v of output row y's block is the sum over the tap row
+    // and channels for tap column v at this cell.  The next tile's pixels
+    // are fetched while the MMAs run.
     fetch(tile + gridDim.x);
-    ok = run_layer([&](int first) {
-      for (int y = first; y < G5_R2; y += G5_ISSUERS)
-        for (int v = 0; v < 3; ++v)
-          g5_mma(tmem + 16 * y, da2 + y * kRowD + v * kCellD, dbm + (15 + v) * kMatD, v > 0);
+    ok = run_layer([&] {
+      for (int r = 0; r < G5_R2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
     });
     if (!ok) break;
-    for (int y = h; y < G5_Y; y += 2) {
-      uint32_t r0, r1, r2;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
-                   : "=r"(r0) : "r"(lane_addr + 16 * y));
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
-                   : "=r"(r1) : "r"(lane_addr + 16 * (y + 1) + 1));
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n"
-                   : "=r"(r2) : "r"(lane_addr + 16 * (y + 2) + 2));
-      g5_wait_ld();
-      const float z =
-          (__uint_as_float(r0) + __uint_as_float(r1)) + __uint_as_float(r2) + bias[2 * kC];
+    // logit of cell x: column 0 of cell x + column 1 of cell x + 1 + column 2
+    // of cell x + 2 (shuffles; the next lane quarter's first lanes through
+    // shared memory)
+    float c0[3], c1[3], c2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int y = h + 2 * i;
+      const uint32_t a = lane_addr + 16 * (y + 2);
+      c0[i] = __uint_as_float(g5_ld1(a));
+      c1[i] = __uint_as_float(g5_ld1(a + 1));
+      c2[i] = __uint_as_float(g5_ld1(a + 2));
+    }
+    g5_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int y = h + 2 * i;
+      if (lane == 0) {
+        s_edge[y][q][0] = c1[i];
+        s_edge[y][q][1] = c2[i];
+      } else if (lane == 1) {
+        s_edge[y][q][2] = c2[i];
+      }
+    }
+    g5_clear(lane_addr, h);  // the next tile's layer-1 accumulators
+    g5_fence_before();
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int y = h + 2 * i;
+      float s1 = __shfl_down_sync(0xffffffffu, c1[i], 1);
+      float s2 = __shfl_down_sync(0xffffffffu, c2[i], 2);
+      if (q < 3) {
+        if (lane == 31) s1 = s_edge[y][q + 1][0];
+        if (lane == 30) s2 = s_edge[y][q + 1][1];
+        if (lane == 31) s2 = s_edge[y][q + 1][2];
+      }
+      const float z = (c0[i] + s1) + s2 + bias[2 * kC];
       const int gy = ys + y, gx = xs + cell;
       if (cell < G5_X && gy < I.H && gx < I.W) {
         if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
         if (prob) prob[(long long)gy * I.W + gx] = 1.0f / (1.0f + expf(-z));
       }
     }
-    g5_fence_before();
-    __syncthreads();  // the tile's reads of TMEM and of the x0 / a2 planes are done
+    __syncthreads();  // the tile's reads of the x0 / a2 planes and of s_edge are done
   }
   if (!ok && tid == 0) atomicExch(status, 1);
   g5_fence_before();
