@@ -382,6 +382,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
+// max(lo, 0), max(hi, 0) rounded to BF16 and packed (lo in the low half): one
+// conversion with ReLU (the rounding keeps the sign, so ReLU before or after
+// it gives the same value)
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                          uint32_t b1) {
@@ -638,7 +646,8 @@ constexpr int G5_OFF_B3 = G5_OFF_B2 + 3 * G5_B2;
 constexpr int G5_OFF_BIAS = G5_OFF_B3 + 2 * G5_N3 * 16;
 constexpr int G5_OFF_X0 = G5_OFF_BIAS + 256;           // x0, later a2 (x0 is dead by then)
 constexpr int G5_OFF_A1 = G5_OFF_X0 + 2 * G5_A2P;
-constexpr int G5_SMEM = G5_OFF_A1 + 2 * G5_A1P;
+constexpr int G5_OFF_RAW = G5_OFF_A1 + 2 * G5_A1P;      // the next tile's pixels (32-bit)
+constexpr int G5_SMEM = G5_OFF_RAW + G5_R0 * G5_CW * 4;
 constexpr int G5_THREADS = 256;
 constexpr int G5_BLOCKS = G5_R0 + 2;                   // TMEM blocks (output rows -2 .. R0 - 1)
 constexpr int G5_TMEM_COLS = 256;
@@ -808,30 +817,45 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   const uint64_t db2 = g5_desc(g5_smem(g5 + G5_OFF_B2), G5_N2 * 16, 128);
   const uint64_t db3 = g5_desc(g5_smem(g5 + G5_OFF_B3), G5_N3 * 16, 128);
   constexpr uint64_t kCellD = 1, kRowD = G5_RP / 16, kB1D = G5_B1 / 16, kB2D = G5_B2 / 16;
-  // the next tile's input pixels, loaded while the tile's last layer runs
+  // the next tile's input pixels, fetched while the tile's last layer runs:
+  // RGBX words copied asynchronously (cp.async, no register waits on them)
+  // into the raw buffer, 3-byte pixels into registers; bit j of pre_in set
+  // where word j is a pixel of the image (zero input elsewhere).  Each
+  // thread later reads back only the words it fetched.
   constexpr int kPre = (G5_R0 * G5_CW + G5_THREADS - 1) / G5_THREADS;
-  uint32_t pre[kPre];
+  static_assert(kPre <= 32, "one validity bit per fetched word");
+  uint32_t pre[kPre], pre_in = 0u;
+  uint32_t* raw = reinterpret_cast<uint32_t*>(g5 + G5_OFF_RAW);
   auto fetch = [&](int t) {
     const int xs = (t % tiles_x) * G5_X, ys = (t / tiles_x) * G5_Y;
+    pre_in = 0u;
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
       const int e = tid + j * G5_THREADS;
       const int r = e / G5_CW, c = e - r * G5_CW;
       const int gy = ys - 3 + r, gx = xs - 3 + c;
-      uint32_t px = 0xffffffffu;  // marks a cell outside the image (zero input)
-      if (e < G5_R0 * G5_CW && t < ntiles && gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) {
-        const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
-        if (word) px = *reinterpret_cast<const uint32_t*>(src) & 0x00ffffffu;
-        else px = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
-      }
-      pre[j] = px;
+      const bool in =
+          e < G5_R0 * G5_CW && t < ntiles && gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
+      pre_in |= in ? 1u << j : 0u;
+      if (!in) continue;
+      const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
+      if (word)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(g5_smem(raw + e)),
+                     "l"(src)
+                     : "memory");
+      else
+        pre[j] = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
 
   // one layer: thread 0 issues its MMAs (in order) and commits them to the
-  // mbarrier, then waits on it; the others wait at the barrier after it
-  auto run_layer = [&](auto issue) -> bool {
+  // mbarrier, then waits on it; the others wait at the barrier after it.
+  // `before` runs between the proxy fence and the barrier (global loads
+  // issued there are in flight while the MMAs run)
+  auto run_layer = [&](auto issue, auto before) -> bool {
     g5_proxy_fence();  // the generic-proxy writes of the operands, for the tensor cores
+    before();
     __syncthreads();
     if (tid == 0) {
       g5_fence_after();
@@ -853,14 +877,15 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     const int xs = (tile % tiles_x) * G5_X, ys = (tile / tiles_x) * G5_Y;
     // x0 rows ys - 3 .. ys + G5_Y + 2, cells xs - 3 .. xs + 126 (zero outside
     // the image), from the pixels fetched during the previous tile
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
       const int e = tid + j * G5_THREADS;
       if (e >= G5_R0 * G5_CW) break;
       const int r = e / G5_CW, c = e - r * G5_CW;
-      const uint32_t px = pre[j];
+      const uint32_t px = word ? raw[e] : pre[j];
       uint32_t w01 = 0u, w23 = 0u;
-      if (px != 0xffffffffu) {
+      if ((pre_in >> j) & 1u) {
         const float cr = (float)(px & 255u) * (1.0f / 255.0f) - 0.5f;
         const float cg = (float)((px >> 8) & 255u) * (1.0f / 255.0f) - 0.5f;
         const float cb = (float)((px >> 16) & 255u) * (1.0f / 255.0f) - 0.5f;
@@ -874,13 +899,16 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       for (int r = 0; r < G5_R0; r += 2)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N1>(tmem + 16 * r, dx0 + r * kRowD + v * kCellD, db1 + v * kB1D);
-    });
+    }, [] {});
     if (!ok) break;
     // this thread's output rows (block parity h), two tcgen05.ld per wait:
     // z + bias, ReLU, BF16, into the next layer's two planes (0 outside the
     // image); then its blocks are cleared for the next layer
-    auto act_rows = [&](int rows, int gy0, int gx0, const float* b, unsigned char* planes,
+    auto act_rows = [&](int rows, int gy0, int gx0, const float* bs, unsigned char* planes,
                         int plane_bytes) {
+      float b[16];  // in registers: the stores below may not alias them
+#pragma unroll
+      for (int k = 0; k < 16; ++k) b[k] = bs[k];
       for (int y = h; y < rows; y += 4) {
         uint32_t z[2][16];
         const bool two = y + 2 < rows;
@@ -895,8 +923,8 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
           uint32_t w[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k)
-            w[k] = in ? pack_bf16(fmaxf(__uint_as_float(z[i][2 * k]) + b[2 * k], 0.0f),
-                                  fmaxf(__uint_as_float(z[i][2 * k + 1]) + b[2 * k + 1], 0.0f))
+            w[k] = in ? pack_bf16_relu(__uint_as_float(z[i][2 * k]) + b[2 * k],
+                                       __uint_as_float(z[i][2 * k + 1]) + b[2 * k + 1])
                       : 0u;
           unsigned char* dst = planes + yy * G5_RP + cell * 16;
           *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -912,21 +940,21 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       for (int r = 0; r < G5_R1; ++r)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N2>(tmem + 16 * r, da1 + r * kRowD + v * kCellD, db2 + v * kB2D);
-    });
+    }, [] {});
     if (!ok) break;
     act_rows(G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);  // a2 over x0
     // layer 3 (one output channel): a2 rows r, unshifted, into blocks r ..
     // r + 2; column v of output row y's block is the sum over the tap row
     // and channels for tap column v at this cell.  The next tile's pixels
     // are fetched while the MMAs run.
-    fetch(tile + gridDim.x);
     ok = run_layer([&] {
       for (int r = 0; r < G5_R2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
-    });
+    }, [&] { fetch(tile + gridDim.x); });
     if (!ok) break;
     // logit of cell x: column 0 of cell x + column 1 of cell x + 1 + column 2
     // of cell x + 2 (shuffles; the next lane quarter's first lanes through
     // shared memory)
+    const float b3 = bias[2 * kC];
     float c0[3], c1[3], c2[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -960,7 +988,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
         if (lane == 30) s2 = s_edge[y][q + 1][1];
         if (lane == 31) s2 = s_edge[y][q + 1][2];
       }
-      const float z = (c0[i] + s1) + s2 + bias[2 * kC];
+      const float z = (c0[i] + s1) + s2 + b3;
       const int gy = ys + y, gx = xs + cell;
       if (cell < G5_X && gy < I.H && gx < I.W) {
         if (flags) flags[(long long)gy * flag_pitch + gx] = z > logit_threshold ? 1 : 0;
