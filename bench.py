@@ -993,6 +993,60 @@ def bench_gate(frames=64, train_steps=800):
 
     ms_plain, ms_gate, ms_gated = timed(plain), timed(gate_only), timed(gated)
     ms_exact = timed(exact)
+
+    # the forms of the gated filter on single frames along the ramp: the
+    # pair-reuse tiles (every tile holding a flag runs in full), the
+    # per-window tiles (the flagged pixels of each tile compacted, one window
+    # each) and the sparse form (the flagged pixels of the image listed, one
+    # window each); which pays depends on the flagged fraction
+    def one(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(3):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 3
+
+    per_frame = []
+    for f in sorted({0, frames // 4, frames // 2, 3 * frames // 4, frames - 1}):
+        x, fl = noisy_d[f], flags[0]
+        gate.infer(x, 0.5, flags=fl, stream=stream)
+        frac = fl.float().mean().item()
+        t_plain = one(lambda: vfilt.filter(x, out_plain[0], stream=stream, **kw))
+        t_gate = one(lambda: gate.infer(x, 0.5, flags=fl, stream=stream))
+        t_reuse = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
+        vfilt.set_option("pair_reuse", 0)
+        try:
+            t_win = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
+        finally:
+            vfilt.set_option("pair_reuse", 1)
+        vfilt.set_option("gated_sparse", 1000)
+        try:
+            t_sparse = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
+        finally:
+            vfilt.set_option("gated_sparse", 0)
+        # the same with the gate trained on the generator's masks alone
+        fm = flags[1]
+        gate_mask.infer(x, 0.5, flags=fm, stream=stream)
+        frac_m = fm.float().mean().item()
+        t_reuse_m = one(lambda: vfilt.filter_gated(x, fm, out_gated[0], stream=stream, **kw))
+        vfilt.set_option("gated_sparse", 1000)
+        try:
+            t_sparse_m = one(lambda: vfilt.filter_gated(x, fm, out_gated[0], stream=stream, **kw))
+        finally:
+            vfilt.set_option("gated_sparse", 0)
+        best = min(t_reuse, t_win, t_sparse)
+        per_frame.append({"frame": f, "flagged": round(frac, 4), "plain_ms": round(t_plain, 3),
+                          "gate_ms": round(t_gate, 3), "gated_reuse_ms": round(t_reuse, 3),
+                          "gated_window_ms": round(t_win, 3),
+                          "gated_sparse_ms": round(t_sparse, 3),
+                          "speedup_best_form": round(t_plain / (t_gate + best), 3),
+                          "mask_gate_flagged": round(frac_m, 4),
+                          "mask_gate_sparse_ms": round(t_sparse_m, 3),
+                          "mask_gate_speedup_best_form":
+                              round(t_plain / (t_gate + min(t_reuse_m, t_sparse_m)), 3)})
     # quality, untimed
     ps_plain, ps_gated, ps_mask, ps_noisy, differ, flagged = [], [], [], [], [], []
 
@@ -1035,7 +1089,8 @@ def bench_gate(frames=64, train_steps=800):
             "psnr_plain_db_mean": round(float(np.mean(ps_plain)), 3),
             "psnr_gated_db_mean": round(float(np.mean(ps_gated)), 3),
             "gated_differs_from_plain_mean": round(float(np.mean(differ)), 4),
-            "frames_generated_s": round(gen_s, 1), "gpu_launches_gated": 2 * frames}
+            "frames_generated_s": round(gen_s, 1), "gpu_launches_gated": 2 * frames,
+            "per_frame_forms": per_frame}
 
 
 def run_case(args):

@@ -143,8 +143,9 @@ const char* vf_last_error(const vf_ctx* ctx);
  *                      windows; the EVMF work-queue kernel picks its own).
  *   VF_OPT_GATE_TENSOR_CORES  the engine of vf_gate_infer: 1 (default) the
  *                      three convolutions on the 5th-generation tensor cores
- *                      (tcgen05 MMAs with TMEM accumulators, one per 3 x 3
- *                      tap over rows of 128 cells); 2 the warp-level mma
+ *                      (tcgen05 MMAs with TMEM accumulators over rows of 128
+ *                      cells, a layer's three tap rows side by side in one
+ *                      MMA's N dimension); 2 the warp-level mma
  *                      instructions of earlier tensor cores; both with BF16
  *                      operands (activations rounded to BF16 between layers)
  *                      and FP32 accumulation; 0: CUDA cores with FP32
@@ -155,12 +156,22 @@ const char* vf_last_error(const vf_ctx* ctx);
  *                      drains, and wait for its completion (and the
  *                      visibility of its memory) before their first access
  *                      to device memory, so stream order is kept; 0: plain
- *                      launches. */
+ *                      launches.
+ *   VF_OPT_GATED_SPARSE  vf_filter_gated's sparse form, in flagged pixels per
+ *                      mille (0 .. 1000): a first kernel copies the
+ *                      unflagged pixels and lists the flagged ones, a second
+ *                      filters the listed pixels one window each; when the
+ *                      list holds more than that many per mille of the
+ *                      pixels, the tile form runs instead (the choice is made
+ *                      on the device, from the list's length: no host
+ *                      synchronisation).  0 (default): the tile form only;
+ *                      1000: the sparse form only. */
 typedef enum {
   VF_OPT_PAIR_REUSE = 0,
   VF_OPT_TILE_ROWS = 1,
   VF_OPT_GATE_TENSOR_CORES = 2,
-  VF_OPT_OVERLAP_LAUNCH = 3
+  VF_OPT_OVERLAP_LAUNCH = 3,
+  VF_OPT_GATED_SPARSE = 4
 } vf_option;
 vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value);
 

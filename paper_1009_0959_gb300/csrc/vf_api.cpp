@@ -59,6 +59,10 @@ struct vf_ctx {
   int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF, EVBDF), 2 always
   int gate_tc = 1;     // gate inference: 0 CUDA cores, 1 tcgen05, 2 warp-level mma
   int overlap = 1;     // programmatic dependent launches for vf_filter
+  int gated_sparse = 0;  // vf_filter_gated: sparse form up to this many flagged per mille
+  int* d_glist = nullptr;  // its pixel list and counter
+  unsigned* d_gcount = nullptr;
+  size_t glist_cap = 0;
   // device staging of vf_filter_host (grown on demand, freed by vf_destroy)
   uint8_t* d_stage = nullptr;
   size_t stage_bytes = 0;
@@ -135,6 +139,8 @@ vf_status vf_create(vf_ctx** ctx) {
 void vf_destroy(vf_ctx* ctx) {
   if (!ctx) return;
   if (ctx->d_stage) cudaFree(ctx->d_stage);
+  if (ctx->d_glist) cudaFree(ctx->d_glist);
+  if (ctx->d_gcount) cudaFree(ctx->d_gcount);
   for (auto& sl : ctx->slots) {
     if (sl.stream) {
       cudaStreamSynchronize(sl.stream);
@@ -173,6 +179,10 @@ vf_status vf_set_option(vf_ctx* ctx, vf_option opt, int value) {
       ctx->gate_tc = value;
       return VF_OK;
     case VF_OPT_OVERLAP_LAUNCH: ctx->overlap = value != 0; return VF_OK;
+    case VF_OPT_GATED_SPARSE:
+      if (value < 0 || value > 1000) return fail(ctx, VF_ERR_ARG, "gated sparse 0 .. 1000");
+      ctx->gated_sparse = value;
+      return VF_OK;
     case VF_OPT_TILE_ROWS:
       if (value != 2 && value != 4 && value != 8) return fail(ctx, VF_ERR_ARG, "tile rows 2, 4 or 8");
       ctx->tile_rows = value;
@@ -520,6 +530,33 @@ vf_status launch_single(vf_ctx* ctx, Launch L, const LaunchClass& cls, cudaStrea
                       : launch_packed(L, cls.precision, cls.crit, cls.w, cls.apx, cls.deg, ty,
                                       (int)grid, s);
   if (e != cudaSuccess) return fail(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+  return VF_OK;
+}
+
+int gated_sparse_permille(const vf_ctx* ctx) { return ctx->gated_sparse; }
+
+vf_status gated_scratch(vf_ctx* ctx, size_t pixels, int** list, unsigned** count) {
+  if (!ctx->d_gcount && device_alloc(&ctx->d_gcount, sizeof(unsigned)) != cudaSuccess) {
+    ctx->d_gcount = nullptr;
+    cudaGetLastError();
+    return fail(ctx, VF_ERR_OOM, "gated list allocation failed");
+  }
+  if (pixels > ctx->glist_cap) {
+    if (ctx->d_glist) {
+      cudaDeviceSynchronize();  // earlier calls may still read the old list
+      cudaFree(ctx->d_glist);
+    }
+    ctx->d_glist = nullptr;
+    ctx->glist_cap = 0;
+    if (device_alloc(&ctx->d_glist, pixels * sizeof(int)) != cudaSuccess) {
+      ctx->d_glist = nullptr;
+      cudaGetLastError();
+      return fail(ctx, VF_ERR_OOM, "gated list allocation failed");
+    }
+    ctx->glist_cap = pixels;
+  }
+  *list = ctx->d_glist;
+  *count = ctx->d_gcount;
   return VF_OK;
 }
 

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "vf_internal.h"
+#include "vf_kernels.cuh"
 
 namespace vf {
 cudaError_t launch_gated_w3(const Launch&, const uint8_t*, long long, int, int, int, int, int,
@@ -29,6 +30,12 @@ cudaError_t launch_gated_w5(const Launch&, const uint8_t*, long long, int, int, 
                             cudaStream_t);
 cudaError_t launch_gated_w7(const Launch&, const uint8_t*, long long, int, int, int, int, int,
                             cudaStream_t);
+cudaError_t launch_sparse_w3(const Launch&, const int*, const unsigned*, unsigned, int, int, int,
+                             int, cudaStream_t);
+cudaError_t launch_sparse_w5(const Launch&, const int*, const unsigned*, unsigned, int, int, int,
+                             int, cudaStream_t);
+cudaError_t launch_sparse_w7(const Launch&, const int*, const unsigned*, unsigned, int, int, int,
+                             int, cudaStream_t);
 }  // namespace vf
 
 namespace {
@@ -1117,6 +1124,35 @@ vf_status run_train(vf_gate* g, const Images& I, const uint8_t* targets, cudaStr
   return VF_OK;
 }
 
+
+// Sparse form of the gated filter, first kernel: every unflagged pixel is
+// copied and every flagged one listed (y * width + x; warp-aggregated
+// appends, so the list's order varies between runs -- a listed pixel's
+// output does not depend on it).
+__global__ void __launch_bounds__(256)
+    gated_compact(const __grid_constant__ Launch L, const uint8_t* __restrict__ flags,
+                  long long flag_pitch, int* __restrict__ list, unsigned* __restrict__ count) {
+  const long long total = (long long)L.width * L.height;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < total; i0 += step) {
+    const long long i = i0 + threadIdx.x;  // the loop is uniform over the block
+    bool f = false;
+    if (i < total) {
+      const int y = (int)(i / L.width), x = (int)(i - (long long)y * L.width);
+      f = flags[(long long)y * flag_pitch + x] != 0;
+      if (!f) store_px(L, x, y, load_px(L, x, y));
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (m != 0u) {
+      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+      unsigned base = 0u;
+      if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (f) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1300,6 +1336,39 @@ vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int 
   if (cls.crit == kEVMF || cls.crit == kEVBDF || cls.precision != VF_FP32)
     return set_error(ctx, VF_ERR_UNSUPPORTED, "the gated form runs VMF, BVDF and AMNF in FP32");
   cudaStream_t s = (cudaStream_t)stream;
+  // the sparse form (VF_OPT_GATED_SPARSE): compaction, then one window per
+  // listed pixel if the list is short enough; the tile form below then
+  // returns at once (the choice is read on the device, from the counter)
+  const int permille = gated_sparse_permille(ctx);
+  const long long total = (long long)width * height;
+  if (permille > 0 && total <= 0x7fffffffLL) {
+    int* list = nullptr;
+    unsigned* count = nullptr;
+    st = gated_scratch(ctx, (size_t)total, &list, &count);
+    if (st != VF_OK) return st;
+    const unsigned limit =
+        permille >= 1000 ? 0xffffffffu : (unsigned)(total * permille / 1000);
+    int dev = 0, sms = 1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+      const long long blocks = std::min<long long>((total + 255) / 256, 8LL * sms);
+      gated_compact<<<(int)blocks, 256, 0, s>>>(L, d_flags, (long long)flag_pitch, list, count);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      switch (cls.w) {
+        case 3: e = launch_sparse_w3(L, list, count, limit, sms, cls.crit, cls.apx, cls.deg, s); break;
+        case 5: e = launch_sparse_w5(L, list, count, limit, sms, cls.crit, cls.apx, cls.deg, s); break;
+        default: e = launch_sparse_w7(L, list, count, limit, sms, cls.crit, cls.apx, cls.deg, s); break;
+      }
+    }
+    if (e != cudaSuccess) return set_error(ctx, VF_ERR_CUDA, cudaGetErrorString(e));
+    if (permille >= 1000) return VF_OK;
+    L.gate_count = count;
+    L.gate_limit = limit;
+  }
   if (use_pair_reuse(ctx, cls.w, cls.crit)) {
     // the pair-reuse tiles with the flags read in the finish phase (and
     // whole tiles without a flag copied): every pair term of a tile is

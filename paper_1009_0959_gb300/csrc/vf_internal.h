@@ -46,6 +46,10 @@ struct Launch {
   // whose flag byte is non-zero, copy the others (null for every other call)
   const uint8_t* flags;
   long long flag_pitch;
+  // the gated filter's tile forms when the sparse form may take the call: a
+  // CTA returns at once if *gate_count <= gate_limit (null otherwise)
+  const unsigned* gate_count;
+  unsigned gate_limit;
 };
 
 // Register aggregates (fully unrolled pair loop) or shared-memory aggregate
@@ -168,6 +172,10 @@ vf_status launch_single(vf_ctx* ctx, Launch L, const LaunchClass& cls, cudaStrea
 
 // Gate inference engine (context option): 0 CUDA cores, 1 tcgen05, 2 mma.sync.
 int gate_tensor_cores(const vf_ctx* ctx);
+// VF_OPT_GATED_SPARSE (per mille of the pixels) and the sparse form's scratch:
+// a list of H x W pixel indices and its counter (grown on demand, VF_ERR_OOM)
+int gated_sparse_permille(const vf_ctx* ctx);
+vf_status gated_scratch(vf_ctx* ctx, size_t pixels, int** list, unsigned** count);
 
 // Whether an FP32 call of window w and criterion crit runs the pair-reuse
 // kernels under the context's VF_OPT_PAIR_REUSE setting.

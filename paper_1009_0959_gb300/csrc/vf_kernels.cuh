@@ -409,6 +409,22 @@ __device__ __forceinline__ TileSmem carve(int W, bool reg, int TY, int threads) 
 
 // FLOATS = false stages only the packed pixels (the VMF selection works on
 // them directly).
+// A staged sample's FP32 colour; .w = 1/|x| for the angle criteria (0 for
+// the zero vector), 0 otherwise.
+template <int CRIT>
+__device__ __forceinline__ float4 stage_cell(uint32_t v) {
+  float r = (float)(v & 255u), g = (float)((v >> 8) & 255u), b = (float)((v >> 16) & 255u);
+  float w = 0.0f;
+  if (CRIT == kBVDF || CRIT == kEVBDF) {
+    float n2 = fmaf(r, r, fmaf(g, g, b * b));
+    if (n2 > 0.0f) {
+      float y = rsqrtf(n2);
+      w = y * fmaf(-0.5f * n2 * y, y, 1.5f);  // one Newton step
+    }
+  }
+  return make_float4(r, g, b, w);
+}
+
 template <int CRIT, bool FLOATS = true>
 __device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, int x0, int y0, int R) {
   const int cells = t.sw * t.sh;
@@ -419,16 +435,7 @@ __device__ __forceinline__ void stage_tile(const Launch& L, const TileSmem& t, i
     uint32_t v = load_px(L, gx, gy);
     t.raw[idx] = v;
     if constexpr (!FLOATS) continue;
-    float r = (float)(v & 255u), g = (float)((v >> 8) & 255u), b = (float)((v >> 16) & 255u);
-    float w = 0.0f;
-    if (CRIT == kBVDF || CRIT == kEVBDF) {
-      float n2 = fmaf(r, r, fmaf(g, g, b * b));
-      if (n2 > 0.0f) {
-        float y = rsqrtf(n2);
-        w = y * fmaf(-0.5f * n2 * y, y, 1.5f);  // one Newton step
-      }
-    }
-    t.px[idx] = make_float4(r, g, b, w);
+    t.px[idx] = stage_cell<CRIT>(v);
   }
 }
 

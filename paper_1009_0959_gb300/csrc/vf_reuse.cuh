@@ -633,6 +633,7 @@ template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     reuse_kernel(const __grid_constant__ Launch L) {
   pdl_begin();
+  if (L.gate_count != nullptr && *L.gate_count <= L.gate_limit) return;  // the sparse form ran
   reuse_any_tile<W, CRIT, APX, DEG, RTY, NT>(L, blockIdx.x);
 }
 

@@ -159,7 +159,8 @@ def context():
     return ctx
 
 
-OPTIONS = {"pair_reuse": 0, "tile_rows": 1, "gate_tensor_cores": 2, "overlap_launch": 3}
+OPTIONS = {"pair_reuse": 0, "tile_rows": 1, "gate_tensor_cores": 2, "overlap_launch": 3,
+           "gated_sparse": 4}
 
 
 def set_option(name: str, value: int):

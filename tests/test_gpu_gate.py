@@ -205,6 +205,51 @@ def test_gated_reuse_sparse_flags(vf, w, approx):
     assert st.tolist()[0] == h * wd and st.tolist()[2] == int(f.sum())
 
 
+@pytest.mark.parametrize("crit,w,approx", [("bvdf", 5, "poly"), ("bvdf", 3, "exact"),
+                                            ("bvdf", 7, "poly"), ("vmf", 5, "exact"),
+                                            ("vmf", 7, "exact"), ("amnfe", 5, "rational"),
+                                            ("amnfg", 7, "poly"), ("amnfg", 3, "exact")])
+def test_gated_sparse_form(vf, crit, w, approx):
+    """VF_OPT_GATED_SPARSE: the compacted list of flagged pixels, one window
+    each, gives the per-window gated form's bytes (the same window code on
+    the same staged samples) and counters, at any flag density, with no flag
+    and with every flag; under a limit the device picks the sparse form for
+    a sparse map and the tile form (pair-reuse tiles for BVDF) otherwise."""
+    h, wd = 53, 141
+    clean, noisy = synth.noisy(h, wd, 0.2, 60 + w)
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    kw = dict(criterion=crit, window=w, approx=approx, degree=4)
+    rng = np.random.default_rng(w)
+    maps = {d: torch.from_numpy((rng.random((h, wd)) < d).astype(np.uint8)).cuda()
+            for d in (0.0, 0.05, 0.6, 1.0)}
+
+    def run(flags, sparse, reuse):
+        vf.set_option("gated_sparse", sparse)
+        vf.set_option("pair_reuse", reuse)
+        try:
+            st = torch.zeros(3, dtype=torch.int64, device="cuda")
+            out = vf.filter_gated(t, flags, stats=st, **kw)
+            torch.cuda.synchronize()
+        finally:
+            vf.set_option("gated_sparse", 0)
+            vf.set_option("pair_reuse", 1)
+        return out, st.tolist()
+
+    for d, flags in maps.items():
+        ref, st_ref = run(flags, 0, 0)
+        out, st = run(flags, 1000, 0)
+        assert torch.equal(out, ref), d
+        assert st == st_ref and st[0] == h * wd and st[2] == int(flags.sum().item())
+        if d == 0.0:
+            assert torch.equal(out, t)
+        # under a 30 % limit: the sparse form below it, the tile form above
+        auto, st_a = run(flags, 300, 1)
+        tiles, st_t = run(flags, 0, 1)
+        want, st_w = (out, st) if d <= 0.3 else (tiles, st_t)
+        assert torch.equal(auto, want), d
+        assert st_a == st_w
+
+
 def test_trained_gate_beats_plain_filter(vf):
     """Trained on the GPU by the library's own kernels, the gate flags the
     impulses; the gated 5 x 5 minimax BVDF keeps the clean pixels untouched
