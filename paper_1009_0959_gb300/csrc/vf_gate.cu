@@ -653,8 +653,10 @@ constexpr int G5_OFF_B3 = G5_OFF_B2 + 3 * G5_B2;
 constexpr int G5_OFF_BIAS = G5_OFF_B3 + 2 * G5_N3 * 16;
 constexpr int G5_OFF_X0 = G5_OFF_BIAS + 256;           // x0, later a2 (x0 is dead by then)
 constexpr int G5_OFF_A1 = G5_OFF_X0 + 2 * G5_A2P;
+constexpr int G5_RAW_CW = G5_CW + 2;                  // raw cells per row: xs - 4 .. xs + 127
 constexpr int G5_OFF_RAW = G5_OFF_A1 + 2 * G5_A1P;      // the next tile's pixels (32-bit)
-constexpr int G5_SMEM = G5_OFF_RAW + G5_R0 * G5_CW * 4;
+constexpr int G5_SMEM = G5_OFF_RAW + G5_R0 * G5_RAW_CW * 4;
+static_assert(G5_X % 4 == 0 && G5_RAW_CW % 4 == 0, "raw rows are whole 16-byte chunks");
 constexpr int G5_THREADS = 256;
 constexpr int G5_BLOCKS = G5_R0 + 2;                   // TMEM blocks (output rows -2 .. R0 - 1)
 constexpr int G5_TMEM_COLS = 256;
@@ -824,45 +826,59 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   const uint64_t db2 = g5_desc(g5_smem(g5 + G5_OFF_B2), G5_N2 * 16, 128);
   const uint64_t db3 = g5_desc(g5_smem(g5 + G5_OFF_B3), G5_N3 * 16, 128);
   constexpr uint64_t kCellD = 1, kRowD = G5_RP / 16, kB1D = G5_B1 / 16, kB2D = G5_B2 / 16;
-  // the next tile's input pixels, fetched while the tile's last layer runs:
-  // RGBX words copied asynchronously (cp.async, no register waits on them)
-  // into the raw buffer, 3-byte pixels into registers; bit j of pre_in set
-  // where word j is a pixel of the image (zero input elsewhere).  Each
-  // thread later reads back only the words it fetched.
+  // the next tile's input pixels, fetched while the tile's last layer runs,
+  // into the raw buffer (rows of cells xs - 4 .. xs + 127): RGBX rows in
+  // 16-byte chunks by cp.async (zero-filled past the image's right edge)
+  // where the image and its pitch are 16-byte aligned, else 32-bit words by
+  // cp.async, or 3-byte pixels into registers.  Which cells lie inside the
+  // image is decided again from their coordinates when they are staged.
   constexpr int kPre = (G5_R0 * G5_CW + G5_THREADS - 1) / G5_THREADS;
-  static_assert(kPre <= 32, "one validity bit per fetched word");
-  uint32_t pre[kPre], pre_in = 0u;
+  constexpr int kChunks = G5_R0 * (G5_RAW_CW / 4);
+  const bool vec = I.channels == 4 && (reinterpret_cast<uintptr_t>(I.img) & 15) == 0 &&
+                   (I.pitch & 15) == 0;
+  uint32_t pre[kPre];
   uint32_t* raw = reinterpret_cast<uint32_t*>(g5 + G5_OFF_RAW);
   auto fetch = [&](int t) {
     const int xs = (t % tiles_x) * G5_X, ys = (t / tiles_x) * G5_Y;
-    pre_in = 0u;
-#pragma unroll
-    for (int j = 0; j < kPre; ++j) {
-      const int e = tid + j * G5_THREADS;
-      const int r = e / G5_CW, c = e - r * G5_CW;
-      const int gy = ys - 3 + r, gx = xs - 3 + c;
-      const bool in =
-          e < G5_R0 * G5_CW && t < ntiles && gy >= 0 && gy < I.H && gx >= 0 && gx < I.W;
-      pre_in |= in ? 1u << j : 0u;
-      if (!in) continue;
-      const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
-      if (word)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(g5_smem(raw + e)),
-                     "l"(src)
+    if (vec) {
+      for (int j = tid; j < kChunks; j += G5_THREADS) {
+        const int r = j / (G5_RAW_CW / 4), q = j - r * (G5_RAW_CW / 4);
+        const int gy = ys - 3 + r, x = xs - 4 + 4 * q;  // x: a multiple of 4
+        int bytes = 0;
+        if (t < ntiles && gy >= 0 && gy < I.H && x >= 0) bytes = min(16, max(0, (I.W - x) * 4));
+        const uint8_t* src = bytes ? I.img + (long long)gy * I.pitch + 4LL * x : I.img;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                         g5_smem(raw + r * G5_RAW_CW + 4 * q)),
+                     "l"(src), "r"(bytes)
                      : "memory");
-      else
-        pre[j] = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kPre; ++j) {
+        const int e = tid + j * G5_THREADS;
+        const int r = e / G5_CW, c = e - r * G5_CW;
+        const int gy = ys - 3 + r, gx = xs - 3 + c;
+        if (e >= G5_R0 * G5_CW || t >= ntiles || gy < 0 || gy >= I.H || gx < 0 || gx >= I.W)
+          continue;
+        const uint8_t* src = I.img + (long long)gy * I.pitch + (long long)gx * I.channels;
+        if (word)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                           g5_smem(raw + r * G5_RAW_CW + c + 1)),
+                       "l"(src)
+                       : "memory");
+        else
+          pre[j] = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16);
+      }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
 
   // one layer: thread 0 issues its MMAs (in order) and commits them to the
   // mbarrier, then waits on it; the others wait at the barrier after it.
-  // `before` runs between the proxy fence and the barrier (global loads
-  // issued there are in flight while the MMAs run)
-  auto run_layer = [&](auto issue, auto before) -> bool {
+  // `during` runs on every thread while the MMAs are in flight (thread 0:
+  // after issuing them)
+  auto run_layer = [&](auto issue, auto during) -> bool {
     g5_proxy_fence();  // the generic-proxy writes of the operands, for the tensor cores
-    before();
     __syncthreads();
     if (tid == 0) {
       g5_fence_after();
@@ -870,8 +886,9 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               bar));
-      s_ok = g5_wait(bar, parity) ? 1 : 0;
     }
+    during();
+    if (tid == 0) s_ok = g5_wait(bar, parity) ? 1 : 0;
     __syncthreads();
     parity ^= 1u;
     g5_fence_after();
@@ -880,22 +897,29 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
 
   bool ok = true;
   fetch(blockIdx.x);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();  // the first tile's raw pixels, copied by every thread
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int xs = (tile % tiles_x) * G5_X, ys = (tile / tiles_x) * G5_Y;
     // x0 rows ys - 3 .. ys + G5_Y + 2, cells xs - 3 .. xs + 126 (zero outside
     // the image), from the pixels fetched during the previous tile
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
       const int e = tid + j * G5_THREADS;
       if (e >= G5_R0 * G5_CW) break;
       const int r = e / G5_CW, c = e - r * G5_CW;
-      const uint32_t px = word ? raw[e] : pre[j];
+      const int gy = ys - 3 + r, gx = xs - 3 + c;
+      const uint32_t px = (vec || word) ? raw[r * G5_RAW_CW + c + 1] : pre[j];
       uint32_t w01 = 0u, w23 = 0u;
-      if ((pre_in >> j) & 1u) {
-        const float cr = (float)(px & 255u) * (1.0f / 255.0f) - 0.5f;
-        const float cg = (float)((px >> 8) & 255u) * (1.0f / 255.0f) - 0.5f;
-        const float cb = (float)((px >> 16) & 255u) * (1.0f / 255.0f) - 0.5f;
+      if (gy >= 0 && gy < I.H && gx >= 0 && gx < I.W) {
+        // byte k as the FP32 number 2^23 + byte (one byte permute) minus 2^23:
+        // the byte's value exactly, without an integer-to-float conversion
+        auto chan = [&](uint32_t sel) {
+          return __uint_as_float(__byte_perm(px, 0x4B000000u, sel)) - 8388608.0f;
+        };
+        const float cr = chan(0x7540u) * (1.0f / 255.0f) - 0.5f;
+        const float cg = chan(0x7541u) * (1.0f / 255.0f) - 0.5f;
+        const float cb = chan(0x7542u) * (1.0f / 255.0f) - 0.5f;
         w01 = pack_bf16(cr, cg);
         w23 = pack_bf16(cb, 0.0f);
       }
@@ -984,6 +1008,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     }
     g5_clear(lane_addr, h);  // the next tile's layer-1 accumulators
     g5_fence_before();
+    asm volatile("cp.async.wait_all;\n" ::: "memory");  // published by the barrier
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
