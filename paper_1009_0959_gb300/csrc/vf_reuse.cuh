@@ -243,32 +243,28 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   stage_tile<CRIT>(L, t, x0, y0, R);
   __syncthreads();
 
-  // 1. term table.  Work items are (offset row dy, region pixel p): w - 1 or
-  //    2w - 1 terms each, spread over all threads so that they reach the
-  //    barrier together; consecutive threads take consecutive pixels.  An
-  //    entry whose partner p + delta lies outside the region is 0, so the
-  //    forward reads of phase 2 need no bounds test.  Work items are (offset
-  //    column dx, region pixel p), w - 1 or w terms each (dy = 0 only for
-  //    dx > 0): (2w - 1) x region items of nearly equal cost, so the last
-  //    round leaves few threads idle.
+  // 1. term table.  Entries whose partner p + delta lies outside the region
+  //    (past its last row, or across its left or right edge, where the flat
+  //    index wraps to another row) belong to no window of the tile: phase 2
+  //    reads them only into sums for windows that are discarded (below), so
+  //    their values do not matter.  Work items are (offset column dx, region
+  //    pixel p), w - 1 or w terms each (dy = 0 only for dx > 0): (2w - 1) x
+  //    region items of nearly equal cost, so the last round leaves few
+  //    threads idle.
   auto row_terms = [&](const auto& term, const auto* src) {
     if constexpr (NT >= NR) {
       // one thread per region pixel: every offset is a compile-time constant
-      // and the pixel's own sample is loaded once.  A partner past the
-      // region's end reads the next shared array (its term is zeroed).
+      // and the pixel's own sample is loaded once; no bound test (a partner
+      // past the region's end reads the next shared array)
       const int p = threadIdx.x;
       if (p >= NR) return;
-      const int r = p / RX, c = p - r * RX;
       const auto xp = load_sample(src + p);
       auto one = [&](auto DX) {
         constexpr int dx = decltype(DX)::value;
-        const bool col_in = c + dx >= 0 && c + dx < RX;
 #pragma unroll
         for (int dy = 0; dy <= M; ++dy) {
           if (dy == 0 && dx <= 0) continue;
-          float v = term(xp, load_sample(src + p + dy * RX + dx));
-          v = (col_in && r + dy < RY) ? v : 0.0f;
-          T[fwd_index<W>(dy, dx) * NR + p] = v;
+          T[fwd_index<W>(dy, dx) * NR + p] = term(xp, load_sample(src + p + dy * RX + dx));
         }
       };
       static_for<-M, M>(one);
@@ -303,25 +299,28 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   // 2. box sums of each region pixel's distance field, scattered to the
   //    windows of this tile that contain it: width-w sums along each of the
   //    2w - 1 field rows, then height-w sums down the columns, both sharing
-  //    their common partial sums (additions only)
+  //    their common partial sums (additions only).  A window that is kept
+  //    (its output inside the tile) holds only partners inside the region,
+  //    and each of its sums is an exact expression over its own field
+  //    entries (the shared partial sums are sums of subsets of both), so the
+  //    entries of partners outside the region -- forward entries never
+  //    zeroed, mirrored reads that wrap across a region edge or start up to
+  //    (w - 1)(RX + 1) floats before a table row (in the packed pixels'
+  //    array) -- reach only discarded windows, and need no bound test.
   for (int p = threadIdx.x; p < NR; p += G::THREADS) {
     const int r = p / RX, c = p - r * RX;
     float h[2 * M + 1][W];  // h[dy + M][ex + R]: field row dy summed over dx in ex +- R
 #pragma unroll
     for (int dy = -M; dy <= M; ++dy) {
       float d[2 * M + 1];
-      const bool row_in = r + dy >= 0 && r + dy < RY;
 #pragma unroll
       for (int dx = -M; dx <= M; ++dx) {
         if (dy > 0 || (dy == 0 && dx > 0)) {
-          d[dx + M] = T[fwd_index<W>(dy, dx) * NR + p];  // 0 when p + delta is outside
+          d[dx + M] = T[fwd_index<W>(dy, dx) * NR + p];
         } else if (dy == 0 && dx == 0) {
           d[dx + M] = 0.0f;
         } else {
-          const int cq = c + dx;
-          d[dx + M] = (row_in && cq >= 0 && cq < RX)
-                          ? T[fwd_index<W>(-dy, -dx) * NR + p + dy * RX + dx]
-                          : 0.0f;
+          d[dx + M] = T[fwd_index<W>(-dy, -dx) * NR + p + dy * RX + dx];
         }
       }
       box_sums<W>(d, h[dy + M]);
