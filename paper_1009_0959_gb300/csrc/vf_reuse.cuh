@@ -24,6 +24,7 @@
 // another order (FP32, relative differences of a few 1e-7).
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "vf_kernels.cuh"
@@ -54,7 +55,7 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
-inline size_t reuse_smem_bytes(int w, int rty = kRTY) {
+__host__ __device__ constexpr size_t reuse_smem_bytes(int w, int rty = kRTY) {
   size_t rx = kRTX + w - 1, ry = rty + w - 1, nr = rx * ry, m = w - 1;
   size_t nd = m * (2 * m + 1) + m;
   return nr * 20 + nd * nr * 4 + (size_t)w * w * kRTX * rty * 4;
@@ -223,8 +224,10 @@ __device__ __forceinline__ void box_sums(const float (&v)[2 * W - 1], float (&ou
   }
 }
 
+// Phases 1-3 of a tile whose region is staged (px, raw) and visible to the
+// whole CTA.
 template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
-__device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
+__device__ __forceinline__ void reuse_tile_body(const Launch& L, int tile) {
   using G = ReuseGeom<W, RTY, NT>;
   constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M, ND = G::ND;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -234,14 +237,6 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   float* A = T + ND * NR;                                  // [N][OUT]
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kRTX, y0 = tyi * RTY;
-
-  TileSmem t;
-  t.px = px;
-  t.raw = raw;
-  t.sw = RX;
-  t.sh = RY;
-  stage_tile<CRIT>(L, t, x0, y0, R);
-  __syncthreads();
 
   // 1. term table.  Entries whose partner p + delta lies outside the region
   //    (past its last row, or across its left or right edge, where the flat
@@ -347,6 +342,70 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
 
   // 3. selection / weighting per output
   reuse_finish<W, CRIT, APX, DEG, RTY, NT>(L, px, raw, A, x0, y0);
+}
+
+template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
+__device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
+  using G = ReuseGeom<W, RTY, NT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  TileSmem t;
+  t.px = reinterpret_cast<float4*>(smem);
+  t.raw = reinterpret_cast<uint32_t*>(smem + G::NR * 16);
+  t.sw = G::RX;
+  t.sh = G::RY;
+  stage_tile<CRIT>(L, t, txi * kRTX, tyi * RTY, G::R);
+  __syncthreads();
+  reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+}
+
+// Persistent form of the tall tiles (one thread per region pixel, w <= 5):
+// each CTA loops over tiles blockIdx.x, + gridDim.x, ...; while a tile's
+// phases run, the next tile's region pixels are copied by cp.async into a
+// spare buffer after the tile's shared memory (each thread the pixel it
+// stages), so that staging waits on no global load.  32-bit pixels only.
+inline size_t reuse_persistent_smem_bytes(int w, int rty) {
+  return reuse_smem_bytes(w, rty) + (size_t)(kRTX + w - 1) * (rty + w - 1) * 4;
+}
+
+template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
+__device__ __forceinline__ void reuse_tiles_persistent(const Launch& L, int ntiles) {
+  using G = ReuseGeom<W, RTY, NT>;
+  constexpr int R = G::R, RX = G::RX, NR = G::NR;
+  static_assert(NT >= NR && W <= 5, "tall tiles, one thread per region pixel");
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* px = reinterpret_cast<float4*>(smem);
+  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
+  uint32_t* next = reinterpret_cast<uint32_t*>(smem + reuse_smem_bytes(W, RTY));
+  const int p = threadIdx.x;
+  const int ry = p / RX, rx = p - ry * RX;
+  auto prefetch = [&](int tile) {
+    if (p < NR) {
+      const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+      const int gy = min(max(tyi * RTY + ry - R, 0), L.height - 1);
+      const int gx = min(max(txi * kRTX + rx - R, 0), L.width - 1);
+      const uint8_t* src = L.in + (long long)gy * L.in_pitch + 4LL * gx;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(next + p)),
+                   "l"(src)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile);
+  for (; tile < ntiles; tile += gridDim.x) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (p < NR) {  // the pixel this thread fetched
+      const uint32_t v = next[p];
+      raw[p] = v;
+      px[p] = stage_cell<CRIT>(v);
+    }
+    __syncthreads();  // the region is staged; `next` is free again
+    if (tile + (int)gridDim.x < ntiles) prefetch(tile + gridDim.x);
+    reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+    __syncthreads();  // the finish phase's reads are done before the next staging
+  }
 }
 
 // Chunked form for large windows, where the whole term table would not fit in
@@ -636,9 +695,41 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
   reuse_any_tile<W, CRIT, APX, DEG, RTY, NT>(L, blockIdx.x);
 }
 
+// The persistent tall-tile form (plain calls on 32-bit pixels)
+template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    reuse_persistent_kernel(const __grid_constant__ Launch L, int ntiles) {
+  pdl_begin();
+  reuse_tiles_persistent<W, CRIT, APX, DEG, RTY, NT>(L, ntiles);
+}
+
 template <int W, int CRIT, int APX, int DEG, int RTY = reuse_tile_rows(W, CRIT),
           int NT = reuse_threads(W, RTY)>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
+  if constexpr (W <= 5 && NT >= (kRTX + W - 1) * (RTY + W - 1)) {
+    if (L.flags == nullptr && L.vec4_in) {
+      const size_t smem = reuse_persistent_smem_bytes(W, RTY);
+      auto kern = reuse_persistent_kernel<W, CRIT, APX, DEG, RTY, NT>;
+      // resident CTAs of the whole device, found once per device (the
+      // attribute set with it)
+      static int resident[16] = {};
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e != cudaSuccess) return e;
+      int& res = resident[dev & 15];
+      if (res == 0) {
+        int sms = 0, per_sm = 0;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+        if (e != cudaSuccess) return e;
+        res = std::max(per_sm, 1) * sms;
+      }
+      return launch_maybe_pdl(L.pdl != 0, kern, dim3(std::min(grid, res)), dim3(NT), smem, s, L,
+                              grid);
+    }
+  }
   const size_t smem = reuse_any_smem_bytes(W, RTY);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(reuse_kernel<W, CRIT, APX, DEG, RTY, NT>,
