@@ -364,6 +364,8 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
 // phases run, the next tile's region pixels are copied by cp.async into a
 // spare buffer after the tile's shared memory (each thread the pixel it
 // stages), so that staging waits on no global load.  32-bit pixels only.
+// Gated form: a tile none of whose outputs is flagged is copied from the
+// staged region (the others read the flags in the finish phase).
 inline size_t reuse_persistent_smem_bytes(int w, int rty) {
   return reuse_smem_bytes(w, rty) + (size_t)(kRTX + w - 1) * (rty + w - 1) * 4;
 }
@@ -401,9 +403,24 @@ __device__ __forceinline__ void reuse_tiles_persistent(const Launch& L, int ntil
       raw[p] = v;
       px[p] = stage_cell<CRIT>(v);
     }
-    __syncthreads();  // the region is staged; `next` is free again
+    const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+    const int x0 = txi * kRTX, y0 = tyi * RTY;
+    const int ox = p % kRTX, oy = p / kRTX;
+    const bool out = p < G::OUT && x0 + ox < L.width && y0 + oy < L.height;
+    bool skip = false;
+    if (L.flags != nullptr) {  // gated form: a tile without a flag is copied whole
+      const bool f = out && L.flags[(long long)(y0 + oy) * L.flag_pitch + x0 + ox] != 0;
+      skip = !__syncthreads_or(f);  // also the barrier after staging
+    } else {
+      __syncthreads();  // the region is staged; `next` is free again
+    }
     if (tile + (int)gridDim.x < ntiles) prefetch(tile + gridDim.x);
-    reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+    if (skip) {
+      if (out) store_px(L, x0 + ox, y0 + oy, raw[(oy + R) * RX + ox + R]);
+      block_stats(L, out ? 1 : 0, 0, 0);
+    } else {
+      reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+    }
     __syncthreads();  // the finish phase's reads are done before the next staging
   }
 }
@@ -695,11 +712,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
   reuse_any_tile<W, CRIT, APX, DEG, RTY, NT>(L, blockIdx.x);
 }
 
-// The persistent tall-tile form (plain calls on 32-bit pixels)
+// The persistent tall-tile form (32-bit pixels)
 template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
 __global__ void __launch_bounds__(NT, 1)
     reuse_persistent_kernel(const __grid_constant__ Launch L, int ntiles) {
   pdl_begin();
+  if (L.gate_count != nullptr && *L.gate_count <= L.gate_limit) return;  // the sparse form ran
   reuse_tiles_persistent<W, CRIT, APX, DEG, RTY, NT>(L, ntiles);
 }
 
@@ -707,7 +725,7 @@ template <int W, int CRIT, int APX, int DEG, int RTY = reuse_tile_rows(W, CRIT),
           int NT = reuse_threads(W, RTY)>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
   if constexpr (W <= 5 && NT >= (kRTX + W - 1) * (RTY + W - 1)) {
-    if (L.flags == nullptr && L.vec4_in) {
+    if (L.vec4_in) {
       const size_t smem = reuse_persistent_smem_bytes(W, RTY);
       auto kern = reuse_persistent_kernel<W, CRIT, APX, DEG, RTY, NT>;
       // resident CTAs of the whole device, found once per device (the
