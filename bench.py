@@ -120,12 +120,12 @@ class Clocks:
 #   (sm__pipe_fma_cycles_active.avg.pct_of_peak_sustained_active / 100).
 # Keyed (criterion, approx, degree, window); degree 0 for exact / rational.
 MEASURED_PER_PIXEL = {
-    ('bvdf', 'exact', 0, 5): {"fp32": 1590.4, "inst": 2695.3, "dram": 7.034, "fma_pipe": 0.425},
-    ('bvdf', 'poly', 2, 5): {"fp32": 1422.4, "inst": 2528.7, "dram": 6.998, "fma_pipe": 0.413},
-    ('bvdf', 'poly', 3, 5): {"fp32": 1530.6, "inst": 2637.0, "dram": 7.034, "fma_pipe": 0.424},
-    ('bvdf', 'poly', 4, 5): {"fp32": 1638.9, "inst": 2748.0, "dram": 7.017, "fma_pipe": 0.444},
-    ('bvdf', 'poly', 5, 5): {"fp32": 1747.2, "inst": 2856.2, "dram": 7.033, "fma_pipe": 0.447},
-    ('bvdf', 'poly', 6, 5): {"fp32": 1855.5, "inst": 2967.2, "dram": 7.028, "fma_pipe": 0.456},
+    ('bvdf', 'exact', 0, 5): {"fp32": 1590.4, "inst": 2440.0, "dram": 6.960, "fma_pipe": 0.473},
+    ('bvdf', 'poly', 2, 5): {"fp32": 1422.4, "inst": 2274.0, "dram": 6.960, "fma_pipe": 0.450},
+    ('bvdf', 'poly', 3, 5): {"fp32": 1530.6, "inst": 2382.0, "dram": 6.960, "fma_pipe": 0.483},
+    ('bvdf', 'poly', 4, 5): {"fp32": 1638.9, "inst": 2490.0, "dram": 6.940, "fma_pipe": 0.484},
+    ('bvdf', 'poly', 5, 5): {"fp32": 1747.2, "inst": 2602.0, "dram": 6.950, "fma_pipe": 0.485},
+    ('bvdf', 'poly', 6, 5): {"fp32": 1855.5, "inst": 2711.0, "dram": 6.950, "fma_pipe": 0.491},
     ('evmf', 'poly', 4, 5): {"fp32": 814.9, "inst": 1921.1, "dram": 6.898, "fma_pipe": 0.361},
     ('evmf', 'rational', 0, 5): {"fp32": 934.1, "inst": 2068.9, "dram": 6.947, "fma_pipe": 0.384},
     ("evmf", "exact", 0, 5): {"fp32": 1083.8, "inst": 2432.6, "dram": 6.899, "fma_pipe": 0.378},
