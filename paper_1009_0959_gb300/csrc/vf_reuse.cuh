@@ -359,72 +359,6 @@ __device__ __forceinline__ void reuse_tile(const Launch& L, int tile) {
   reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
 }
 
-// Persistent form of the tall tiles (one thread per region pixel, w <= 5):
-// each CTA loops over tiles blockIdx.x, + gridDim.x, ...; while a tile's
-// phases run, the next tile's region pixels are copied by cp.async into a
-// spare buffer after the tile's shared memory (each thread the pixel it
-// stages), so that staging waits on no global load.  32-bit pixels only.
-// Gated form: a tile none of whose outputs is flagged is copied from the
-// staged region (the others read the flags in the finish phase).
-inline size_t reuse_persistent_smem_bytes(int w, int rty) {
-  return reuse_smem_bytes(w, rty) + (size_t)(kRTX + w - 1) * (rty + w - 1) * 4;
-}
-
-template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
-__device__ __forceinline__ void reuse_tiles_persistent(const Launch& L, int ntiles) {
-  using G = ReuseGeom<W, RTY, NT>;
-  constexpr int R = G::R, RX = G::RX, NR = G::NR;
-  static_assert(NT >= NR && W <= 5, "tall tiles, one thread per region pixel");
-  extern __shared__ __align__(16) unsigned char smem[];
-  float4* px = reinterpret_cast<float4*>(smem);
-  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
-  uint32_t* next = reinterpret_cast<uint32_t*>(smem + reuse_smem_bytes(W, RTY));
-  const int p = threadIdx.x;
-  const int ry = p / RX, rx = p - ry * RX;
-  auto prefetch = [&](int tile) {
-    if (p < NR) {
-      const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
-      const int gy = min(max(tyi * RTY + ry - R, 0), L.height - 1);
-      const int gx = min(max(txi * kRTX + rx - R, 0), L.width - 1);
-      const uint8_t* src = L.in + (long long)gy * L.in_pitch + 4LL * gx;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
-                       (uint32_t)__cvta_generic_to_shared(next + p)),
-                   "l"(src)
-                   : "memory");
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-  int tile = blockIdx.x;
-  if (tile < ntiles) prefetch(tile);
-  for (; tile < ntiles; tile += gridDim.x) {
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    if (p < NR) {  // the pixel this thread fetched
-      const uint32_t v = next[p];
-      raw[p] = v;
-      px[p] = stage_cell<CRIT>(v);
-    }
-    const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
-    const int x0 = txi * kRTX, y0 = tyi * RTY;
-    const int ox = p % kRTX, oy = p / kRTX;
-    const bool out = p < G::OUT && x0 + ox < L.width && y0 + oy < L.height;
-    bool skip = false;
-    if (L.flags != nullptr) {  // gated form: a tile without a flag is copied whole
-      const bool f = out && L.flags[(long long)(y0 + oy) * L.flag_pitch + x0 + ox] != 0;
-      skip = !__syncthreads_or(f);  // also the barrier after staging
-    } else {
-      __syncthreads();  // the region is staged; `next` is free again
-    }
-    if (tile + (int)gridDim.x < ntiles) prefetch(tile + gridDim.x);
-    if (skip) {
-      if (out) store_px(L, x0 + ox, y0 + oy, raw[(oy + R) * RX + ox + R]);
-      block_stats(L, out ? 1 : 0, 0, 0);
-    } else {
-      reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
-    }
-    __syncthreads();  // the finish phase's reads are done before the next staging
-  }
-}
-
 // Chunked form for large windows, where the whole term table would not fit in
 // shared memory next to a useful occupancy (w = 7: 84 x 532 floats).  The
 // table is built one forward offset row dy = k at a time (2w - 1 entries per
@@ -552,13 +486,14 @@ __device__ __forceinline__ void reuse_chunked_tile(const Launch& L, int tile) {
 // offset rows and writes them to the window slots once at the end, instead
 // of adding each field row's contributions to the slots in shared memory
 // (w^2 read-modify-writes per field row).  Same sums, another order.
-inline size_t reuse_chunked_reg_smem_bytes(int w, int rty) {
+__host__ __device__ constexpr size_t reuse_chunked_reg_smem_bytes(int w, int rty) {
   size_t rx = kRTX + w - 1, ry = rty + w - 1, nr = rx * ry;
   return nr * 20 + (size_t)(2 * w - 1) * nr * 4 + (size_t)w * w * kRTX * rty * 4;
 }
 
+// The tile's phases once its region is staged (px, raw) and visible.
 template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
-__device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile) {
+__device__ __forceinline__ void reuse_chunked_reg_tile_body(const Launch& L, int tile) {
   using G = ReuseGeom<W, RTY, NT>;
   constexpr int R = G::R, RX = G::RX, RY = G::RY, NR = G::NR, M = G::M;
   constexpr int ROW = 2 * M + 1;  // entries of one offset row
@@ -570,14 +505,6 @@ __device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile
   float* A = T + ROW * NR;                                // [N][OUT]
   const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
   const int x0 = txi * kRTX, y0 = tyi * RTY;
-
-  TileSmem t;
-  t.px = px;
-  t.raw = raw;
-  t.sw = RX;
-  t.sh = RY;
-  stage_tile<CRIT>(L, t, x0, y0, R);
-  __syncthreads();
 
   const int p = threadIdx.x;
   const bool mine = p < NR;
@@ -675,6 +602,21 @@ __device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile
   reuse_finish<W, CRIT, APX, DEG, RTY, NT>(L, px, raw, A, x0, y0);
 }
 
+template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
+__device__ __forceinline__ void reuse_chunked_reg_tile(const Launch& L, int tile) {
+  using G = ReuseGeom<W, RTY, NT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+  TileSmem t;
+  t.px = reinterpret_cast<float4*>(smem);
+  t.raw = reinterpret_cast<uint32_t*>(smem + G::NR * 16);
+  t.sw = G::RX;
+  t.sh = G::RY;
+  stage_tile<CRIT>(L, t, txi * kRTX, tyi * RTY, G::R);
+  __syncthreads();
+  reuse_chunked_reg_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+}
+
 // One 32 x 8 tile per CTA (a 256-thread CTA whose shared memory is reused:
 // callers looping over tiles must __syncthreads() between calls).
 template <int W, int CRIT, int APX, int DEG, int RTY = kRTY, int NT = kRTX * RTY>
@@ -693,6 +635,72 @@ __device__ __forceinline__ void reuse_any_tile(const Launch& L, int tile) {
     reuse_chunked_tile<W, CRIT, APX, DEG>(L, tile);
   } else {
     reuse_tile<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+  }
+}
+
+// Persistent form of the tall tiles (one thread per region pixel, w <= 5):
+// each CTA loops over tiles blockIdx.x, + gridDim.x, ...; while a tile's
+// phases run, the next tile's region pixels are copied by cp.async into a
+// spare buffer after the tile's shared memory (each thread the pixel it
+// stages), so that staging waits on no global load.  32-bit pixels only.
+// Gated form: a tile none of whose outputs is flagged is copied from the
+// staged region (the others read the flags in the finish phase).
+__host__ __device__ constexpr size_t reuse_persistent_smem_bytes(int w, int rty) {
+  return reuse_smem_bytes(w, rty) + (size_t)(kRTX + w - 1) * (rty + w - 1) * 4;
+}
+
+template <int W, int CRIT, int APX, int DEG, int RTY, int NT>
+__device__ __forceinline__ void reuse_tiles_persistent(const Launch& L, int ntiles) {
+  using G = ReuseGeom<W, RTY, NT>;
+  constexpr int R = G::R, RX = G::RX, NR = G::NR;
+  static_assert(NT >= NR && W <= 5, "tall tiles, one thread per region pixel");
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* px = reinterpret_cast<float4*>(smem);
+  uint32_t* raw = reinterpret_cast<uint32_t*>(smem + NR * 16);
+  uint32_t* next = reinterpret_cast<uint32_t*>(smem + reuse_smem_bytes(W, RTY));
+  const int p = threadIdx.x;
+  const int ry = p / RX, rx = p - ry * RX;
+  auto prefetch = [&](int tile) {
+    if (p < NR) {
+      const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+      const int gy = min(max(tyi * RTY + ry - R, 0), L.height - 1);
+      const int gx = min(max(txi * kRTX + rx - R, 0), L.width - 1);
+      const uint8_t* src = L.in + (long long)gy * L.in_pitch + 4LL * gx;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(next + p)),
+                   "l"(src)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int tile = blockIdx.x;
+  if (tile < ntiles) prefetch(tile);
+  for (; tile < ntiles; tile += gridDim.x) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (p < NR) {  // the pixel this thread fetched
+      const uint32_t v = next[p];
+      raw[p] = v;
+      px[p] = stage_cell<CRIT>(v);
+    }
+    const int tyi = tile / L.tiles_x, txi = tile - tyi * L.tiles_x;
+    const int x0 = txi * kRTX, y0 = tyi * RTY;
+    const int ox = p % kRTX, oy = p / kRTX;
+    const bool out = p < G::OUT && x0 + ox < L.width && y0 + oy < L.height;
+    bool skip = false;
+    if (L.flags != nullptr) {  // gated form: a tile without a flag is copied whole
+      const bool f = out && L.flags[(long long)(y0 + oy) * L.flag_pitch + x0 + ox] != 0;
+      skip = !__syncthreads_or(f);  // also the barrier after staging
+    } else {
+      __syncthreads();  // the region is staged; `next` is free again
+    }
+    if (tile + (int)gridDim.x < ntiles) prefetch(tile + gridDim.x);
+    if (skip) {
+      if (out) store_px(L, x0 + ox, y0 + oy, raw[(oy + R) * RX + ox + R]);
+      block_stats(L, out ? 1 : 0, 0, 0);
+    } else {
+      reuse_tile_body<W, CRIT, APX, DEG, RTY, NT>(L, tile);
+    }
+    __syncthreads();  // the finish phase's reads are done before the next staging
   }
 }
 
@@ -724,6 +732,8 @@ __global__ void __launch_bounds__(NT, 1)
 template <int W, int CRIT, int APX, int DEG, int RTY = reuse_tile_rows(W, CRIT),
           int NT = reuse_threads(W, RTY)>
 cudaError_t launch_reuse_one(const Launch& L, int grid, cudaStream_t s) {
+  // (7 x 7: the loop around the 49 register window sums spills; one tile per
+  // CTA measured faster, 4.82 against 5.43 ms at 4096^2)
   if constexpr (W <= 5 && NT >= (kRTX + W - 1) * (RTY + W - 1)) {
     if (L.vec4_in) {
       const size_t smem = reuse_persistent_smem_bytes(W, RTY);
