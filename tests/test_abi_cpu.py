@@ -106,6 +106,15 @@ def test_options(vf):
     vf.set_option("tile_rows", 4)
     with pytest.raises(vf.VFError):
         vf.set_option("tile_rows", 3)
+    for engine in (0, 2, 1):
+        vf.set_option("gate_tensor_cores", engine)
+    with pytest.raises(vf.VFError):
+        vf.set_option("gate_tensor_cores", 3)
+    for permille in (1000, 150, 0):  # the gated filter's sparse-form limit
+        vf.set_option("gated_sparse", permille)
+    for bad in (-1, 1001):
+        with pytest.raises(vf.VFError):
+            vf.set_option("gated_sparse", bad)
 
 
 @pytest.mark.parametrize("fn,interval", [("exp", (0.0, 10.0)), ("ent", (0.05, 1.0)),
