@@ -1010,38 +1010,51 @@ def bench_gate(frames=64, train_steps=800):
         return a.elapsed_time(b) / 3
 
     per_frame = []
-    for f in sorted({0, frames // 4, frames // 2, 3 * frames // 4, frames - 1}):
+    for f in sorted({0, frames // 16, frames // 8, 3 * frames // 16, frames // 4, frames // 2,
+                     3 * frames // 4, frames - 1}):
         x, fl = noisy_d[f], flags[0]
         gate.infer(x, 0.5, flags=fl, stream=stream)
         frac = fl.float().mean().item()
         t_plain = one(lambda: vfilt.filter(x, out_plain[0], stream=stream, **kw))
         t_gate = one(lambda: gate.infer(x, 0.5, flags=fl, stream=stream))
-        t_reuse = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
+        t_auto = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
+        vfilt.set_option("gated_sparse", 0)
+        try:
+            t_reuse = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
+        finally:
+            vfilt.set_option("gated_sparse", 200)
         vfilt.set_option("pair_reuse", 0)
+        vfilt.set_option("gated_sparse", 0)
         try:
             t_win = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
         finally:
             vfilt.set_option("pair_reuse", 1)
+            vfilt.set_option("gated_sparse", 200)
         vfilt.set_option("gated_sparse", 1000)
         try:
             t_sparse = one(lambda: vfilt.filter_gated(x, fl, out_gated[0], stream=stream, **kw))
         finally:
-            vfilt.set_option("gated_sparse", 0)
+            vfilt.set_option("gated_sparse", 200)
         # the same with the gate trained on the generator's masks alone
         fm = flags[1]
         gate_mask.infer(x, 0.5, flags=fm, stream=stream)
         frac_m = fm.float().mean().item()
-        t_reuse_m = one(lambda: vfilt.filter_gated(x, fm, out_gated[0], stream=stream, **kw))
+        vfilt.set_option("gated_sparse", 0)
+        try:
+            t_reuse_m = one(lambda: vfilt.filter_gated(x, fm, out_gated[0], stream=stream, **kw))
+        finally:
+            vfilt.set_option("gated_sparse", 200)
         vfilt.set_option("gated_sparse", 1000)
         try:
             t_sparse_m = one(lambda: vfilt.filter_gated(x, fm, out_gated[0], stream=stream, **kw))
         finally:
-            vfilt.set_option("gated_sparse", 0)
+            vfilt.set_option("gated_sparse", 200)
         best = min(t_reuse, t_win, t_sparse)
         per_frame.append({"frame": f, "flagged": round(frac, 4), "plain_ms": round(t_plain, 3),
                           "gate_ms": round(t_gate, 3), "gated_reuse_ms": round(t_reuse, 3),
                           "gated_window_ms": round(t_win, 3),
                           "gated_sparse_ms": round(t_sparse, 3),
+                          "gated_default_ms": round(t_auto, 3),
                           "speedup_best_form": round(t_plain / (t_gate + best), 3),
                           "mask_gate_flagged": round(frac_m, 4),
                           "mask_gate_sparse_ms": round(t_sparse_m, 3),

@@ -59,7 +59,7 @@ struct vf_ctx {
   int pair_reuse = 1;  // 0 never, 1 where it pays (BVDF, EVBDF), 2 always
   int gate_tc = 1;     // gate inference: 0 CUDA cores, 1 tcgen05, 2 warp-level mma
   int overlap = 1;     // programmatic dependent launches for vf_filter
-  int gated_sparse = 0;  // vf_filter_gated: sparse form up to this many flagged per mille
+  int gated_sparse = 200;  // vf_filter_gated: sparse form up to this many flagged per mille
   int* d_glist = nullptr;  // its pixel list and counter
   unsigned* d_gcount = nullptr;
   size_t glist_cap = 0;

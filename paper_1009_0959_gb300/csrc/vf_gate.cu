@@ -1151,30 +1151,60 @@ vf_status run_train(vf_gate* g, const Images& I, const uint8_t* targets, cudaStr
 
 
 // Sparse form of the gated filter, first kernel: every unflagged pixel is
-// copied and every flagged one listed (y * width + x; warp-aggregated
-// appends, so the list's order varies between runs -- a listed pixel's
-// output does not depend on it).
+// copied and every flagged one listed (y * width + x).  A CTA takes 1,024
+// pixels at a time (four per thread, each group of 256 coalesced), counts
+// its flagged ones with warp ballots and claims their list slots with one
+// atomic add; the order of the list varies between runs (a listed pixel's
+// output does not depend on it).  Once the list is longer than `limit` the
+// tile form will run and rewrite every pixel, so the CTA stops.
+constexpr int kCompactPer = 4;  // pixels per thread and round
 __global__ void __launch_bounds__(256)
     gated_compact(const __grid_constant__ Launch L, const uint8_t* __restrict__ flags,
-                  long long flag_pitch, int* __restrict__ list, unsigned* __restrict__ count) {
+                  long long flag_pitch, int* __restrict__ list, unsigned* __restrict__ count,
+                  unsigned limit) {
+  __shared__ unsigned s_off[8];  // per warp: first slot after the CTA's base
+  __shared__ unsigned s_base, s_tot;
   const long long total = (long long)L.width * L.height;
-  const long long step = (long long)gridDim.x * blockDim.x;
-  for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < total; i0 += step) {
-    const long long i = i0 + threadIdx.x;  // the loop is uniform over the block
-    bool f = false;
-    if (i < total) {
-      const int y = (int)(i / L.width), x = (int)(i - (long long)y * L.width);
-      f = flags[(long long)y * flag_pitch + x] != 0;
-      if (!f) store_px(L, x, y, load_px(L, x, y));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const long long chunk = 256LL * kCompactPer, step = (long long)gridDim.x * chunk;
+  for (long long c0 = blockIdx.x * chunk; c0 < total; c0 += step) {  // uniform over the CTA
+    unsigned m[kCompactPer];
+    unsigned mine = 0;
+#pragma unroll
+    for (int k = 0; k < kCompactPer; ++k) {
+      const long long i = c0 + k * 256 + threadIdx.x;
+      bool f = false;
+      if (i < total) {
+        const int y = (int)(i / L.width), x = (int)(i - (long long)y * L.width);
+        f = flags[(long long)y * flag_pitch + x] != 0;
+        if (!f) store_px(L, x, y, load_px(L, x, y));
+      }
+      m[k] = __ballot_sync(0xffffffffu, f);
+      mine += __popc(m[k]);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, f);
-    if (m != 0u) {
-      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-      unsigned base = 0u;
-      if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (f) list[base + __popc(m & ((1u << lane) - 1u))] = (int)i;
+    if (lane == 0) s_off[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned tot = 0;
+      for (int w = 0; w < 8; ++w) {
+        const unsigned c = s_off[w];
+        s_off[w] = tot;
+        tot += c;
+      }
+      s_tot = tot;
+      s_base = tot ? atomicAdd(count, tot) : 0u;
     }
+    __syncthreads();
+    const unsigned base = s_base, tot = s_tot;
+    if (tot != 0u && base + tot > limit) return;  // uniform: the tile form takes the call
+    unsigned slot = base + s_off[warp];
+#pragma unroll
+    for (int k = 0; k < kCompactPer; ++k) {
+      if ((m[k] >> lane) & 1u) list[slot + __popc(m[k] & below)] = (int)(c0 + k * 256 + threadIdx.x);
+      slot += __popc(m[k]);
+    }
+    __syncthreads();  // s_off and s_base are rewritten in the next round
   }
 }
 
@@ -1378,8 +1408,10 @@ vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) {
-      const long long blocks = std::min<long long>((total + 255) / 256, 8LL * sms);
-      gated_compact<<<(int)blocks, 256, 0, s>>>(L, d_flags, (long long)flag_pitch, list, count);
+      const long long blocks =
+          std::min<long long>((total + 256 * kCompactPer - 1) / (256 * kCompactPer), 8LL * sms);
+      gated_compact<<<(int)blocks, 256, 0, s>>>(L, d_flags, (long long)flag_pitch, list, count,
+                                                limit);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

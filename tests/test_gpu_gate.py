@@ -158,6 +158,7 @@ def test_gated_filter_identities(vf, mode):
     t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
     kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
     vf.set_option("pair_reuse", mode)
+    vf.set_option("gated_sparse", 0)  # the tile forms
     try:
         plain = vf.filter(t, **kw)
         ones = torch.ones((45, 77), dtype=torch.uint8, device="cuda")
@@ -171,6 +172,7 @@ def test_gated_filter_identities(vf, mode):
         torch.cuda.synchronize()
     finally:
         vf.set_option("pair_reuse", 1)
+        vf.set_option("gated_sparse", 200)
     m = half.bool().unsqueeze(-1).expand_as(t)
     assert torch.equal(mixed[m], plain[m]) and torch.equal(mixed[~m], t[~m])
     assert st[2].item() == int(half.sum().item()) and st[0].item() == 45 * 77
@@ -196,9 +198,13 @@ def test_gated_reuse_sparse_flags(vf, w, approx):
     f[100, 140] = f[64, 3] = f[129, 149] = 1
     flags = torch.from_numpy(f).cuda()
     st = torch.zeros(3, dtype=torch.int64, device="cuda")
-    out = vf.filter_gated(t, flags, stats=st, **kw)
-    none = vf.filter_gated(t, torch.zeros_like(flags), **kw)
-    torch.cuda.synchronize()
+    vf.set_option("gated_sparse", 0)  # the tile form, whatever the flagged fraction
+    try:
+        out = vf.filter_gated(t, flags, stats=st, **kw)
+        none = vf.filter_gated(t, torch.zeros_like(flags), **kw)
+        torch.cuda.synchronize()
+    finally:
+        vf.set_option("gated_sparse", 200)
     m = flags.bool().unsqueeze(-1).expand_as(t)
     assert torch.equal(out[m], plain[m]) and torch.equal(out[~m], t[~m])
     assert torch.equal(none, t)
@@ -231,7 +237,7 @@ def test_gated_sparse_form(vf, crit, w, approx):
             out = vf.filter_gated(t, flags, stats=st, **kw)
             torch.cuda.synchronize()
         finally:
-            vf.set_option("gated_sparse", 0)
+            vf.set_option("gated_sparse", 200)
             vf.set_option("pair_reuse", 1)
         return out, st.tolist()
 
