@@ -263,20 +263,20 @@ __device__ __forceinline__ void reuse_tile_body(const Launch& L, int tile) {
         }
       };
       static_for<-M, M>(one);
-      return;
-    }
-    for (int item = threadIdx.x; item < (2 * M + 1) * NR; item += G::THREADS) {
-      const int dxi = item / NR, p = item - dxi * NR;
-      const int dx = dxi - M;
-      const int r = p / RX, c = p - r * RX;
-      const bool col_in = c + dx >= 0 && c + dx < RX;
-      const auto xp = load_sample(src + p);
+    } else {
+      for (int item = threadIdx.x; item < (2 * M + 1) * NR; item += G::THREADS) {
+        const int dxi = item / NR, p = item - dxi * NR;
+        const int dx = dxi - M;
+        const int r = p / RX, c = p - r * RX;
+        const bool col_in = c + dx >= 0 && c + dx < RX;
+        const auto xp = load_sample(src + p);
 #pragma unroll
-      for (int dy = 0; dy <= M; ++dy) {
-        if (dy == 0 && dx <= 0) continue;
-        float v = 0.0f;
-        if (col_in && r + dy < RY) v = term(xp, load_sample(src + p + dy * RX + dx));
-        T[fwd_index<W>(dy, dx) * NR + p] = v;
+        for (int dy = 0; dy <= M; ++dy) {
+          if (dy == 0 && dx <= 0) continue;
+          float v = 0.0f;
+          if (col_in && r + dy < RY) v = term(xp, load_sample(src + p + dy * RX + dx));
+          T[fwd_index<W>(dy, dx) * NR + p] = v;
+        }
       }
     }
   };
