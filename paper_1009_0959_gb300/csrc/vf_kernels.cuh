@@ -561,16 +561,24 @@ __device__ __forceinline__ uint32_t amnf_finish(const Launch& L, const TileSmem&
     return rawc;
   }
   float wsum = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+  const uint32_t rc = rawc & 0x00ffffffu;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     float4 xi = t.px[(py + i / W) * t.sw + px + i % W];
+    const uint32_t ri = t.raw[(py + i / W) * t.sw + px + i % W] & 0x00ffffffu;
     float rh = rcp_approx(L.kappa_scale * agg(i));  // 1 / h_i
-    float dx = xc.x - xi.x, dy = xc.y - xi.y, dz = xc.z - xi.z;
+    // ||x_C - x_i||_1 or ||x_C - x_i||_2^2: exact integers from the packed
+    // bytes (byte-wise |difference|, summed or squared and summed), read as
+    // FP32 through the bits of 2^23 + value: the same values the FP32
+    // differences give, in two integer instructions and one subtraction
     float u;
     if constexpr (CRIT == kAMNFE) {
-      u = (fabsf(dx) + fabsf(dy) + fabsf(dz)) * rh;  // ||(x_C - x_i) / h_i||_1
+      const float d1 = __uint_as_float(__vsadu4(rc, ri) + 0x4B000000u) - 8388608.0f;
+      u = d1 * rh;  // ||(x_C - x_i) / h_i||_1
     } else {
-      u = 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * (rh * rh);  // 0.5 ||.||_2^2
+      const uint32_t d = __vabsdiffu4(rc, ri);
+      const float d2 = __uint_as_float(__dp4a(d, d, 0x4B000000u)) - 8388608.0f;
+      u = 0.5f * d2 * (rh * rh);  // 0.5 ||.||_2^2
     }
     float wi = (rh * rh * rh) * expneg<APX, DEG>(L, u);
     wsum += wi;
