@@ -495,9 +495,19 @@ vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, 
 /* vf_filter restricted to the pixels whose flag byte is non-zero; all other
  * pixels are copied from d_in.  VMF, BVDF, AMNFE and AMNFG in FP32 (EVMF has
  * its own switch: VF_ERR_UNSUPPORTED).  Otherwise as vf_filter; the third
- * counter (VF_STAT_SWITCHED) counts the flagged pixels.  Where vf_filter
- * runs the pair-reuse kernels (VF_OPT_PAIR_REUSE) so does this call, with
- * the same sums: a flagged pixel gets exactly vf_filter's output. */
+ * counter (VF_STAT_SWITCHED) counts the flagged pixels.  Two forms, chosen
+ * on the device under VF_OPT_GATED_SPARSE from the number of flags:
+ *   tile form    where vf_filter runs the pair-reuse kernels
+ *                (VF_OPT_PAIR_REUSE) so does this call, with the same sums
+ *                (tiles without a flag are copied whole), else the
+ *                per-window kernels on each tile's flagged pixels; a flagged
+ *                pixel gets vf_filter's output
+ *   sparse form  the flagged pixels are listed and each is filtered with its
+ *                own window by the per-window kernels' code (the bytes of
+ *                the tile form with VF_OPT_PAIR_REUSE = 0); it can differ
+ *                from vf_filter's output only where two aggregates lie
+ *                within rounding of each other (near ties).
+ * Uses a pixel list in the context's scratch (grown on demand: VF_ERR_OOM). */
 vf_status vf_filter_gated(vf_ctx* ctx, const uint8_t* d_in, uint8_t* d_out, int height, int width,
                           int channels, size_t in_pitch, size_t out_pitch, const uint8_t* d_flags,
                           size_t flag_pitch, const vf_params* p, void* stream,
