@@ -536,6 +536,13 @@ def summarize(sections):
                        "speedup_gated_vs_exact": g.get("speedup_gated_vs_exact"),
                        "psnr_gain_db": round(g["psnr_gated_db_mean"] - g["psnr_plain_db_mean"], 3),
                        "flagged_fraction_mean": g["flagged_fraction_mean"]}
+        pf = g.get("per_frame_forms") or []
+        if pf:  # the cleanest frame: gate + the library's default gated form
+            f0 = min(pf, key=lambda r: r["flagged"])
+            out["gate"]["cleanest_frame"] = {
+                "flagged": f0["flagged"],
+                "speedup_vs_plain": round(f0["plain_ms"] / (f0["gate_ms"] + f0["gated_default_ms"]),
+                                          3)}
     return out
 
 
