@@ -745,13 +745,12 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
                    long long flag_pitch, float* prob, int tiles_x, int ntiles, int* status) {
   extern __shared__ __align__(128) unsigned char g5[];
   __shared__ uint32_t s_taddr;
-  __shared__ __align__(8) unsigned long long s_bar;
-  __shared__ int s_ok;
+  __shared__ __align__(8) unsigned long long s_bar[6];  // the two halves of each layer
+  __shared__ int s_fail;
   __shared__ float s_edge[G5_Y][4][3];  // layer 3: lanes 0, 1 of each quarter, for lanes 30, 31
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, block parity
   const int cell = 32 * q + lane;         // the cell (TMEM lane) this thread reads back
-  const uint32_t bar = g5_smem(&s_bar);
   float* bias = reinterpret_cast<float*>(g5 + G5_OFF_BIAS);
 
   // B operands ([K half][n][8 k], 16 bytes per n) and biases, once.  Column
@@ -797,8 +796,10 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
         make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(1));
+    for (int k = 0; k < 6; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(g5_smem(&s_bar[k])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_fail = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -873,26 +874,40 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
 
-  // one layer: thread 0 issues its MMAs (in order) and commits them to the
-  // mbarrier, then waits on it; the others wait at the barrier after it.
-  // `during` runs on every thread while the MMAs are in flight (thread 0:
-  // after issuing them)
-  auto run_layer = [&](auto issue, auto during) -> bool {
-    g5_proxy_fence();  // the generic-proxy writes of the operands, for the tensor cores
+  // Each layer's MMAs go out in two halves, each committed to its own
+  // mbarrier: the epilogue of the first half's finished output rows runs
+  // while the second half's MMAs do (and the next layer's first half while
+  // the epilogue of the second).  Thread 0 issues (in order: the halves
+  // accumulate onto shared blocks) right after a barrier that published the
+  // operands; every thread then waits on the mbarrier itself (bounded; a
+  // wait that gives up marks the tile failed and the loop stops).
+  auto publish = [&] {  // operands (generic proxy) and cleared blocks, for the MMAs
+    g5_fence_before();
+    g5_proxy_fence();
     __syncthreads();
+  };
+  auto issue = [&](int k, auto mmas) {
     if (tid == 0) {
       g5_fence_after();
-      issue();
+      mmas();
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              bar));
+              g5_smem(&s_bar[k])));
     }
-    during();
-    if (tid == 0) s_ok = g5_wait(bar, parity) ? 1 : 0;
-    __syncthreads();
-    parity ^= 1u;
+  };
+  auto await = [&](int k) {
+    if (!g5_wait(g5_smem(&s_bar[k]), parity)) s_fail = 1;
     g5_fence_after();
-    return s_ok != 0;
+  };
+  // clears this warp's blocks (parity h) among [lo, hi)
+  auto clear = [&](int lo, int hi) {
+    const uint32_t z = 0u;
+    for (int b = lo + ((h - lo) & 1); b < hi; b += 2)
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+          "%1,%1,%1,%1};\n" ::"r"(lane_addr + 16 * b),
+          "r"(z));
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
   };
 
   bool ok = true;
@@ -925,24 +940,30 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
       }
       *reinterpret_cast<uint4*>(g5 + G5_OFF_X0 + r * G5_RP + c * 16) = make_uint4(w01, w23, 0u, 0u);
     }
-    // layer 1: x0 row pairs (r, r + 1), r even, into blocks r .. r + 3
-    ok = run_layer([&] {
-      for (int r = 0; r < G5_R0; r += 2)
+    // layer 1: x0 row pairs (r, r + 1), r even, into blocks r .. r + 3; the
+    // first half (x0 rows 0-5) completes output rows 0-3 (blocks 2-5)
+    publish();
+    issue(0, [&] {
+      for (int r = 0; r < G5_R0 / 2; r += 2)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N1>(tmem + 16 * r, dx0 + r * kRowD + v * kCellD, db1 + v * kB1D);
-    }, [] {});
-    if (!ok) break;
-    // this thread's output rows (block parity h), two tcgen05.ld per wait:
-    // z + bias, ReLU, BF16, into the next layer's two planes (0 outside the
-    // image); then its blocks are cleared for the next layer
-    auto act_rows = [&](int rows, int gy0, int gx0, const float* bs, unsigned char* planes,
-                        int plane_bytes) {
+    });
+    issue(1, [&] {
+      for (int r = G5_R0 / 2; r < G5_R0; r += 2)
+        for (int v = 0; v < 3; ++v)
+          g5_mma<G5_N1>(tmem + 16 * r, dx0 + r * kRowD + v * kCellD, db1 + v * kB1D);
+    });
+    // output rows [y0, y1) of this thread's parity h, two tcgen05.ld per
+    // wait: z + bias, ReLU, BF16, into the next layer's two planes (0
+    // outside the image)
+    auto act_rows = [&](int y0, int y1, int gy0, int gx0, const float* bs,
+                        unsigned char* planes, int plane_bytes) {
       float b[16];  // in registers: the stores below may not alias them
 #pragma unroll
       for (int k = 0; k < 16; ++k) b[k] = bs[k];
-      for (int y = h; y < rows; y += 4) {
+      for (int y = y0 + ((h - y0) & 1); y < y1; y += 4) {
         uint32_t z[2][16];
-        const bool two = y + 2 < rows;
+        const bool two = y + 2 < y1;
         g5_ld16(lane_addr + 16 * (y + 2), z[0]);
         if (two) g5_ld16(lane_addr + 16 * (y + 4), z[1]);
         g5_wait_ld();
@@ -962,26 +983,54 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
           *reinterpret_cast<uint4*>(dst + plane_bytes) = make_uint4(w[4], w[5], w[6], w[7]);
         }
       }
-      g5_clear(lane_addr, h);
-      g5_fence_before();
     };
-    act_rows(G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
-    // layer 2: a1 rows r, shifted by tap column v, into blocks r .. r + 2
-    ok = run_layer([&] {
-      for (int r = 0; r < G5_R1; ++r)
+    // layer 1, first half: a1 rows 0-3; blocks 0-5 cleared (the second
+    // half's MMAs write blocks 6-13)
+    await(0);
+    act_rows(0, 4, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
+    clear(0, 6);
+    publish();
+    // layer 2, first half: a1 rows 0-3 into blocks 0-5 (output rows 0-1 complete)
+    issue(2, [&] {
+      for (int r = 0; r < 4; ++r)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N2>(tmem + 16 * r, da1 + r * kRowD + v * kCellD, db2 + v * kB2D);
-    }, [] {});
-    if (!ok) break;
-    act_rows(G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);  // a2 over x0
-    // layer 3 (one output channel): a2 rows r, unshifted, into blocks r ..
-    // r + 2; column v of output row y's block is the sum over the tap row
-    // and channels for tap column v at this cell.  The next tile's pixels
-    // are fetched while the MMAs run.
-    ok = run_layer([&] {
-      for (int r = 0; r < G5_R2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
-    }, [&] { fetch(tile + gridDim.x); });
-    if (!ok) break;
+    });
+    // layer 1, second half: a1 rows 4-9; blocks 6-13 cleared
+    await(1);
+    act_rows(4, G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
+    clear(6, G5_BLOCKS);
+    publish();
+    // layer 2, second half: a1 rows 4-9 into blocks 4-11
+    issue(3, [&] {
+      for (int r = 4; r < G5_R1; ++r)
+        for (int v = 0; v < 3; ++v)
+          g5_mma<G5_N2>(tmem + 16 * r, da1 + r * kRowD + v * kCellD, db2 + v * kB2D);
+    });
+    // layer 2, first half: a2 rows 0-1 (over x0, whose MMAs are done);
+    // blocks 0-3 cleared
+    await(2);
+    act_rows(0, 2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);
+    clear(0, 4);
+    publish();
+    // layer 3 (one output channel), first half: a2 rows 0-1, unshifted, into
+    // blocks 0-3; column v of output row y's block is the sum over the tap
+    // row and channels for tap column v at this cell
+    issue(4, [&] {
+      for (int r = 0; r < 2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
+    });
+    // layer 2, second half: a2 rows 2-7; blocks 4-13 cleared
+    await(3);
+    act_rows(2, G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);
+    clear(4, G5_BLOCKS);
+    publish();
+    // layer 3, second half: a2 rows 2-7 into blocks 2-9; the next tile's
+    // pixels are fetched while the MMAs run
+    issue(5, [&] {
+      for (int r = 2; r < G5_R2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
+    });
+    fetch(tile + gridDim.x);
+    await(5);
     // logit of cell x: column 0 of cell x + column 1 of cell x + 1 + column 2
     // of cell x + 2 (shuffles; the next lane quarter's first lanes through
     // shared memory)
@@ -1006,7 +1055,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
         s_edge[y][q][2] = c2[i];
       }
     }
-    g5_clear(lane_addr, h);  // the next tile's layer-1 accumulators
+    clear(0, 10);  // the next tile's layer-1 accumulators (blocks 10-13 are clear)
     g5_fence_before();
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // published by the barrier
     __syncthreads();
@@ -1027,7 +1076,9 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
         if (prob) prob[(long long)gy * I.W + gx] = 1.0f / (1.0f + expf(-z));
       }
     }
+    parity ^= 1u;
     __syncthreads();  // the tile's reads of the x0 / a2 planes and of s_edge are done
+    ok = s_fail == 0;  // uniform: read after the barrier
   }
   if (!ok && tid == 0) atomicExch(status, 1);
   g5_fence_before();
