@@ -657,7 +657,8 @@ constexpr int G5_RAW_CW = G5_CW + 2;                  // raw cells per row: xs -
 constexpr int G5_OFF_RAW = G5_OFF_A1 + 2 * G5_A1P;      // the next tile's pixels (32-bit)
 constexpr int G5_SMEM = G5_OFF_RAW + G5_R0 * G5_RAW_CW * 4;
 static_assert(G5_X % 4 == 0 && G5_RAW_CW % 4 == 0, "raw rows are whole 16-byte chunks");
-constexpr int G5_THREADS = 256;
+constexpr int G5_THREADS = 256;                        // epilogue threads (eight warps)
+constexpr int G5_BLOCK = G5_THREADS + 32;              // and one warp that issues the MMAs
 constexpr int G5_BLOCKS = G5_R0 + 2;                   // TMEM blocks (output rows -2 .. R0 - 1)
 constexpr int G5_TMEM_COLS = 256;
 static_assert(G5_R0 * G5_RP <= 2 * G5_A2P, "x0 fits in the a2 planes it shares");
@@ -740,7 +741,7 @@ __device__ __forceinline__ void g5_proxy_fence() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(G5_THREADS, 2)
+__global__ void __launch_bounds__(G5_BLOCK, 2)
     gate_infer_tc5(Images I, const __nv_bfloat16* wb, float logit_threshold, uint8_t* flags,
                    long long flag_pitch, float* prob, int tiles_x, int ntiles, int* status) {
   extern __shared__ __align__(128) unsigned char g5[];
@@ -749,6 +750,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   __shared__ int s_fail;
   __shared__ float s_edge[G5_Y][4][3];  // layer 3: lanes 0, 1 of each quarter, for lanes 30, 31
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool worker = warp < G5_THREADS / 32;  // the last warp only issues MMAs
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter, block parity
   const int cell = 32 * q + lane;         // the cell (TMEM lane) this thread reads back
   float* bias = reinterpret_cast<float*>(g5 + G5_OFF_BIAS);
@@ -756,7 +758,8 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   // B operands ([K half][n][8 k], 16 bytes per n) and biases, once.  Column
   // group g of an operand (n = 16 g + o) holds tap row 2 - g (layer 1's
   // second K half, the next input row: tap row 3 - g).
-  for (int e = tid; e < 3 * G5_N1 * 16 + 3 * G5_N2 * 16 + G5_N3 * 16; e += G5_THREADS) {
+  for (int e = tid; worker && e < 3 * G5_N1 * 16 + 3 * G5_N2 * 16 + G5_N3 * 16;
+       e += G5_THREADS) {
     int off, nn, idx;
     float v = 0.0f;
     if (e < 3 * G5_N1 * 16) {  // layer 1, tap column tv: K = (row half, channel)
@@ -790,7 +793,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   else if (tid < 2 * kC) bias[tid] = __bfloat162float(wb[OFF_B2 + tid - kC]);
   else if (tid == 2 * kC) bias[tid] = __bfloat162float(wb[OFF_B3]);
   // the two padding cells of every a1 row (read only by discarded cells)
-  for (int e = tid; e < 2 * G5_R1 * 2; e += G5_THREADS) {
+  for (int e = tid; worker && e < 2 * G5_R1 * 2; e += G5_THREADS) {
     const int plane = e / (2 * G5_R1), r = (e / 2) % G5_R1, c = 128 + (e & 1);
     *reinterpret_cast<uint4*>(g5 + G5_OFF_A1 + plane * G5_A1P + r * G5_RP + c * 16) =
         make_uint4(0u, 0u, 0u, 0u);
@@ -812,7 +815,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   g5_fence_after();
   const uint32_t tmem = s_taddr;
   const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
-  g5_clear(lane_addr, h);  // the first tile's accumulators
+  if (worker) g5_clear(lane_addr, h);  // the first tile's accumulators
   g5_fence_before();
   uint32_t parity = 0;
   const bool word = I.channels == 4 && (reinterpret_cast<uintptr_t>(I.img) & 3) == 0 &&
@@ -840,6 +843,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
   uint32_t pre[kPre];
   uint32_t* raw = reinterpret_cast<uint32_t*>(g5 + G5_OFF_RAW);
   auto fetch = [&](int t) {
+    if (!worker) return;
     const int xs = (t % tiles_x) * G5_X, ys = (t / tiles_x) * G5_Y;
     if (vec) {
       for (int j = tid; j < kChunks; j += G5_THREADS) {
@@ -887,7 +891,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     __syncthreads();
   };
   auto issue = [&](int k, auto mmas) {
-    if (tid == 0) {
+    if (tid == G5_THREADS) {
       g5_fence_after();
       mmas();
       asm volatile(
@@ -896,11 +900,13 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     }
   };
   auto await = [&](int k) {
+    if (!worker) return;
     if (!g5_wait(g5_smem(&s_bar[k]), parity)) s_fail = 1;
     g5_fence_after();
   };
   // clears this warp's blocks (parity h) among [lo, hi)
   auto clear = [&](int lo, int hi) {
+    if (!worker) return;
     const uint32_t z = 0u;
     for (int b = lo + ((h - lo) & 1); b < hi; b += 2)
       asm volatile(
@@ -921,7 +927,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
       const int e = tid + j * G5_THREADS;
-      if (e >= G5_R0 * G5_CW) break;
+      if (!worker || e >= G5_R0 * G5_CW) break;
       const int r = e / G5_CW, c = e - r * G5_CW;
       const int gy = ys - 3 + r, gx = xs - 3 + c;
       const uint32_t px = (vec || word) ? raw[r * G5_RAW_CW + c + 1] : pre[j];
@@ -958,6 +964,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     // outside the image)
     auto act_rows = [&](int y0, int y1, int gy0, int gx0, const float* bs,
                         unsigned char* planes, int plane_bytes) {
+      if (!worker) return;
       float b[16];  // in registers: the stores below may not alias them
 #pragma unroll
       for (int k = 0; k < 16; ++k) b[k] = bs[k];
@@ -1035,24 +1042,26 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     // of cell x + 2 (shuffles; the next lane quarter's first lanes through
     // shared memory)
     const float b3 = bias[2 * kC];
-    float c0[3], c1[3], c2[3];
+    float c0[3] = {}, c1[3] = {}, c2[3] = {};
+    if (worker) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int y = h + 2 * i;
-      const uint32_t a = lane_addr + 16 * (y + 2);
-      c0[i] = __uint_as_float(g5_ld1(a));
-      c1[i] = __uint_as_float(g5_ld1(a + 1));
-      c2[i] = __uint_as_float(g5_ld1(a + 2));
-    }
-    g5_wait_ld();
+      for (int i = 0; i < 3; ++i) {
+        const int y = h + 2 * i;
+        const uint32_t a = lane_addr + 16 * (y + 2);
+        c0[i] = __uint_as_float(g5_ld1(a));
+        c1[i] = __uint_as_float(g5_ld1(a + 1));
+        c2[i] = __uint_as_float(g5_ld1(a + 2));
+      }
+      g5_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int y = h + 2 * i;
-      if (lane == 0) {
-        s_edge[y][q][0] = c1[i];
-        s_edge[y][q][1] = c2[i];
-      } else if (lane == 1) {
-        s_edge[y][q][2] = c2[i];
+      for (int i = 0; i < 3; ++i) {
+        const int y = h + 2 * i;
+        if (lane == 0) {
+          s_edge[y][q][0] = c1[i];
+          s_edge[y][q][1] = c2[i];
+        } else if (lane == 1) {
+          s_edge[y][q][2] = c2[i];
+        }
       }
     }
     clear(0, 10);  // the next tile's layer-1 accumulators (blocks 10-13 are clear)
@@ -1060,7 +1069,7 @@ __global__ void __launch_bounds__(G5_THREADS, 2)
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // published by the barrier
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 3 && worker; ++i) {
       const int y = h + 2 * i;
       float s1 = __shfl_down_sync(0xffffffffu, c1[i], 1);
       float s2 = __shfl_down_sync(0xffffffffu, c2[i], 2);
@@ -1399,7 +1408,7 @@ vf_status vf_gate_infer(vf_gate* g, const uint8_t* d_in, int height, int width, 
     e = cudaFuncSetAttribute(gate_infer_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              G5_SMEM);
     if (e == cudaSuccess) {
-      gate_infer_tc5<<<grid, G5_THREADS, G5_SMEM, (cudaStream_t)stream>>>(
+      gate_infer_tc5<<<grid, G5_BLOCK, G5_SMEM, (cudaStream_t)stream>>>(
           I, g->wb, thr, d_flags, (long long)flag_pitch, d_prob, tiles_x, (int)ntiles,
           g->d_status);
       e = cudaGetLastError();
