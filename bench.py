@@ -129,7 +129,8 @@ MEASURED_PER_PIXEL = {
     ('evmf', 'poly', 4, 5): {"fp32": 814.9, "inst": 1921.1, "dram": 6.898, "fma_pipe": 0.361},
     ('evmf', 'rational', 0, 5): {"fp32": 934.1, "inst": 2068.9, "dram": 6.947, "fma_pipe": 0.384},
     ("evmf", "exact", 0, 5): {"fp32": 1083.8, "inst": 2432.6, "dram": 6.899, "fma_pipe": 0.378},
-    ("amnfe", "exact", 0, 5): {"fp32": 506.0, "inst": 1289.1, "dram": 7.040, "fma_pipe": 0.308},
+    ("amnfe", "exact", 0, 5): {"fp32": 406.0, "inst": 1260.0, "dram": 7.050, "fma_pipe": 0.291},
+    ("amnfe", "rational", 0, 5): {"fp32": 481.0, "inst": 1314.0, "dram": 7.040, "fma_pipe": 0.298},
     ("vmf", "exact", 0, 5): {"fp32": 613.5, "inst": 1466.3, "dram": 7.063, "fma_pipe": 0.439},
 }
 
