@@ -640,10 +640,15 @@ __global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv
 // 124 x 6 (the 128-cell rows shrink by two cells per layer); two CTAs per
 // SM, persistent over the tiles.  Numerics as gate_infer_tc: BF16 input and
 // activations between layers, BF16 weights, FP32 accumulation and biases.
-constexpr int G5_X = 124, G5_Y = 6;                    // outputs per tile
+constexpr int G5_X = 124, G5_Y = 6;                    // outputs per tile (8: no faster)
 constexpr int G5_CW = 130;                             // cells per staged row
 constexpr int G5_RP = G5_CW * 16;                      // bytes per staged row
 constexpr int G5_R0 = G5_Y + 6, G5_R1 = G5_Y + 4, G5_R2 = G5_Y + 2;  // rows of x0, a1, a2
+// the halves of each layer: layer 1's first half takes the x0 row pairs below
+// G5_H1 and completes output rows [0, G5_O1); layer 2's first half takes a1
+// rows [0, G5_O1) and completes rows [0, G5_O2); layer 3's a2 rows [0, G5_O2)
+constexpr int G5_H1 = 2 * ((G5_R0 / 2 + 1) / 2), G5_O1 = G5_H1 - 2, G5_O2 = G5_O1 - 2;
+static_assert(G5_Y % 2 == 0 && G5_O2 > 0, "even tile heights, non-empty halves");
 constexpr int G5_A1P = G5_R1 * G5_RP, G5_A2P = G5_R2 * G5_RP;      // plane bytes
 constexpr int G5_N1 = 64, G5_N2 = 48, G5_N3 = 48;      // MMA widths of the layers
 constexpr int G5_B1 = 2 * G5_N1 * 16, G5_B2 = 2 * G5_N2 * 16;  // bytes of one B operand
@@ -950,12 +955,12 @@ __global__ void __launch_bounds__(G5_BLOCK, 2)
     // first half (x0 rows 0-5) completes output rows 0-3 (blocks 2-5)
     publish();
     issue(0, [&] {
-      for (int r = 0; r < G5_R0 / 2; r += 2)
+      for (int r = 0; r < G5_H1; r += 2)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N1>(tmem + 16 * r, dx0 + r * kRowD + v * kCellD, db1 + v * kB1D);
     });
     issue(1, [&] {
-      for (int r = G5_R0 / 2; r < G5_R0; r += 2)
+      for (int r = G5_H1; r < G5_R0; r += 2)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N1>(tmem + 16 * r, dx0 + r * kRowD + v * kCellD, db1 + v * kB1D);
     });
@@ -994,47 +999,47 @@ __global__ void __launch_bounds__(G5_BLOCK, 2)
     // layer 1, first half: a1 rows 0-3; blocks 0-5 cleared (the second
     // half's MMAs write blocks 6-13)
     await(0);
-    act_rows(0, 4, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
-    clear(0, 6);
+    act_rows(0, G5_O1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
+    clear(0, G5_O1 + 2);
     publish();
     // layer 2, first half: a1 rows 0-3 into blocks 0-5 (output rows 0-1 complete)
     issue(2, [&] {
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < G5_O1; ++r)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N2>(tmem + 16 * r, da1 + r * kRowD + v * kCellD, db2 + v * kB2D);
     });
     // layer 1, second half: a1 rows 4-9; blocks 6-13 cleared
     await(1);
-    act_rows(4, G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
-    clear(6, G5_BLOCKS);
+    act_rows(G5_O1, G5_R1, ys - 2, xs - 2, bias, g5 + G5_OFF_A1, G5_A1P);
+    clear(G5_O1 + 2, G5_BLOCKS);
     publish();
     // layer 2, second half: a1 rows 4-9 into blocks 4-11
     issue(3, [&] {
-      for (int r = 4; r < G5_R1; ++r)
+      for (int r = G5_O1; r < G5_R1; ++r)
         for (int v = 0; v < 3; ++v)
           g5_mma<G5_N2>(tmem + 16 * r, da1 + r * kRowD + v * kCellD, db2 + v * kB2D);
     });
     // layer 2, first half: a2 rows 0-1 (over x0, whose MMAs are done);
     // blocks 0-3 cleared
     await(2);
-    act_rows(0, 2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);
-    clear(0, 4);
+    act_rows(0, G5_O2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);
+    clear(0, G5_O2 + 2);
     publish();
     // layer 3 (one output channel), first half: a2 rows 0-1, unshifted, into
     // blocks 0-3; column v of output row y's block is the sum over the tap
     // row and channels for tap column v at this cell
     issue(4, [&] {
-      for (int r = 0; r < 2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
+      for (int r = 0; r < G5_O2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
     });
     // layer 2, second half: a2 rows 2-7; blocks 4-13 cleared
     await(3);
-    act_rows(2, G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);
-    clear(4, G5_BLOCKS);
+    act_rows(G5_O2, G5_R2, ys - 1, xs - 1, bias + kC, g5 + G5_OFF_X0, G5_A2P);
+    clear(G5_O2 + 2, G5_BLOCKS);
     publish();
     // layer 3, second half: a2 rows 2-7 into blocks 2-9; the next tile's
     // pixels are fetched while the MMAs run
     issue(5, [&] {
-      for (int r = 2; r < G5_R2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
+      for (int r = G5_O2; r < G5_R2; ++r) g5_mma<G5_N3>(tmem + 16 * r, da2 + r * kRowD, db3);
     });
     fetch(tile + gridDim.x);
     await(5);
@@ -1042,10 +1047,11 @@ __global__ void __launch_bounds__(G5_BLOCK, 2)
     // of cell x + 2 (shuffles; the next lane quarter's first lanes through
     // shared memory)
     const float b3 = bias[2 * kC];
-    float c0[3] = {}, c1[3] = {}, c2[3] = {};
+    constexpr int kOut = G5_Y / 2;  // output rows per thread
+    float c0[kOut] = {}, c1[kOut] = {}, c2[kOut] = {};
     if (worker) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
+      for (int i = 0; i < kOut; ++i) {
         const int y = h + 2 * i;
         const uint32_t a = lane_addr + 16 * (y + 2);
         c0[i] = __uint_as_float(g5_ld1(a));
@@ -1054,7 +1060,7 @@ __global__ void __launch_bounds__(G5_BLOCK, 2)
       }
       g5_wait_ld();
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
+      for (int i = 0; i < kOut; ++i) {
         const int y = h + 2 * i;
         if (lane == 0) {
           s_edge[y][q][0] = c1[i];
@@ -1064,12 +1070,12 @@ __global__ void __launch_bounds__(G5_BLOCK, 2)
         }
       }
     }
-    clear(0, 10);  // the next tile's layer-1 accumulators (blocks 10-13 are clear)
+    clear(0, G5_R2 + 2);  // the next tile's layer-1 accumulators (the rest are clear)
     g5_fence_before();
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // published by the barrier
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 3 && worker; ++i) {
+    for (int i = 0; i < kOut && worker; ++i) {
       const int y = h + 2 * i;
       float s1 = __shfl_down_sync(0xffffffffu, c1[i], 1);
       float s2 = __shfl_down_sync(0xffffffffu, c2[i], 2);
