@@ -631,12 +631,14 @@ __global__ void __launch_bounds__(TC_THREADS) gate_infer_tc(Images I, const __nv
 // 56 MMAs per tile instead of 162 with one MMA of N = 16 per tap: at these
 // widths an MMA costs the tensor core nearly the same time whatever its N
 // (measured: 61 cycles back to back from one thread for N = 16 .. 64, 66 at
-// 128), so the count is what bounds the kernel.  One thread issues a layer's
-// MMAs (in order: they accumulate onto shared blocks) and commits them to an
-// mbarrier; after the (bounded) wait all eight warps read the accumulators
-// back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4) .. + 31, the blocks
-// of one parity), add the bias, apply ReLU, round to BF16 and write the next
-// layer's planes, then clear the blocks they own.  Outputs per CTA tile:
+// 128), so the count is what bounds the kernel.  A ninth warp only issues
+// the MMAs (in order: they accumulate onto shared blocks), each layer in two
+// halves committed to mbarriers of their own; after the (bounded) wait for a
+// half the eight other warps read its finished output rows back with
+// tcgen05.ld (warp w: TMEM lanes 32 (w mod 4) .. + 31, the blocks of one
+// parity), add the bias, apply ReLU, round to BF16 and write the next
+// layer's planes, then clear the blocks they own -- while the second half's
+// MMAs run.  Outputs per CTA tile:
 // 124 x 6 (the 128-cell rows shrink by two cells per layer); two CTAs per
 // SM, persistent over the tiles.  Numerics as gate_infer_tc: BF16 input and
 // activations between layers, BF16 weights, FP32 accumulation and biases.
