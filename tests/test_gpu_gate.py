@@ -256,6 +256,43 @@ def test_gated_sparse_form(vf, crit, w, approx):
         assert st_a == st_w
 
 
+def test_gated_sparse_form_large(vf):
+    """The sparse form on a 1500 x 2048 image: the compaction's CTAs take
+    several rounds of 1,024 pixels each, and above the limit they stop early
+    (the tile form then rewrites every pixel).  Forced sparse and the
+    per-window tile form agree byte for byte at 5 % flags; under the default
+    limit a 50 % map gives the tile form's bytes and a 5 % map the sparse
+    form's."""
+    h, wd = 1500, 2048
+    clean, noisy = synth.noisy(h, wd, 0.15, 77)
+    t = torch.from_numpy(synth.to_rgbx(noisy)).cuda()
+    kw = dict(criterion="bvdf", window=5, approx="poly", degree=4)
+    rng = np.random.default_rng(3)
+
+    def run(flags, sparse, reuse):
+        vf.set_option("gated_sparse", sparse)
+        vf.set_option("pair_reuse", reuse)
+        try:
+            st = torch.zeros(3, dtype=torch.int64, device="cuda")
+            out = vf.filter_gated(t, flags, stats=st, **kw)
+            torch.cuda.synchronize()
+        finally:
+            vf.set_option("gated_sparse", 200)
+            vf.set_option("pair_reuse", 1)
+        return out, st.tolist()
+
+    for d in (0.05, 0.5):
+        flags = torch.from_numpy((rng.random((h, wd)) < d).astype(np.uint8)).cuda()
+        window, st_w = run(flags, 0, 0)
+        sparse, st_s = run(flags, 1000, 0)
+        assert torch.equal(sparse, window) and st_s == st_w
+        assert st_s[0] == h * wd and st_s[2] == int(flags.sum().item())
+        tiles, st_t = run(flags, 0, 1)
+        auto, st_a = run(flags, 200, 1)
+        want, st_want = (sparse, st_s) if d < 0.2 else (tiles, st_t)
+        assert torch.equal(auto, want) and st_a == st_want
+
+
 def test_trained_gate_beats_plain_filter(vf):
     """Trained on the GPU by the library's own kernels, the gate flags the
     impulses; the gated 5 x 5 minimax BVDF keeps the clean pixels untouched
