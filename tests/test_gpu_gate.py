@@ -288,6 +288,11 @@ def test_gated_sparse_form_large(vf):
         assert torch.equal(sparse, window) and st_s == st_w
         assert st_s[0] == h * wd and st_s[2] == int(flags.sum().item())
         tiles, st_t = run(flags, 0, 1)
+        # the persistent pair-reuse tiles, many per CTA: the plain filter's
+        # bytes where flagged, the input elsewhere
+        plain = vf.filter(t, **kw)
+        m = flags.bool().unsqueeze(-1).expand_as(t)
+        assert torch.equal(tiles[m], plain[m]) and torch.equal(tiles[~m], t[~m])
         auto, st_a = run(flags, 200, 1)
         want, st_want = (sparse, st_s) if d < 0.2 else (tiles, st_t)
         assert torch.equal(auto, want) and st_a == st_want
