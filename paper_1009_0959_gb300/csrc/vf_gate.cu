@@ -1097,7 +1097,13 @@ __global__ void __launch_bounds__(G5_BLOCK, 2)
     __syncthreads();  // the tile's reads of the x0 / a2 planes and of s_edge are done
     ok = s_fail == 0;  // uniform: read after the barrier
   }
-  if (!ok && tid == 0) atomicExch(status, 1);
+  if (!ok) {
+    if (tid == 0) atomicExch(status, 1);
+    // a wait gave up: before the accumulators are freed, wait once more
+    // (bounded) on the tile's last commit, which tracks every MMA issued
+    // before it (the tile's phase is parity ^ 1 after the flip above)
+    if (worker) g5_wait(g5_smem(&s_bar[5]), parity ^ 1u);
+  }
   g5_fence_before();
   __syncthreads();
   if (warp == 0) {
