@@ -182,6 +182,10 @@ def main():
     ap.add_argument("--sections-out", default="bench_sections.json",
                     help="file for the per-variant, batched, precision, quality-study, EVF and "
                          "gate sections (the printed line carries a summary of them)")
+    ap.add_argument("--streams", type=int, default=3, choices=[1, 2, 3, 4, 6, 8, 12, 16, 24],
+                    help="streams of the graph-captured step: launch i on stream i mod S (S "
+                         "divides the 48 pool slots, so launches sharing an output slot share "
+                         "a stream; 3 = one per image)")
     ap.add_argument("--tile-rows", type=int, default=4, choices=[2, 4, 8],
                     help="VF_OPT_TILE_ROWS of the per-window kernels (default 4)")
     args = ap.parse_args()
@@ -250,13 +254,18 @@ def main():
     stream = torch.cuda.current_stream()
     per = {vkey(c, a, d, w): [] for (c, a, d, w, k) in launches}
 
-    lanes = [torch.cuda.Stream() for _ in range(2)]  # images 1 and 2 in the multi-stream form
+    # streams 1 .. S-1 of the multi-stream form (stream 0: the current one).
+    # Launch i writes pool slot (counter + i) mod POOL and runs on stream i
+    # mod S; S divides POOL, so two launches of a step that share a slot run
+    # on one stream, in order.
+    lanes = [torch.cuda.Stream() for _ in range(args.streams - 1)]
 
     def step(record, multi=False):
         """One step; record: events around every launch (True), around the
         launches of one kernel class (its key), or none (False).  multi: the
-        three images' launches on three streams (forked from and joined to the
-        current stream), so one kernel's tail overlaps the next image's."""
+        launches spread over S streams (forked from and joined to the current
+        stream; S = 3: one per image), so one kernel's tail overlaps the next
+        launches on the other streams."""
         base = torch.cuda.current_stream()  # the bench stream, or the capture stream below
         if multi:
             fork = torch.cuda.Event()
@@ -267,7 +276,8 @@ def main():
             slot = (step.counter + i) % POOL
             src = pool_in[(slot // 3) * 3 + k]  # a copy of image k, rotating
             rec = record is True or record == vkey(c, a, d, w)
-            s = lanes[k - 1] if multi and k > 0 else base
+            j = i % args.streams
+            s = lanes[j - 1] if multi and j > 0 else base
             with torch.cuda.stream(s):
                 if rec:
                     e0 = torch.cuda.Event(enable_timing=True)
@@ -395,7 +405,7 @@ def main():
                              (POOL * 8),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "launch": ("one step captured as a CUDA graph of its vf_filter calls "
-                                  "(three images on three streams), replayed K times")
+                                  "(launch i on stream i mod %d), replayed K times" % args.streams)
                                  if graph is not None else
                                  "vf_filter calls (graph capture failed: %s)" % graph_error},
             "eager": {"value": round(value_eager, 1), "ms_per_step": round(ms_eager / args.steps, 3),
