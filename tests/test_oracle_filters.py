@@ -178,6 +178,29 @@ def test_bvdf_scaled_impulse_kept():
     np.testing.assert_allclose(agg, 0.0, atol=1e-12)
 
 
+def test_bvdf_sums_angles_not_cosine_distances():
+    """BVDF ranks each sample by the sum of its angles to the others (Sec.
+    3.1).  A 3 x 3 window in the R-G plane: five samples along R (0 deg), one
+    at theta = atan(100/173), about 30 deg, three along G (90 deg).  Angle
+    sums: R theta + 3 pi/2 (about 300 deg), the middle sample 5 theta +
+    3 (pi/2 - theta) (about 330 deg), G 5 pi/2 + pi/2 - theta (about 510
+    deg), so an R sample wins, the first in raster order.  Summing the
+    cosine distance 1 - cos instead (3.13, 2.17, 5.50) would pick the
+    middle sample."""
+    r, m, g = (200, 0, 0), (173, 100, 0), (0, 200, 0)
+    img = np.array([[r, r, g], [r, m, r], [g, r, g]], np.uint8)
+    th = math.atan2(100, 173)
+    want = {r: th + 3 * math.pi / 2, m: 5 * th + 3 * (math.pi / 2 - th),
+            g: 5 * math.pi / 2 + (math.pi / 2 - th)}
+    xs = _window(img, 1, 1, 3)
+    agg = F.window_aggregates(F.Config("bvdf", 3), xs)
+    for x, v in zip(xs, agg):
+        assert v == pytest.approx(want[tuple(int(t) for t in x)], rel=1e-12)
+    out, d = F.filter_image(img, F.Config("bvdf", 3))
+    assert d["sel"][1, 1] == 0
+    assert tuple(out[1, 1]) == r
+
+
 # ---------------------------------------------------------------- AMNF
 
 
@@ -201,6 +224,14 @@ def test_amnf_two_value_closed_form(crit, k):
     y = ((n - k) * wa * a + k * wb * b) / ((n - k) * wa + k * wb)
     got = F.window_amnf(F.Config(crit, 3), xs)
     np.testing.assert_allclose(got, y, rtol=1e-13)
+    # the filter writes y rounded to the nearest 8-bit level (the output is a
+    # colour of the 8-bit image): the same window as a 3 x 3 image, centre
+    # output; y has no channel near a half level, and channels with a
+    # fraction above one half tell rounding from truncation
+    frac = y - np.floor(y)
+    assert (np.abs(frac - 0.5) > 1e-6).all()
+    out, _ = F.filter_image(xs.reshape(3, 3, 3).astype(np.uint8), F.Config(crit, 3))
+    np.testing.assert_array_equal(out[1, 1], np.floor(y) + (frac > 0.5))
 
 
 def test_amnf_within_window_range():
