@@ -28,6 +28,47 @@ def test_conv_shift_and_zero_padding():
     np.testing.assert_allclose(z, ref)
 
 
+def test_forward_closed_form_through_the_relus():
+    """A hand-wired network whose logit has a closed form.  Layer 1 splits
+    the centred red channel r = R/255 - 1/2 into a1[0] = max(r, 0) and
+    a1[1] = max(-r, 0); layer 2 forms a2[0] = max(0.5 a1[1] - 0.1, 0) and
+    a2[1] = max(a1[0] + 3 a1[1], 0); layer 3 weighs them 1 and 2, so
+    z3 = max(0.5 max(-r, 0) - 0.1, 0) + 2 (max(r, 0) + 3 max(-r, 0)) and
+    p = sigmoid(z3).  Without the first ReLU a2[1] would be max(-2r, 0),
+    without the second a2[0] could go negative; an uncentred input, a bias
+    after the ReLU or layer 2's [out][in] weights read as [in][out]
+    (0.5 and 1 swapped) change it too."""
+    R = np.array([[0, 12, 60, 76], [127, 128, 200, 255]], np.uint8)
+    img = np.zeros(R.shape + (3,), np.uint8)
+    img[..., 0] = R
+    img[..., 1] = 77  # other channels: weight 0
+    p = {name: np.zeros(shp) for name, shp in G.SHAPES}
+    p["W1"][0, 0, 1, 1], p["W1"][1, 0, 1, 1] = 1.0, -1.0
+    p["W2"][0, 1, 1, 1] = 0.5
+    p["W2"][1, 0, 1, 1], p["W2"][1, 1, 1, 1] = 1.0, 3.0
+    p["b2"][0] = -0.1
+    p["W3"][0, 0, 1, 1], p["W3"][0, 1, 1, 1] = 1.0, 2.0
+    c = G.forward(img, G.flatten(p))
+    r = R / 255.0 - 0.5
+    pos, neg = np.maximum(r, 0.0), np.maximum(-r, 0.0)
+    z3 = np.maximum(0.5 * neg - 0.1, 0.0) + 2.0 * (pos + 3.0 * neg)
+    np.testing.assert_allclose(c["z3"], z3, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(c["p"], 1.0 / (1.0 + np.exp(-z3)), rtol=1e-13)
+
+
+def test_target_mask_rule():
+    """A pixel is a target when some channel moved by more than the threshold
+    (12 levels): 13 in one channel is, 12 is not, and 5 + 5 + 5 in three
+    channels is not (the largest channel decides, not the sum)."""
+    clean = np.full((1, 5, 3), 100, np.uint8)
+    noisy = clean.copy()
+    noisy[0, 1] = (113, 100, 100)
+    noisy[0, 2] = (100, 88, 100)
+    noisy[0, 3] = (105, 95, 105)
+    noisy[0, 4] = (100, 100, 87)
+    np.testing.assert_array_equal(G.target_mask(clean, noisy), [[0, 1, 0, 0, 1]])
+
+
 def test_conv_grads_adjoint():
     """<dz, conv(x)> is linear in x and W: its gradients are the adjoints."""
     rng = np.random.default_rng(1)
