@@ -68,6 +68,37 @@ def test_exp_paper_rational_level(golden):
     assert 0.9 * eps <= err <= 1.2 * eps
 
 
+@pytest.mark.parametrize("key,kind,f,lo,hi", [
+    ("exp_rational", "exp", lambda z: np.exp(-z), 0.0, 10.0),
+    ("ent_rational", "ent", lambda z: z * np.log(z), 0.05, 1.0)])
+def test_paper_rationals_through_python_approximant(golden, key, kind, f, lo, hi):
+    """The printed (4,4) rationals (tab_exp_rat, tab_ent_rat) evaluated by the
+    oracle's Python `Approximant` (the coefficients the C oracle and the GPU
+    tests receive): within [0.9, 1.2] x the printed eps of the target."""
+    ap = AP.exp_approximant("rational", 4) if kind == "exp" else AP.ent_approximant("rational", 4)
+    z = np.linspace(lo, hi, 40001)
+    err = float(np.max(np.abs(ap(z) - f(z))))
+    eps = golden[key]["eps"]
+    assert 0.9 * eps <= err <= 1.2 * eps
+
+
+def test_acos_pieces_are_table1(golden):
+    """The BVDF pieces the filters receive (`acos_pieces`, degree 4, the
+    oracle's own fit) are Table 1's rows: the same intervals, coefficients to
+    the printed digits, and the pieces within their printed eps of arccos on
+    each side of z = 0.5 (Sec. 3.1)."""
+    assert AP.ACOS_LO_INTERVAL == pytest.approx(tuple(golden["table1_arccos"]["interval"]))
+    assert AP.ACOS_HI_INTERVAL == pytest.approx(tuple(golden["table1_arcsin"]["interval"]))
+    lo, hi = AP.acos_pieces(4)
+    np.testing.assert_allclose(lo.num, golden["table1_arccos"]["coef"], rtol=2e-5, atol=2e-10)
+    np.testing.assert_allclose(hi.num, golden["table1_arcsin"]["coef"], rtol=2e-5, atol=2e-10)
+    z = np.linspace(0.0, 0.5, 20001)
+    assert np.max(np.abs(lo(z) - np.arccos(z))) <= golden["table1_arccos"]["eps"] * 1.001
+    z = np.linspace(0.5, 1.0, 20001)
+    assert np.max(np.abs(hi(np.sqrt(1.0 - z)) - np.arccos(z))) <= (
+        golden["table1_arcsin"]["eps"] * 1.001)
+
+
 @pytest.mark.parametrize("degree", [2, 3, 4])
 def test_exp_own_rational_level(degree):
     """The oracle's own (d,d) rational: its levelled error is attained by the C

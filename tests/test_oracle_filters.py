@@ -423,6 +423,18 @@ def test_metrics():
     np.testing.assert_allclose(lab_white, [100.0, 0.0, 0.0], atol=1e-9)
     red = M.srgb_to_lab(np.array([[255, 0, 0]], np.uint8))[0]
     np.testing.assert_allclose(red, [53.24, 80.09, 67.20], atol=0.1)  # textbook sRGB red
+    # a mid-tone exercises the sRGB transfer curve: sRGB (128, 128, 128) is
+    # L* 53.59, a* = b* = 0 in the standard conversion tables
+    grey = M.srgb_to_lab(np.array([[128, 128, 128]], np.uint8))[0]
+    np.testing.assert_allclose(grey, [53.59, 0.0, 0.0], atol=0.01)
+    # NCD: summed Lab distances over summed Lab norms of the first image;
+    # white vs red per pixel |(100, 0, 0) - (53.24, 80.09, 67.20)| / 100
+    wr = math.sqrt(46.76 ** 2 + 80.09 ** 2 + 67.20 ** 2) / 100.0
+    white = np.full((1, 2, 3), 255, np.uint8)
+    both_red = np.array([[[255, 0, 0], [255, 0, 0]]], np.uint8)
+    one_red = np.array([[[255, 255, 255], [255, 0, 0]]], np.uint8)
+    assert M.ncd(white, both_red) == pytest.approx(wr, rel=2e-3)
+    assert M.ncd(white, one_red) == pytest.approx(wr / 2, rel=2e-3)
     c = np.full((10, 10, 3), 100, np.uint8)
     d = c + 2
     assert M.psnr(c, d) == pytest.approx(10 * math.log10(255 ** 2 / 4))

@@ -93,6 +93,34 @@ def test_equioscillation(name, interval, degree):
     assert R.max_error(f, fit, a, b, 400001) <= fit.eps * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("degree", [3, 5])
+def test_equioscillation_oscillatory_target(degree):
+    """cos(12 z) on [0, 1], a target with nearly two periods on the
+    interval: the fit alternates p + 2 times at the level, and the level is
+    the maximum error over the interval."""
+    f = lambda z: np.cos(12.0 * np.asarray(z, dtype=np.float64))  # noqa: E731
+    fit = R.remez(f, 0.0, 1.0, degree)
+    e = R.equioscillation(f, fit)
+    assert len(e) == degree + 2
+    assert np.all(np.sign(e[1:]) == -np.sign(e[:-1]))
+    np.testing.assert_allclose(np.abs(e), fit.eps, rtol=1e-6)
+    assert R.max_error(f, fit, 0.0, 1.0, 400001) <= fit.eps * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("freq,degree", [(30.0, 3), (25.0, 4)])
+def test_zero_polynomial_when_the_target_alternates(freq, degree):
+    """cos(f z) on [0, 1] reaches +1 and -1 alternately at z = k pi / f, more
+    than p + 2 times for these f: by Chebyshev's alternation theorem the
+    zero polynomial is the best approximation and the level is exactly 1.
+    The exchange meets more than p + 2 extrema on the way and must keep the
+    p + 2 that contain the global maximum."""
+    f = lambda z: np.cos(freq * np.asarray(z, dtype=np.float64))  # noqa: E731
+    fit = R.remez(f, 0.0, 1.0, degree)
+    assert fit.eps == pytest.approx(1.0, rel=1e-6)
+    z = np.linspace(0.0, 1.0, 20001)
+    assert np.max(np.abs(fit(z))) < 1e-6  # the zero polynomial, up to the exchange's tolerance
+
+
 def test_degree_monotone():
     """More degrees of freedom never increase the minimax error."""
     for name, (a, b) in [("acos_lo", AP.ACOS_LO_INTERVAL), ("exp", (0.0, 10.0))]:
