@@ -195,6 +195,32 @@ def test_set_coefficients_round_trip(vf, golden):
     assert den[0] == 1.0 and np.isfinite(num).all()
 
 
+def test_set_coefficients_error_inside_the_interval(vf):
+    """The maximum error the library reports for a caller's approximant is
+    taken over the whole interval, not only near its ends: the zero
+    polynomial of z ln z on [0.05, 1] errs most at z = 1/e, by exactly 1/e
+    (a minimax fit errs most at the ends as well, so it cannot show this)."""
+    import math
+    try:
+        vf.set_coefficients("ent", "poly", 2, [0.0, 0.0, 0.0], lo=0.05, hi=1.0)
+        _, _, eps = vf.get_approximant("ent", "poly", 2, 0.05, 1.0)
+        assert eps == pytest.approx(1.0 / math.e, rel=1e-7)
+    finally:
+        vf.set_coefficients("ent", "poly", 2)
+
+
+def test_default_params_are_the_papers(vf):
+    """kappa = 0.33 (Sec. 3.2, the recommended kernel-width factor), the EXP
+    cut-off T = 10 (Sec. 3.2) and the ENT cut-off chosen per window (Sec. 3.3's
+    T = 0.05 at n = 9: a negative value asks for it)."""
+    import ctypes
+    p = vf.Params()
+    vf.lib().vf_default_params(ctypes.byref(p))  # the C defaults themselves
+    assert p.kappa == pytest.approx(0.33)
+    assert p.exp_cutoff == pytest.approx(10.0)
+    assert p.ent_cutoff < 0.0
+
+
 def test_set_coefficients_errors(vf):
     E = vf.VFError
     with pytest.raises(E) as e:
@@ -208,6 +234,10 @@ def test_set_coefficients_errors(vf):
     assert e.value.name == "VF_ERR_UNSUPPORTED"
     with pytest.raises(E) as e:  # denominator 1 - z/5 vanishes at z = 5
         vf.set_coefficients("exp", "rational_fit", 2, [1.0, 0.0, 0.0], [1.0, -0.2, 0.0], 0.0, 10.0)
+    assert e.value.name == "VF_ERR_ARG"
+    with pytest.raises(E) as e:  # a zero between sample points: the sign change tells
+        vf.set_coefficients("exp", "rational_fit", 2, [1.0, 0.0, 0.0],
+                            [1.0, -1.0 / 5.00003, 0.0], 0.0, 10.0)
     assert e.value.name == "VF_ERR_ARG"
     with pytest.raises(E) as e:
         vf.set_coefficients("ent", "poly", 2, [0.0, float("nan"), 0.0], lo=0.05, hi=1.0)
