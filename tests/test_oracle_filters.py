@@ -400,6 +400,32 @@ def test_noise_rates():
     assert (pats == 7).mean() > 0.2
 
 
+def test_impulse_values_uniform():
+    """Eq. eq_noise: a replaced channel takes a random value r_k, uniform on
+    0..255 (random-valued impulses, not salt-and-pepper): over 95,000-115,000
+    replaced channels of a flat image every level occurs, with mean 127.5 and
+    standard deviation sqrt((256^2 - 1) / 12) = 73.9 within sampling error."""
+    flat = np.full((400, 400, 3), 77, np.uint8)
+    for noisy in (synth.impulse_uncorrelated(flat, 0.24, 31),
+                  synth.impulse_correlated(flat, 0.4, 32)):
+        v = noisy[noisy != 77].astype(np.float64)
+        assert v.size > 90_000
+        assert len(np.unique(v)) == 255  # every level but the flat one
+        sd = math.sqrt((256 ** 2 - 1) / 12.0)
+        assert abs(v.mean() - 127.5) < 4 * sd / math.sqrt(v.size) + 0.3
+        assert v.std() == pytest.approx(sd, rel=0.01)
+
+
+def test_gaussian_noise_sigma():
+    """The Gaussian part of the mixed model: zero mean, standard deviation
+    sigma (here 10 levels on a flat mid-grey image, far from the clamps)."""
+    flat = np.full((300, 300, 3), 128, np.uint8)
+    d = synth.gaussian(flat, 10.0, 41).astype(np.float64) - 128.0
+    assert abs(d.mean()) < 4 * 10.0 / math.sqrt(d.size)
+    # rounding to integers adds variance 1/12
+    assert d.std() == pytest.approx(math.sqrt(100.0 + 1.0 / 12.0), rel=0.01)
+
+
 def test_generator_deterministic():
     a = synth.noisy(64, 48, 0.1, 5)[1]
     b = synth.noisy(64, 48, 0.1, 5)[1]
