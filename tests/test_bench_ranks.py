@@ -99,3 +99,34 @@ def test_roofline_object():
     assert r["traffic"] == 7 * (1 << 20) and r["bound"] == "alu"
     empty = bench.roofline("x", None, 100, 1.0, 2000.0)
     assert empty["frac"] is None and empty["traffic"] is None
+
+
+def test_clock_summary():
+    """The clock record of the result line from nvidia-smi's csv,noheader,
+    nounits lines: median SM clock, the largest maximum clock, every throttle
+    reason seen Active (sw_power_cap here), peak power ([N/A] skipped)."""
+    lines = [
+        "0, 2070, 2070, 220.76, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1965, 2070, 1390.12, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, [N/A], 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "garbage line\n",
+    ]
+    ck = bench.clock_summary(lines)
+    assert ck["sm_mhz"] == 2070.0 and ck["sm_max_mhz"] == 2070.0
+    assert ck["reasons"] == ["sw_power_cap"] and ck["samples"] == 3
+    assert ck["power_w_max"] == 1390.12
+    hot = bench.clock_summary([lines[0].replace("Not Active, Not Active, Not Active, Not Active",
+                                                "Active, Not Active, Active, Not Active")])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.clock_summary([])["reasons"] == ["no samples"]
+
+
+def test_clocks_without_nvidia_smi(monkeypatch):
+    """Where nvidia-smi cannot be started the record says so instead of
+    failing the run."""
+    def no_smi(*a, **k):
+        raise OSError("nvidia-smi not found")
+    monkeypatch.setattr(bench.subprocess, "Popen", no_smi)
+    c = bench.Clocks(0)
+    c.start()
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
