@@ -181,9 +181,10 @@ typedef struct {
 } vfo_diag;
 
 /* Sec. 3 / Fig. fig_window: gather the n window samples of (r,c) in raster
- * order, with the borders replicating the nearest pixel. */
+ * order, with the borders replicating the nearest pixel; off[i] (optional) is
+ * the pixel index sample i was read from. */
 static void vfo_gather(const uint8_t* img, int H, int W, int C, int w, int r, int c,
-                       double x[][3]) {
+                       double x[][3], size_t* off) {
   int R = w / 2, i = 0;
   for (int dy = -R; dy <= R; ++dy) {
     int rr = r + dy;
@@ -194,6 +195,7 @@ static void vfo_gather(const uint8_t* img, int H, int W, int C, int w, int r, in
       if (cc < 0) cc = 0;
       if (cc > W - 1) cc = W - 1;
       const uint8_t* px = img + ((size_t)rr * W + cc) * C;
+      if (off) off[i] = (size_t)rr * W + cc;
       x[i][0] = px[0];
       x[i][1] = px[1];
       x[i][2] = px[2];
@@ -339,11 +341,16 @@ int vfo_filter_rows(const uint8_t* img, int H, int W, int C, const vfo_params* p
   if (w < 1 || (w & 1) == 0 || w * w > VFO_MAXN || C < 3 || H < 1 || W < 1) return -1;
   int n = w * w, Cc = (n + 1) / 2 - 1;
   double (*x)[3] = malloc(sizeof(double[3]) * (size_t)n);
-  if (!x) return -1;
+  size_t* off = malloc(sizeof(size_t) * (size_t)n);
+  if (!x || !off) {
+    free(x);
+    free(off);
+    return -1;
+  }
   for (int r = row0; r < row1; ++r) {
     for (int c = 0; c < W; ++c) {
       size_t pix = (size_t)r * W + c;
-      vfo_gather(img, H, W, C, w, r, c, x);
+      vfo_gather(img, H, W, C, w, r, c, x, off);
       double y[3];
       int sel = -1, sw = 0;
       double gap = INFINITY;
@@ -382,21 +389,26 @@ int vfo_filter_rows(const uint8_t* img, int H, int W, int C, const vfo_params* p
         }
         default:
           free(x);
+          free(off);
           return -1;
       }
+      /* bytes past the colour (RGBX): those of the selected sample's pixel
+       * for a selection, of the centre pixel for a weighted mean */
       uint8_t* o = out + pix * C;
       if (sel >= 0) {
         for (int k = 0; k < 3; ++k) o[k] = (uint8_t)x[sel][k];
+        for (int k = 3; k < C; ++k) o[k] = img[off[sel] * C + k];
       } else {
         for (int k = 0; k < 3; ++k) o[k] = vfo_round_u8(y[k]);
+        for (int k = 3; k < C; ++k) o[k] = img[pix * C + k];
       }
-      for (int k = 3; k < C; ++k) o[k] = img[pix * C + k];
       if (dg && dg->sel) dg->sel[pix] = sel;
       if (dg && dg->gap) dg->gap[pix] = gap;
       if (dg && dg->sw) dg->sw[pix] = (uint8_t)sw;
     }
   }
   free(x);
+  free(off);
   return 0;
 }
 

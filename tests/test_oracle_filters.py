@@ -101,6 +101,30 @@ def test_impulse_removed(crit):
         np.testing.assert_array_equal(out[3, 3], (90, 140, 60))
 
 
+@pytest.mark.parametrize("crit", ["vmf", "bvdf", "evmf", "evbdf", "amnfe", "amnfg"])
+def test_fourth_byte_convention(crit):
+    """RGBX images: only the first three bytes are colour (Sec. 3: RGB
+    vectors).  The library's convention for the fourth byte: a selection
+    (VMF, BVDF, the switched EVMF / EVBDF, or their centre when not switched)
+    carries the selected sample's pixel's byte, a weighted mean (AMNF) the
+    centre pixel's.  Checked on random fourth bytes, borders included."""
+    clean, noisy = synth.noisy(13, 17, 0.3, 44)
+    rng = np.random.default_rng(45)
+    img = np.concatenate([noisy, rng.integers(0, 256, (13, 17, 1)).astype(np.uint8)], axis=2)
+    out, d = F.filter_image(img, F.Config(crit, 3))
+    np.testing.assert_array_equal(out[..., :3], F.filter_image(noisy, F.Config(crit, 3))[0])
+    for r in range(13):
+        for c in range(17):
+            s = d["sel"][r, c]
+            if s < 0:
+                src = (r, c)
+            else:
+                src = (min(max(r + s // 3 - 1, 0), 12), min(max(c + s % 3 - 1, 0), 16))
+                assert (img[src][:3] == out[r, c, :3]).all()
+            assert out[r, c, 3] == img[src][3]
+    assert (d["sel"] >= 0).any() if crit not in ("amnfe", "amnfg") else (d["sel"] < 0).all()
+
+
 def test_border_replicates():
     """1 x 1 and 1 x n images: every window repeats border pixels."""
     img = np.array([[[10, 20, 30]]], np.uint8)
