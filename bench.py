@@ -469,24 +469,30 @@ def main():
                                                            e2e_sync_s * 1e3), 1),
                    "sync_call": "vf_filter_host per launch (waits after each image)"}
 
+    # the side sections run after the step's own measurements; a failure in
+    # one is recorded in its place and the result line is still printed
     if not args.no_batch:
-        sections["batched"] = bench_batch()
+        run_section(sections, "batched", bench_batch)
     if not args.no_precision:
-        sections["precision"] = bench_precision()
-        sections["rational_fit"] = bench_rational_fit()
-        sections["quality_study"] = bench_quality_study()
-        sections["generalized_evf"] = bench_generalized_evf()
+        run_section(sections, "precision", bench_precision)
+        run_section(sections, "rational_fit", bench_rational_fit)
+        run_section(sections, "quality_study", bench_quality_study)
+        run_section(sections, "generalized_evf", bench_generalized_evf)
     if not args.no_gate:
-        sections["gate"] = bench_gate()
+        run_section(sections, "gate", bench_gate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(imgs, V, budget_s=15.0)
-    line["summary"] = summarize(sections)
+        run_section(line, "cpu_baseline", lambda: cpu_baseline(imgs, V, budget_s=15.0))
+    run_section(line, "summary", lambda: summarize(sections))
     if rank == 0:
         if args.sections_out:
-            os.makedirs(os.path.dirname(os.path.abspath(args.sections_out)), exist_ok=True)
-            with open(args.sections_out, "w") as fh:
-                json.dump(sections, fh, indent=1)
-            line["sections_file"] = args.sections_out
+            try:
+                os.makedirs(os.path.dirname(os.path.abspath(args.sections_out)), exist_ok=True)
+                with open(args.sections_out, "w") as fh:
+                    json.dump(sections, fh, indent=1)
+                line["sections_file"] = args.sections_out
+            except OSError as e:
+                line["sections_file"] = None
+                line["sections_error"] = str(e)[:200]
         print(json.dumps(line, separators=(",", ":")))
     if dist:
         dist.destroy_process_group()
@@ -535,6 +541,17 @@ def roofline(kernel, counts, pixels, launch_ms, sm_mhz):
     return roof
 
 
+def run_section(sections, name, fn):
+    """sections[name] = fn(); an exception is recorded in its place (its type
+    and first line) so that one failing side section leaves the rest of the
+    result line intact."""
+    try:
+        sections[name] = fn()
+    except Exception as e:  # noqa: BLE001 -- any failure of a side section
+        msg = ("%s: %s" % (type(e).__name__, e)).splitlines()[0][:300]
+        sections[name] = {"error": msg}
+
+
 def summarize(sections):
     """A few KB of the side sections for the result line: per filter and window
     the exact Mpix/s and the fastest minimax variant meeting the quality bar;
@@ -548,17 +565,20 @@ def summarize(sections):
         for k, v in pfw.items()}
     out["per_filter_window_columns"] = ["exact Mpix/s", "best minimax meeting the bar",
                                         "its Mpix/s", "speedup over exact"]
+    for name in ("batched", "precision", "gate"):
+        if "error" in (sections.get(name) or {}):
+            out[name] = sections[name]
     b = sections.get("batched")
-    if b:
+    if b and "error" not in b:
         out["batched"] = {"mpix_s": b["mpix_s"], "speedup_vs_per_image": b["speedup_vs_per_image"]}
     pr = sections.get("precision")
-    if pr:
+    if pr and "error" not in pr:
         out["precision"] = {k: [v["mpix_s"], v.get("changed_vs_oracle", v.get("changed_vs_fp32_exact")),
                                 v["psnr_drop_db"]]
                             for k, v in pr["variants"].items() if "/w5/" in k}
         out["precision_columns"] = ["Mpix/s", "changed fraction", "PSNR drop dB"]
     g = sections.get("gate")
-    if g:
+    if g and "error" not in g:
         out["gate"] = {"speedup_gated_vs_plain": g["speedup_gated_vs_plain"],
                        "speedup_gated_vs_exact": g.get("speedup_gated_vs_exact"),
                        "psnr_gain_db": round(g["psnr_gated_db_mean"] - g["psnr_plain_db_mean"], 3),

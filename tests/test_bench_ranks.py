@@ -130,3 +130,30 @@ def test_clocks_without_nvidia_smi(monkeypatch):
     c = bench.Clocks(0)
     c.start()
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_failed_side_section_keeps_the_line():
+    """A side section that raises is recorded as {"error": ...} in its place;
+    the summary of the others is still built."""
+    sections = {"per_filter_window": {
+        "vmf/w3": {"exact_mpix_s": 100.0, "best_minimax": None},
+        "bvdf/w5": {"exact_mpix_s": 10.0, "best_minimax": "poly3",
+                    "poly3": {"mpix_s": 11.0, "speedup": 1.1}}}}
+    bench.run_section(sections, "batched", lambda: {"mpix_s": 5.0, "speedup_vs_per_image": 1.05})
+
+    def boom():
+        raise RuntimeError("CUDA error: an illustrative failure\nsecond line")
+    bench.run_section(sections, "precision", boom)
+    bench.run_section(sections, "gate", lambda: {
+        "speedup_gated_vs_plain": 0.74, "psnr_gated_db_mean": 33.3, "psnr_plain_db_mean": 33.0,
+        "flagged_fraction_mean": 0.36,
+        "per_frame_forms": [{"flagged": 0.3, "plain_ms": 1.0, "gate_ms": 0.2, "gated_default_ms": 0.9},
+                            {"flagged": 0.1, "plain_ms": 1.0, "gate_ms": 0.2, "gated_default_ms": 0.6}]})
+    assert sections["precision"] == {"error": "RuntimeError: CUDA error: an illustrative failure"}
+    out = bench.summarize(sections)
+    assert out["per_filter_window"]["bvdf/w5"] == [10.0, "poly3", 11.0, 1.1]
+    assert out["per_filter_window"]["vmf/w3"] == [100.0, None, None, None]
+    assert out["batched"] == {"mpix_s": 5.0, "speedup_vs_per_image": 1.05}
+    assert out["precision"] == sections["precision"]
+    assert out["gate"]["cleanest_frame"] == {"flagged": 0.1, "speedup_vs_plain": 1.25}
+    assert out["gate"]["psnr_gain_db"] == 0.3
